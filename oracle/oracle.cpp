@@ -1,0 +1,393 @@
+// CPU oracle for the CatBoost training hot path (arXiv 1810.11363).
+//
+// TEST INFRASTRUCTURE ONLY. This file is a plain, slow, single-threaded
+// restatement of what the method computes, in FP64 unless a step fixes the
+// storage precision. It exists so that tests, the smoke check and the CPU
+// baseline of the benchmark can compare the CUDA library against something
+// obviously correct. Nothing in the product path may link, load or call it, and
+// it shares no code with the CUDA sources.
+//
+// Built with -ffp-contract=off so that no multiply-add is fused: the ordered
+// target statistic is evaluated exactly as written, which makes it bit-exact
+// against the GPU for binary labels.
+//
+// Steps and the passages they follow:
+//   permutation      Section 2, the random permutation sigma before Eq. 1
+//                    (generator: SplitMix64, Steele, Lea & Flood 2014; a reading,
+//                    the paper names none)
+//   prior            Section 2, the prior P after Eq. 1
+//   ordered TS       Section 2, Eq. 1
+//   borders / bins   Section 4 "Dense numerical features" (fixed number of bins,
+//                    at most 255 per feature, 8 bits per feature)
+//   gradients        Section 3, g = dLoss/da, Algorithm 1
+//   histogram        Section 4, hist[j][b] = sum over rows with f_j = b of g
+//   split score      Section 3 (enumerate splits, set leaf values, score the
+//                    tree) + Section 4 "Fast scorer" (one split per level)
+//   leaf index       Section 4 "Fast scorer": leaf = sum_i 2^i B(x, f(t,i))
+//   leaf values      Section 3: gradient / Newton step leaf values
+//
+// Parity pins for every function live in tests/test_oracle_*.py.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+namespace {
+
+constexpr int LOSS_RMSE = 0;
+constexpr int LOSS_LOGLOSS = 1;
+constexpr int DTYPE_F32 = 0;
+constexpr int DTYPE_BF16 = 1;
+constexpr int LABEL_BINARY = 0;
+
+// SplitMix64: output i of the generator seeded with `seed` is mix(seed + (i+1)*gamma).
+uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  const uint64_t gamma = 0x9E3779B97F4A7C15ULL;
+  uint64_t z = seed + (i + 1) * gamma;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Round a float to bfloat16 (round to nearest, ties to even) and back.
+float round_to_bf16(float v) {
+  if (std::isnan(v)) return v;
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7FFFu + lsb;
+  u &= 0xFFFF0000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// The value a gradient takes once it is stored: first rounded to FP32, then
+// (for BF16 storage) to bfloat16.
+double stored(double v, int dtype) {
+  float f = static_cast<float>(v);
+  if (dtype == DTYPE_BF16) f = round_to_bf16(f);
+  return static_cast<double>(f);
+}
+
+double score_term(double G, double H, double l2) {
+  double den = H + l2;
+  if (den == 0.0) return 0.0;
+  return G * G / den;
+}
+
+}  // namespace
+
+extern "C" {
+
+// ---------------------------------------------------------------- permutation
+uint64_t or_splitmix64(uint64_t seed, uint64_t i) { return splitmix64_at(seed, i); }
+
+// sigma = row indices ordered by (key_i, i), key_i = SplitMix64 output i.
+void or_make_permutation(uint64_t seed, int64_t n, uint32_t* perm) {
+  std::vector<std::pair<uint64_t, uint32_t>> kv(n);
+  for (int64_t i = 0; i < n; ++i) kv[i] = {splitmix64_at(seed, i), static_cast<uint32_t>(i)};
+  std::sort(kv.begin(), kv.end());
+  for (int64_t p = 0; p < n; ++p) perm[p] = kv[p].second;
+}
+
+// ---------------------------------------------------------------------- prior
+// Binary labels: fraction of positive rows. Real labels: mean label, summed in
+// row order.
+double or_prior(const float* y, int64_t n, int label_kind) {
+  if (label_kind == LABEL_BINARY) {
+    int64_t pos = 0;
+    for (int64_t i = 0; i < n; ++i) pos += (y[i] == 1.0f) ? 1 : 0;
+    return static_cast<double>(pos) / static_cast<double>(n);
+  }
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += static_cast<double>(y[i]);
+  return s / static_cast<double>(n);
+}
+
+// ----------------------------------------------------------------- ordered TS
+// Eq. 1 for one categorical column: walk the rows in permutation order keeping,
+// per category, the label sum S and count N of the rows already seen; the row at
+// position p gets (S + a*P) / (N + a) before its own label is added.
+// cnt_before / sum_before (optional) receive N and S per row (row order).
+void or_ordered_ts(const uint32_t* cat, const float* y, int64_t n, const uint32_t* perm,
+                   double prior, double a, float* ts, uint32_t* cnt_before, double* sum_before) {
+  std::unordered_map<uint32_t, std::pair<double, uint64_t>> seen;
+  seen.reserve(static_cast<size_t>(n < 1024 ? 1024 : n / 4));
+  for (int64_t p = 0; p < n; ++p) {
+    uint32_t r = perm[p];
+    auto& st = seen[cat[r]];
+    double num = st.first + a * prior;
+    double den = static_cast<double>(st.second) + a;
+    ts[r] = static_cast<float>(num / den);
+    if (cnt_before) cnt_before[r] = static_cast<uint32_t>(st.second);
+    if (sum_before) sum_before[r] = st.first;
+    st.first += static_cast<double>(y[r]);
+    st.second += 1;
+  }
+}
+
+// Literal O(n^2) evaluation of Eq. 1 (numerator and denominator summed over
+// j < p), for tiny inputs only.
+void or_ordered_ts_quadratic(const uint32_t* cat, const float* y, int64_t n, const uint32_t* perm,
+                             double prior, double a, float* ts) {
+  for (int64_t p = 0; p < n; ++p) {
+    double s = 0.0, c = 0.0;
+    for (int64_t j = 0; j < p; ++j) {
+      if (cat[perm[j]] == cat[perm[p]]) {
+        s += static_cast<double>(y[perm[j]]);
+        c += 1.0;
+      }
+    }
+    ts[perm[p]] = static_cast<float>((s + a * prior) / (c + a));
+  }
+}
+
+// -------------------------------------------------------------------- borders
+// Borders of one column: v = the column sorted ascending; candidate k (1..B) is
+// v[floor(k*n/(B+1))]; keep the strictly increasing values below max(v). A -0.0
+// border is stored as +0.0. Returns the number of borders, or -1 if the column
+// holds a NaN or an infinity.
+int or_select_borders(const float* x, int64_t n, int max_borders, float* borders) {
+  std::vector<float> v(x, x + n);
+  for (float f : v)
+    if (!std::isfinite(f)) return -1;
+  std::sort(v.begin(), v.end());
+  const float vmax = v[n - 1];
+  int count = 0;
+  for (int k = 1; k <= max_borders; ++k) {
+    int64_t idx = (static_cast<int64_t>(k) * n) / (max_borders + 1);
+    float c = v[idx];
+    if (c == 0.0f) c = 0.0f;  // canonical +0
+    if (!(c < vmax)) continue;
+    if (count > 0 && !(c > borders[count - 1])) continue;
+    borders[count++] = c;
+  }
+  return count;
+}
+
+// ------------------------------------------------------------------- quantise
+// bin = number of borders strictly below x. x is column-major [F][n]; bins is
+// row-major [n][F_pad] and feature f goes to column f_offset + f. When `rows`
+// is given only those m rows are written (sampling at large sizes).
+void or_quantize(const float* x, int64_t n, int F, const float* borders, const int* n_borders,
+                 int max_borders, uint8_t* bins, int F_pad, int f_offset, const int64_t* rows,
+                 int64_t m) {
+  int64_t count = rows ? m : n;
+  for (int64_t t = 0; t < count; ++t) {
+    int64_t r = rows ? rows[t] : t;
+    for (int f = 0; f < F; ++f) {
+      const float* b = borders + static_cast<int64_t>(f) * max_borders;
+      float v = x[static_cast<int64_t>(f) * n + r];
+      int bin = static_cast<int>(std::lower_bound(b, b + n_borders[f], v) - b);
+      bins[r * F_pad + f_offset + f] = static_cast<uint8_t>(bin);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ gradients
+// RMSE: g = pred - y, h = 1. Logloss: p = 1/(1+exp(-pred)), g = p - y,
+// h = p(1-p). Both are then rounded to the storage type.
+void or_gradients(int loss, const float* y, const double* pred, int64_t n, int dtype, double* g,
+                  double* h) {
+  for (int64_t i = 0; i < n; ++i) {
+    double gi, hi;
+    if (loss == LOSS_RMSE) {
+      gi = pred[i] - static_cast<double>(y[i]);
+      hi = 1.0;
+    } else {
+      double p = 1.0 / (1.0 + std::exp(-pred[i]));
+      gi = p - static_cast<double>(y[i]);
+      hi = p * (1.0 - p);
+    }
+    g[i] = stored(gi, dtype);
+    h[i] = stored(hi, dtype);
+  }
+}
+
+double or_round_bf16(double v) { return static_cast<double>(round_to_bf16(static_cast<float>(v))); }
+
+// ------------------------------------------------------------------ histogram
+// hist[l][f][b][s] = sum over rows r with leaf[r] = l and bins[r][f] = b of
+// (g_r, h_r)[s], summed in row order. Layout [L][F][max_bins][2].
+void or_histogram(const uint8_t* bins, int64_t n, int F_pad, int F, const double* g,
+                  const double* h, const uint16_t* leaf, int n_leaves, int max_bins,
+                  double* hist) {
+  std::fill(hist, hist + static_cast<int64_t>(n_leaves) * F * max_bins * 2, 0.0);
+  for (int64_t r = 0; r < n; ++r) {
+    int l = leaf ? leaf[r] : 0;
+    for (int f = 0; f < F; ++f) {
+      int b = bins[r * F_pad + f];
+      double* cell = hist + ((static_cast<int64_t>(l) * F + f) * max_bins + b) * 2;
+      cell[0] += g[r];
+      cell[1] += h[r];
+    }
+  }
+}
+
+// -------------------------------------------------------------- split scores
+// For every feature f with n_borders[f] > 0 and border k < n_borders[f]:
+//   score(f,k) = sum over leaves l of  G_L^2/(H_L+l2) + G_R^2/(H_R+l2)
+// with L = bins <= k and R = bins > k of leaf l; a term whose denominator is 0
+// counts as 0. scores is [F][max_bins-1]; invalid candidates get -inf.
+// The best candidate is the largest score, exact ties going to the smallest f,
+// then the smallest k; second receives the second-largest score over all
+// candidates. Returns 0, or -1 if there is no candidate at all.
+int or_split_scores(const double* hist, int n_leaves, int F, const int* n_borders, int max_bins,
+                    double l2, double* scores, int* best_f, int* best_k, double* best_score,
+                    double* second_score) {
+  const int K = max_bins - 1;
+  const double ninf = -INFINITY;
+  std::vector<double> sufG(max_bins + 1), sufH(max_bins + 1);
+  for (int f = 0; f < F; ++f) {
+    double* sf = scores + static_cast<int64_t>(f) * K;
+    for (int k = 0; k < K; ++k) sf[k] = (k < n_borders[f]) ? 0.0 : ninf;
+    if (n_borders[f] <= 0) continue;
+    for (int l = 0; l < n_leaves; ++l) {
+      const double* hl = hist + (static_cast<int64_t>(l) * F + f) * max_bins * 2;
+      // running sums over bins above k, from the top
+      sufG[max_bins] = 0.0;
+      sufH[max_bins] = 0.0;
+      for (int b = max_bins - 1; b >= 0; --b) {
+        sufG[b] = sufG[b + 1] + hl[2 * b];
+        sufH[b] = sufH[b + 1] + hl[2 * b + 1];
+      }
+      double GL = 0.0, HL = 0.0;
+      for (int k = 0; k < n_borders[f]; ++k) {
+        GL += hl[2 * k];
+        HL += hl[2 * k + 1];
+        sf[k] += score_term(GL, HL, l2) + score_term(sufG[k + 1], sufH[k + 1], l2);
+      }
+    }
+  }
+  int bf = -1, bk = -1;
+  double bs = ninf, ss = ninf;
+  for (int f = 0; f < F; ++f) {
+    for (int k = 0; k < n_borders[f] && k < K; ++k) {
+      double s = scores[static_cast<int64_t>(f) * K + k];
+      if (bf < 0 || s > bs) {
+        if (bf >= 0) ss = std::max(ss, bs);
+        bs = s;
+        bf = f;
+        bk = k;
+      } else {
+        ss = std::max(ss, s);
+      }
+    }
+  }
+  *best_f = bf;
+  *best_k = bk;
+  *best_score = bs;
+  *second_score = ss;
+  return bf < 0 ? -1 : 0;
+}
+
+// ----------------------------------------------------------------- leaf index
+// Level d of an oblivious tree: leaf[r] += 2^d * [bins[r][f] > k].
+void or_update_leaf(const uint8_t* bins, int64_t n, int F_pad, int f, int k, int d,
+                    uint16_t* leaf) {
+  if (f < 0) return;
+  for (int64_t r = 0; r < n; ++r)
+    if (bins[r * F_pad + f] > k) leaf[r] = static_cast<uint16_t>(leaf[r] + (1u << d));
+}
+
+// Leaf index of every row for a whole tree (the scorer's encoding):
+// leaf = sum_i 2^i * [bins[r][f_i] > k_i]; levels with f_i < 0 add nothing.
+void or_tree_leaf_index(const uint8_t* bins, int64_t n, int F_pad, const int* f, const int* k,
+                        int depth, uint16_t* leaf) {
+  for (int64_t r = 0; r < n; ++r) {
+    unsigned idx = 0;
+    for (int i = 0; i < depth; ++i)
+      if (f[i] >= 0 && bins[r * F_pad + f[i]] > k[i]) idx += 1u << i;
+    leaf[r] = static_cast<uint16_t>(idx);
+  }
+}
+
+// --------------------------------------------------------------- leaf values
+// Per-leaf totals (G, H) summed in row order, then the Newton step
+// v = -G/(H + l2) (0 when the denominator is 0).
+void or_leaf_totals(const double* g, const double* h, const uint16_t* leaf, int64_t n,
+                    int n_leaves, double* tot) {
+  std::fill(tot, tot + 2 * n_leaves, 0.0);
+  for (int64_t r = 0; r < n; ++r) {
+    tot[2 * leaf[r]] += g[r];
+    tot[2 * leaf[r] + 1] += h[r];
+  }
+}
+
+void or_leaf_values(const double* tot, int n_leaves, double l2, double* v) {
+  for (int l = 0; l < n_leaves; ++l) {
+    double den = tot[2 * l + 1] + l2;
+    v[l] = (den == 0.0) ? 0.0 : -tot[2 * l] / den;
+  }
+}
+
+void or_apply_leaf_values(const uint16_t* leaf, int64_t n, const double* v, double lr,
+                          double* pred) {
+  for (int64_t r = 0; r < n; ++r) pred[r] += lr * v[leaf[r]];
+}
+
+// ----------------------------------------------------------------------- loss
+double or_loss(int loss, const float* y, const double* pred, int64_t n) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double yi = static_cast<double>(y[i]);
+    if (loss == LOSS_RMSE) {
+      double e = yi - pred[i];
+      s += e * e;
+    } else {
+      double p = 1.0 / (1.0 + std::exp(-pred[i]));
+      s += -(yi * std::log(p) + (1.0 - yi) * std::log(1.0 - p));
+    }
+  }
+  s /= static_cast<double>(n);
+  return loss == LOSS_RMSE ? std::sqrt(s) : s;
+}
+
+// ------------------------------------------------------------------- boosting
+// Classic (non-ordered) boosting of T oblivious trees of depth D on quantised
+// features, starting from pred = 0 (pred is in/out, FP64). Per tree: gradients
+// (rounded to the storage type), D levels of histogram + best split + leaf
+// update, then Newton leaf values and pred += lr * v[leaf].
+// Outputs per tree t and level d (arrays [T][D]): chosen feature and border,
+// best and second-best score; per tree: leaf values v [T][2^D] (before lr) and
+// the training loss after the tree [T].
+void or_fit(const uint8_t* bins, int64_t n, int F_pad, int F, const int* n_borders, int max_bins,
+            const float* y, int loss, int dtype, int depth, int trees, double lr, double l2,
+            double* pred, int* split_f, int* split_k, double* split_score, double* split_second,
+            double* leaf_values, double* losses) {
+  const int L = 1 << depth;
+  std::vector<double> g(n), h(n);
+  std::vector<uint16_t> leaf(n);
+  std::vector<double> hist(static_cast<size_t>(L / 2 > 0 ? L / 2 : 1) * F * max_bins * 2);
+  std::vector<double> scores(static_cast<size_t>(F) * (max_bins > 1 ? max_bins - 1 : 1));
+  std::vector<double> tot(2 * L), v(L);
+  for (int t = 0; t < trees; ++t) {
+    or_gradients(loss, y, pred, n, dtype, g.data(), h.data());
+    std::fill(leaf.begin(), leaf.end(), 0);
+    for (int d = 0; d < depth; ++d) {
+      int nl = 1 << d;
+      or_histogram(bins, n, F_pad, F, g.data(), h.data(), leaf.data(), nl, max_bins, hist.data());
+      int bf, bk;
+      double bs, ss;
+      or_split_scores(hist.data(), nl, F, n_borders, max_bins, l2, scores.data(), &bf, &bk, &bs,
+                      &ss);
+      split_f[t * depth + d] = bf;
+      split_k[t * depth + d] = bk;
+      split_score[t * depth + d] = bs;
+      split_second[t * depth + d] = ss;
+      or_update_leaf(bins, n, F_pad, bf, bk, d, leaf.data());
+    }
+    or_leaf_totals(g.data(), h.data(), leaf.data(), n, L, tot.data());
+    or_leaf_values(tot.data(), L, l2, v.data());
+    for (int l = 0; l < L; ++l) leaf_values[static_cast<int64_t>(t) * L + l] = v[l];
+    or_apply_leaf_values(leaf.data(), n, v.data(), lr, pred);
+    losses[t] = or_loss(loss, y, pred, n);
+  }
+}
+
+}  // extern "C"
