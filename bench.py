@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Throughput of the CatBoost training hot path on the GPU.
+
+One step = one pass of the whole path over the 1M-row Logloss workload (100 float +
+10 categorical features, 254 borders, depth 6, 1000 trees, lr 0.05, L2 3): permutation,
+prior, ordered target statistics, borders, quantisation, then 1000 boosting iterations
+(gradients, 6 levels of histogram + split search + leaf update/partition, leaf values
+and prediction update). Inputs are resident in HBM when a step starts; the L2 is
+flushed (256 MB write) between steps.
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "trees/s and row·feature·bins/s at 1M×110 depth 6; HBM roofline %; batched vs plain"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "hist_kernel_traffic.txt")
+HIST_SOURCE = os.path.join(ROOT, "paper_1810_11363_gb300", "csrc", "tree.cu")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--trees", type=int, default=1000)
+    p.add_argument("--gh", choices=["f32", "bf16"], default="f32")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--ref-sample-trees", type=int, default=2)
+    p.add_argument("--no-graph", action="store_true", help="launch every kernel from the host instead of "
+                                                           "replaying one captured tree")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sms.append(float(parts[1]))
+                    maxes.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": max(maxes) if maxes else None,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def hist_source_hash():
+    with open(HIST_SOURCE, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def recorded_traffic_per_row():
+    """DRAM bytes per histogrammed row from the committed ncu summary, if it was taken on
+    the current histogram source; else None."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            kv = dict(line.split(None, 1) for line in fh if line.strip() and not line.startswith("#"))
+        if kv.get("source_sha256_16", "").strip() != hist_source_hash():
+            return None
+        return float(kv["dram_bytes_per_row"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def oracle_sample(w, F_pad, trees):
+    """The oracle as it stands on the host: one timed preprocessing pass and `trees`
+    boosting iterations. Returns (t_prep, t_per_tree)."""
+    import oracle
+    t0 = time.perf_counter()
+    prep = oracle.preprocess(w, F_pad)
+    t1 = time.perf_counter()
+    oracle.fit(prep["bins"], w.n_features, prep["n_borders"], w.y, w.loss, w.depth, trees, w.lr, w.l2)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / trees, prep
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1810_11363_gb300 import synth, train
+    import oracle
+    w = synth.logloss_1m(trees=args.trees)
+    F_pad = train.f_pad_for(w.n_features)
+    t0 = time.perf_counter()
+    prep = oracle.preprocess(w, F_pad)
+    t_prep = time.perf_counter() - t0
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        oracle.fit(prep["bins"], w.n_features, prep["n_borders"], w.y, w.loss, w.depth, 1, w.lr, w.l2)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    t_tree = sum(times) / len(times)
+    step = t_prep + args.trees * t_tree
+    value = args.trees / step
+    sample = (f"oracle (single-threaded C++ FP64) on logloss_1m: one timed preprocessing pass ({t_prep:.1f} s) "
+              f"and {args.steps} timed single-tree boosting iterations after {args.warmup} untimed "
+              f"({t_tree:.2f} s/tree); a {args.trees}-tree step extrapolated as prep + {args.trees} x tree")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "logloss_1m: n=1,000,000, 100 float + 10 categorical features, 254 borders, "
+                                   f"depth 6, {args.trees} trees, lr 0.05, L2 3", "trees": args.trees},
+            "cpu_baseline": {"value": value, "unit": "trees/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1810_11363_gb300 import cbg, synth, train
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w = synth.logloss_1m(trees=args.trees)
+    T, D = args.trees, w.depth
+
+    def host(a):
+        return torch.from_numpy(np.ascontiguousarray(a.view(np.int32) if a.dtype == np.uint32 else a))
+
+    hx, hcat, hy = host(w.x).pin_memory(), host(w.cat).pin_memory(), host(w.y).pin_memory()
+    x, cat, y = hx.to(dev), hcat.to(dev), hy.to(dev)
+    ctx = cbg.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    use_graph = not args.no_graph
+
+    def step(bufs, graph=use_graph):
+        prep = train.preprocess(ctx, x, cat, y, "binary", w.max_borders, a=w.a, seed=w.seed)
+        bufs.pred.zero_()
+        model = train.fit(ctx, prep, y, w.loss, D, T, w.lr, w.l2, gh_dtype=args.gh, bufs=bufs, use_graph=graph)
+        return prep, model
+
+    prep0 = train.preprocess(ctx, x, cat, y, "binary", w.max_borders, a=w.a, seed=w.seed)
+    bufs = train.alloc_fit(prep0, D, T, args.gh)
+    for _ in range(args.warmup):
+        step(bufs)
+    torch.cuda.synchronize()
+    cbg.cbg_tree_rows_histogrammed(ctx, bufs.shape, bufs.state, reset=True)
+    cbg.cbg_profile_read(ctx, reset=True)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    cbg.cbg_profile_enable(ctx, not use_graph)
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(bufs)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    cbg.cbg_profile_enable(ctx, False)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    hist_ms, hist_launches = cbg.cbg_profile_read(ctx, reset=True)
+    rows_hist = cbg.cbg_tree_rows_histogrammed(ctx, bufs.shape, bufs.state, reset=True)
+    hist_timing = "CUDA events around every histogram launch of the timed steps"
+    if use_graph:
+        # Events cannot time single launches inside a replayed graph: one more (untimed)
+        # step launches every kernel from the host with events around each histogram launch.
+        cbg.cbg_profile_enable(ctx, True)
+        flush.zero_()
+        step(bufs, graph=False)
+        cbg.cbg_profile_enable(ctx, False)
+        hist_ms, hist_launches = cbg.cbg_profile_read(ctx, reset=True)
+        rows_hist = cbg.cbg_tree_rows_histogrammed(ctx, bufs.shape, bufs.state, reset=True)
+        hist_timing = ("CUDA events around every histogram launch of one extra step with host launches "
+                       "(the timed steps replay a captured graph)")
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    trees_total = T * args.steps * ws
+    value = trees_total / (total_ms / 1e3)
+    n, F, mb = w.n, prep0.F, prep0.max_bins
+    rfb = n * F * mb * D * T * args.steps * ws / (total_ms / 1e3)
+
+    # roofline of the histogram kernel: algorithmic bytes = rows read x (F bins + g + h)
+    gh_bytes = 4 if args.gh == "f32" else 2
+    alg_bytes = rows_hist * (F + 2 * gh_bytes)
+    achieved = alg_bytes / (hist_ms / 1e3) / 1e9 if hist_ms > 0 else None
+    peak, peak_kind = measured_peak_hbm()
+    per_row = recorded_traffic_per_row()
+    rows_per_launch = rows_hist / max(hist_launches, 1)
+    roofline = {"bound": "hbm", "kernel": "hist_kernel", "achieved": achieved, "peak": peak,
+                "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": per_row * rows_per_launch if per_row else None,
+                "alg_bytes_per_launch": alg_bytes / max(hist_launches, 1),
+                "launches": hist_launches, "avg_launch_us": hist_ms * 1e3 / max(hist_launches, 1),
+                "timing": hist_timing}
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        h2d = hx.numel() * 4 + hcat.numel() * 4 + hy.numel() * 4
+        d2h = n * 4 + T * D * 16 + T * (1 << D) * 8
+        pred_h = torch.empty(n, dtype=torch.float32).pin_memory()
+        sp_h = torch.empty((T, D, 2), dtype=torch.float64).pin_memory()
+        lv_h = torch.empty((T, 1 << D), dtype=torch.float64).pin_memory()
+        e2e_ms = []
+        for i in range(1 + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xd, cd, yd = hx.to(dev, non_blocking=True), hcat.to(dev, non_blocking=True), hy.to(dev, non_blocking=True)
+            prep = train.preprocess(ctx, xd, cd, yd, "binary", w.max_borders, a=w.a, seed=w.seed)
+            bufs.pred.zero_()
+            model = train.fit(ctx, prep, yd, w.loss, D, T, w.lr, w.l2, gh_dtype=args.gh, bufs=bufs,
+                              use_graph=use_graph)
+            pred_h.copy_(model.pred, non_blocking=True)
+            sp_h.copy_(model.splits, non_blocking=True)
+            lv_h.copy_(model.leaf_values, non_blocking=True)
+            torch.cuda.synchronize()
+            if i > 0:
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e = {"value": T * args.steps * ws / (sum(e2e_ms) / 1e3), "unit": "trees/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": sum(e2e_ms) / len(e2e_ms)}
+
+    launches_per_step = None
+    # kernels of ours per step: preprocessing launches + per tree (levels x kernels + apply)
+    per_level = 7
+    launches_per_step = T * ((D - 1) * per_level + 5 + 1)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_prep, t_tree, _ = oracle_sample(w, prep0.F_pad, args.ref_sample_trees)
+        cpu = {"value": T / (t_prep + T * t_tree), "unit": "trees/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle on logloss_1m: one preprocessing pass ({t_prep:.1f} s) + {args.ref_sample_trees} "
+                         f"trees ({t_tree:.2f} s/tree); {T}-tree step extrapolated as prep + {T} x tree"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.gh, "data": "synthetic",
+                "config": {"workload": "logloss_1m: n=1,000,000, 100 float (40 N(0,1), 30 U(0,1), 30 lognormal) + "
+                                       "10 categorical (K 2..100k, Zipf 1.1), 254 borders (255 bins), depth 6, "
+                                       f"{T} trees, lr 0.05, L2 3, Logloss", "trees_per_step": T,
+                           "parallelism": f"replicas x{ws}", "l2_flush": "256 MB write between steps; inputs "
+                                                                             "(x 400 MB) larger than L2",
+                           "gh_storage": args.gh, "graph_replay": use_graph},
+                "row_feature_bins_per_s": rfb, "gpu_launches": launches_per_step * args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "breakdown": {"step_ms": step_ms}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

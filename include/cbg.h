@@ -1,0 +1,294 @@
+/*
+ * cbg.h -- C ABI of a GB300-native (sm_103a) library for the data-parallel hot
+ * path of CatBoost training, classic (non-ordered) boosting scheme, as defined in
+ * "CatBoost: gradient boosting with categorical features support"
+ * (Dorogush, Ershov, Gulin; arXiv 1810.11363).
+ *
+ * The path: ordered target statistics for categorical features (Section 2,
+ * Eq. 1); quantisation of every feature into uint8 bins (Section 4, "Dense
+ * numerical features"); per-(leaf, feature, bin) gradient/hessian histograms
+ * and L2-regularised split search for oblivious trees (Sections 3 and 4); leaf
+ * values, per-row leaf index and the prediction update (Section 3, Section 4
+ * "Fast scorer").
+ *
+ * Conventions shared by every call
+ *  - Pointers named as device arrays are CUDA device pointers on the context's
+ *    device, owned by the caller; the library never frees them. Pointers named
+ *    as host values are plain host memory.
+ *  - Every call returns a cbg_status: CBG_OK (0) or a negative error code.
+ *    Argument errors are detected on the host before anything is launched and
+ *    return CBG_EINVAL. cbg_last_error() gives a message for the last failure.
+ *  - Calls are asynchronous on the context's stream (launch order is stream
+ *    order); an error raised by a kernel after launch surfaces at the next
+ *    cbg_sync() or *_to_host helper. No call synchronises the host except
+ *    cbg_sync() and the helpers that say so.
+ *  - Layouts: float features and categorical ids are column-major ([F][n]).
+ *    Quantised bins use a grouped layout: features are taken 32 at a time and
+ *    feature f of row r is the byte at ((f / 32) * n + r) * 32 + f % 32, so one
+ *    32-feature group of one row is one 32-byte sector. F_pad (a multiple of 32)
+ *    is the padded feature count; bytes of features F..F_pad-1 must be zero. An
+ *    optional column-major copy bins_t [F][n] speeds up the per-level leaf update.
+ *  - Rows are indexed with int64_t n, 1 <= n <= 2^31 - 1.
+ */
+#ifndef CBG_H
+#define CBG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int cbg_status;
+#define CBG_OK 0
+#define CBG_EINVAL (-1)       /* bad argument, detected on the host          */
+#define CBG_ENOMEM (-2)       /* workspace or state buffer too small          */
+#define CBG_ECUDA (-3)        /* a CUDA runtime call failed                   */
+#define CBG_ETIMEOUT (-4)     /* a bounded device-side wait ran out           */
+#define CBG_EUNSUPPORTED (-5) /* valid request this build does not implement  */
+#define CBG_EDATA (-6)        /* a device-side data check failed (NaN, range) */
+
+enum { CBG_LABEL_BINARY = 0, CBG_LABEL_REAL = 1 };
+enum { CBG_LOSS_RMSE = 0, CBG_LOSS_LOGLOSS = 1 };
+enum { CBG_F32 = 0, CBG_BF16 = 1 };
+
+typedef struct cbg_ctx cbg_ctx;
+
+/* One level of an oblivious tree (Section 4 "Fast scorer": one split per
+ * level). A row goes to the "1" side iff its bin of `feature` is > `border`.
+ * feature = -1 means no candidate existed (every row stays on the "0" side). */
+typedef struct cbg_split {
+  int32_t feature;
+  int32_t border;
+  double score;
+} cbg_split;
+
+/* Histogram tiling. slab_chunks: 16-feature chunks per work item (2);
+ * rows_per_item: rows per CTA of a work unit; threads: threads per histogram
+ * CTA (a multiple of 32, <= 512); blocks_per_sm: unused (the grid is sized by
+ * the occupancy of clusters); cluster: CTAs per thread-block cluster that share
+ * one partial histogram through distributed shared memory (1..16; a smaller
+ * power of two is used if that many cannot be co-resident). Zero fields take
+ * library defaults. */
+typedef struct cbg_tiles {
+  int32_t slab_chunks;
+  int32_t rows_per_item;
+  int32_t threads;
+  int32_t blocks_per_sm;
+  int32_t cluster;
+} cbg_tiles;
+
+/* Shape of one boosting problem's tree state. */
+typedef struct cbg_tree_shape {
+  int64_t n;           /* rows                                   */
+  int32_t F;           /* features (floats + one TS column per categorical) */
+  int32_t F_pad;       /* padded feature count of bins, multiple of 32, >= F */
+  int32_t max_bins;    /* max over features of n_borders + 1, 2..256 (1 allowed: no split) */
+  int32_t max_depth;   /* 1..10                                  */
+  cbg_tiles tiles;     /* histogram tiling (zero fields = defaults) */
+} cbg_tree_shape;
+
+/* ------------------------------------------------------------ context ---- */
+
+/* Create a context on `device` using `cuda_stream` (a cudaStream_t, or NULL for
+ * the legacy default stream). `workspace_bytes` preallocates library scratch for
+ * the one-off steps (sorts and scans); 0 lets the library grow it on demand
+ * (growth is refused with CBG_ENOMEM while the stream is being captured). */
+cbg_status cbg_ctx_create(int device, void* cuda_stream, size_t workspace_bytes, cbg_ctx** out);
+void cbg_ctx_destroy(cbg_ctx* ctx);
+/* Message of the last failure on this context ("" if none). Never NULL. */
+const char* cbg_last_error(const cbg_ctx* ctx);
+/* Wait for the context's stream; returns CBG_ECUDA / CBG_EDATA / CBG_ETIMEOUT
+ * if an asynchronous failure was recorded, else CBG_OK. */
+cbg_status cbg_sync(cbg_ctx* ctx);
+cbg_status cbg_set_stream(cbg_ctx* ctx, void* cuda_stream);
+/* Number of SMs of the context's device (for tiling decisions). */
+int cbg_num_sms(const cbg_ctx* ctx);
+/* Library version string. */
+const char* cbg_version(void);
+
+/* ------------------------------------------------------- preprocessing ---- */
+
+/* The random permutation sigma of Section 2 (before Eq. 1). perm[p] is the row
+ * placed at position p: rows sorted by (k_i, i) with k_i the i-th output of a
+ * SplitMix64 generator seeded with `seed` (the paper names no generator).
+ * perm: device uint32 [n]. */
+cbg_status cbg_make_permutation(cbg_ctx* ctx, uint64_t seed, int64_t n, uint32_t* perm);
+
+/* Prior P of Eq. 1 (Section 2): the positive rate for binary labels, the mean
+ * label for real labels, computed in FP64 and written to the device double
+ * `prior_out`. y: device float [n]; binary labels must be exactly 0 or 1. */
+cbg_status cbg_prior(cbg_ctx* ctx, const float* y, int64_t n, int label_kind, double* prior_out);
+
+/* Ordered target statistics, Eq. 1 (Section 2), for C categorical columns:
+ * the row at position p of sigma gets (S + a*P) / (N + a), where N and S are the
+ * count and label sum of the earlier rows of sigma with the same category.
+ * cat: device uint32 [C][n] (any 32-bit ids); y: device float [n]; perm: device
+ * uint32 [n] (sigma); prior P and weight a > 0 are host doubles. Outputs in row
+ * order: ts device float [C][n] (required); cnt_before device uint32 [C][n] and
+ * sum_before [C][n] (uint32 for BINARY labels, double for REAL labels)
+ * optional (NULL). N and binary S are exact integers; real S is an FP64
+ * segmented prefix sum. (S + a*P)/(N + a) is evaluated in FP64 without
+ * fused multiply-add and rounded to float. */
+cbg_status cbg_ordered_ts(cbg_ctx* ctx, const uint32_t* cat, const float* y, int64_t n, int32_t C,
+                          const uint32_t* perm, double prior, double a, int label_kind, float* ts,
+                          uint32_t* cnt_before, void* sum_before);
+
+/* Quantile borders per feature (Section 4: a fixed number of bins per feature,
+ * at most 255): v = column f sorted ascending; candidate k = 1..max_borders is
+ * v[floor(k*n/(max_borders+1))]; the strictly increasing candidates below max(v)
+ * are kept (a -0.0 border is stored as +0.0). x: device float [F][n];
+ * borders: device float [F][max_borders] (unused tail set to +inf);
+ * n_borders: device int32 [F]. max_borders in 1..254. A NaN or infinity in x
+ * makes the next cbg_sync() return CBG_EDATA. */
+cbg_status cbg_select_borders(cbg_ctx* ctx, const float* x, int64_t n, int32_t F,
+                              int32_t max_borders, float* borders, int32_t* n_borders);
+
+/* Quantisation (Section 4): bin = number of borders strictly below x, written
+ * as uint8 to feature f_offset + f of row r of bins (grouped layout, F_pad a
+ * multiple of 32) and, if bins_t is not NULL, to bins_t[f_offset + f][r]
+ * (column-major, row stride n).
+ * x: device float [F][n]; borders / n_borders as from cbg_select_borders.
+ * Columns outside [f_offset, f_offset+F) are not touched. */
+cbg_status cbg_quantize(cbg_ctx* ctx, const float* x, int64_t n, int32_t F, const float* borders,
+                        const int32_t* n_borders, int32_t max_borders, uint8_t* bins, int32_t F_pad,
+                        int32_t f_offset, uint8_t* bins_t);
+
+/* ------------------------------------------------------------ boosting ---- */
+
+/* Gradients of the loss at pred (Section 3, Algorithm 1: g = dLoss/da):
+ * RMSE g = pred - y, h = 1; Logloss p = 1/(1+exp(-pred)), g = p - y,
+ * h = p(1-p). Computed in FP32 and stored as float (CBG_F32) or bfloat16 with
+ * round-to-nearest-even (CBG_BF16) into g, h (device [n]). */
+cbg_status cbg_gradients(cbg_ctx* ctx, int loss, const float* y, const float* pred, int64_t n,
+                         int gh_dtype, void* g, void* h);
+
+/* Bytes of device scratch one tree build needs for `shape` (after tile
+ * defaults are applied). */
+cbg_status cbg_tree_state_bytes(const cbg_tree_shape* shape, size_t* bytes);
+
+/* Start a tree: every row in leaf 0. state: device scratch of at least
+ * cbg_tree_state_bytes(shape) bytes, 256-byte aligned, owned by the caller and
+ * reused for every level of the tree; leaf: device uint16 [n], set to 0. */
+cbg_status cbg_tree_begin(cbg_ctx* ctx, const cbg_tree_shape* shape, void* state,
+                          size_t state_bytes, uint16_t* leaf);
+
+/* Arguments of one level of greedy oblivious-tree growth. */
+typedef struct cbg_level_args {
+  const cbg_tree_shape* shape; /* host pointer                              */
+  void* state;                 /* device scratch from cbg_tree_begin         */
+  size_t state_bytes;
+  const uint8_t* bins;         /* device, grouped layout (see above)         */
+  const uint8_t* bins_t;       /* device [F][n] or NULL                      */
+  const int32_t* n_borders;    /* device int32 [F]; candidates k < n_borders[f] */
+  const void* g;               /* device [n] gradients (gh_dtype)            */
+  const void* h;               /* device [n] hessians (gh_dtype)             */
+  int32_t gh_dtype;            /* CBG_F32 or CBG_BF16                        */
+  int32_t depth;               /* level d, 0 <= d < max_depth; levels run in order */
+  double l2;                   /* L2 regularisation lambda >= 0              */
+  int32_t force_feature;       /* >= 0: take this split instead of the best  */
+  int32_t force_border;
+  uint16_t* leaf;              /* device [n] in/out: leaf += 2^d [bin > k]   */
+  cbg_split* splits;           /* device [max_depth]: splits[d] is written   */
+  double* child_totals;        /* device [2^(d+1)][2]: (G, H) of every child */
+  double* hist_out;            /* optional device [2^d][F][max_bins][2] FP64 */
+  int32_t last_level;          /* nonzero: skip re-partitioning the rows     */
+} cbg_level_args;
+
+/* One level d (Sections 3-4): FP64 histograms hist[l][f][b] = sum of (g, h)
+ * over rows of leaf l with bin b of feature f, for all 2^d leaves (FP32
+ * accumulation in shared memory, FP64 across blocks; one sibling of each pair
+ * is obtained by subtracting the other from the parent); the split (f, k)
+ * maximising sum_l G_L^2/(H_L+l2) + G_R^2/(H_R+l2) (terms with a zero
+ * denominator count as 0; ties to the smallest f, then k); the leaf update
+ * leaf += 2^d [bin_f > k]; the child totals; and the row partition used by the
+ * next level. */
+cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* args);
+
+/* Leaf values and prediction update (Section 3 leaf values as Newton steps;
+ * Section 4 "Fast scorer" leaf index): v_l = -G_l/(H_l + l2) (0 when the
+ * denominator is 0) from leaf_totals (device double [2^depth][2]), or taken
+ * from leaf_values_in (device double [2^depth]) when leaf_totals is NULL;
+ * leaf_r = sum_i 2^i [bins[r][f_i] > k_i] from splits (device [depth]) unless
+ * leaf_in (device uint16 [n]) is given; pred_r += float(lr * v_{leaf_r}) (pred
+ * device float [n], in/out; lr * v in FP64, the add in FP32). Optional outputs: leaf_out
+ * (device uint16 [n]), leaf_values_out (device double [2^depth], v before lr).
+ * If y, g and h are not NULL the gradients of `loss` at the updated pred are
+ * written to g, h in gh_dtype (fused next-tree gradients). */
+typedef struct cbg_apply_args {
+  const uint8_t* bins;
+  int64_t n;
+  int32_t F_pad;
+  const cbg_split* splits;
+  int32_t depth;
+  const double* leaf_totals;
+  const double* leaf_values_in;
+  double l2;
+  double lr;
+  const uint16_t* leaf_in;
+  uint16_t* leaf_out;
+  float* pred;
+  double* leaf_values_out;
+  const float* y;
+  int32_t loss;
+  int32_t gh_dtype;
+  void* g;
+  void* h;
+} cbg_apply_args;
+cbg_status cbg_apply_tree(cbg_ctx* ctx, const cbg_apply_args* args);
+
+/* Whole boosting run on one problem: T trees of depth D from the current pred
+ * (device float [n], in/out). Per tree: gradients (fused into the previous
+ * tree's apply), D levels of cbg_build_level, cbg_apply_tree. When use_graph is
+ * nonzero one tree is captured as a CUDA graph and replayed. Model outputs:
+ * splits device cbg_split [T][D], leaf_values device double [T][2^D] (v before
+ * lr). g, h: device scratch [n] of gh_dtype; leaf: device uint16 [n];
+ * state: tree-state scratch. */
+typedef struct cbg_boost_args {
+  const cbg_tree_shape* shape;
+  void* state;
+  size_t state_bytes;
+  const uint8_t* bins;
+  const uint8_t* bins_t;
+  const int32_t* n_borders;
+  const float* y;
+  int32_t loss;
+  int32_t gh_dtype;
+  int32_t depth;
+  int32_t trees;
+  double lr;
+  double l2;
+  float* pred;
+  void* g;
+  void* h;
+  uint16_t* leaf;
+  cbg_split* splits;
+  double* leaf_values;
+  double* child_totals;   /* device [2^depth][2] scratch */
+  int32_t use_graph;
+} cbg_boost_args;
+cbg_status cbg_boost(cbg_ctx* ctx, const cbg_boost_args* args);
+
+/* ------------------------------------------------------------ profiling ---- */
+
+/* Device-time accounting of the histogram kernel: while enabled, a pair of CUDA
+ * events is recorded on the context stream around every histogram launch.
+ * cbg_profile_read synchronises the stream and returns the summed device time
+ * (milliseconds) and the number of launches since the last reset (reset != 0
+ * clears both afterwards). Not available while the stream is being captured. */
+cbg_status cbg_profile_enable(cbg_ctx* ctx, int enable);
+cbg_status cbg_profile_read(cbg_ctx* ctx, int reset, double* hist_ms, int64_t* hist_launches);
+
+/* Rows read by histogram launches (rows of the leaves histogrammed directly,
+ * summed over levels) since the tree state was last reset through this call
+ * (reset != 0); synchronises the stream. The state must have been initialised
+ * by cbg_tree_begin. */
+cbg_status cbg_tree_rows_histogrammed(cbg_ctx* ctx, const cbg_tree_shape* shape, void* state, int reset,
+                                      int64_t* rows);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBG_H */

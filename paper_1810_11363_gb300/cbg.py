@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libcbg (include/cbg.h): the same entry points under the same
+names, taking torch tensors (device memory) and Python scalars. Only argument
+marshalling happens here; every step runs in the library's CUDA kernels.
+
+If the library is missing or cannot be built, importing the binding's loader raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+C = ctypes
+c_i32, c_i64, c_u64, c_f64, c_vp = C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_void_p
+
+CBG_OK, CBG_EINVAL, CBG_ENOMEM, CBG_ECUDA, CBG_ETIMEOUT, CBG_EUNSUPPORTED, CBG_EDATA = 0, -1, -2, -3, -4, -5, -6
+LABEL = {"binary": 0, "real": 1}
+LOSS = {"rmse": 0, "logloss": 1}
+DTYPE = {"f32": 0, "bf16": 1}
+STATUS_NAMES = {0: "CBG_OK", -1: "CBG_EINVAL", -2: "CBG_ENOMEM", -3: "CBG_ECUDA", -4: "CBG_ETIMEOUT",
+                -5: "CBG_EUNSUPPORTED", -6: "CBG_EDATA"}
+
+
+class CbgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Split(C.Structure):
+    _fields_ = [("feature", c_i32), ("border", c_i32), ("score", c_f64)]
+
+
+class Tiles(C.Structure):
+    _fields_ = [("slab_chunks", c_i32), ("rows_per_item", c_i32), ("threads", c_i32), ("blocks_per_sm", c_i32),
+                ("cluster", c_i32)]
+
+
+class TreeShape(C.Structure):
+    _fields_ = [("n", c_i64), ("F", c_i32), ("F_pad", c_i32), ("max_bins", c_i32), ("max_depth", c_i32),
+                ("tiles", Tiles)]
+
+
+class LevelArgs(C.Structure):
+    _fields_ = [("shape", C.POINTER(TreeShape)), ("state", c_vp), ("state_bytes", C.c_size_t),
+                ("bins", c_vp), ("bins_t", c_vp), ("n_borders", c_vp), ("g", c_vp), ("h", c_vp),
+                ("gh_dtype", c_i32), ("depth", c_i32), ("l2", c_f64), ("force_feature", c_i32),
+                ("force_border", c_i32), ("leaf", c_vp), ("splits", c_vp), ("child_totals", c_vp),
+                ("hist_out", c_vp), ("last_level", c_i32)]
+
+
+class ApplyArgs(C.Structure):
+    _fields_ = [("bins", c_vp), ("n", c_i64), ("F_pad", c_i32), ("splits", c_vp), ("depth", c_i32),
+                ("leaf_totals", c_vp), ("leaf_values_in", c_vp), ("l2", c_f64), ("lr", c_f64),
+                ("leaf_in", c_vp), ("leaf_out", c_vp), ("pred", c_vp), ("leaf_values_out", c_vp),
+                ("y", c_vp), ("loss", c_i32), ("gh_dtype", c_i32), ("g", c_vp), ("h", c_vp)]
+
+
+class BoostArgs(C.Structure):
+    _fields_ = [("shape", C.POINTER(TreeShape)), ("state", c_vp), ("state_bytes", C.c_size_t),
+                ("bins", c_vp), ("bins_t", c_vp), ("n_borders", c_vp), ("y", c_vp), ("loss", c_i32),
+                ("gh_dtype", c_i32), ("depth", c_i32), ("trees", c_i32), ("lr", c_f64), ("l2", c_f64),
+                ("pred", c_vp), ("g", c_vp), ("h", c_vp), ("leaf", c_vp), ("splits", c_vp),
+                ("leaf_values", c_vp), ("child_totals", c_vp), ("use_graph", c_i32)]
+
+
+# name -> (restype, argtypes); every entry point declared in include/cbg.h
+SIGNATURES = {
+    "cbg_version": (C.c_char_p, []),
+    "cbg_ctx_create": (c_i32, [C.c_int, c_vp, C.c_size_t, C.POINTER(c_vp)]),
+    "cbg_ctx_destroy": (None, [c_vp]),
+    "cbg_last_error": (C.c_char_p, [c_vp]),
+    "cbg_sync": (c_i32, [c_vp]),
+    "cbg_set_stream": (c_i32, [c_vp, c_vp]),
+    "cbg_num_sms": (C.c_int, [c_vp]),
+    "cbg_make_permutation": (c_i32, [c_vp, c_u64, c_i64, c_vp]),
+    "cbg_prior": (c_i32, [c_vp, c_vp, c_i64, C.c_int, c_vp]),
+    "cbg_ordered_ts": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_f64, c_f64, C.c_int, c_vp, c_vp, c_vp]),
+    "cbg_select_borders": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp]),
+    "cbg_quantize": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_i32, c_vp, c_i32, c_i32, c_vp]),
+    "cbg_gradients": (c_i32, [c_vp, C.c_int, c_vp, c_vp, c_i64, C.c_int, c_vp, c_vp]),
+    "cbg_tree_state_bytes": (c_i32, [C.POINTER(TreeShape), C.POINTER(C.c_size_t)]),
+    "cbg_tree_begin": (c_i32, [c_vp, C.POINTER(TreeShape), c_vp, C.c_size_t, c_vp]),
+    "cbg_build_level": (c_i32, [c_vp, C.POINTER(LevelArgs)]),
+    "cbg_apply_tree": (c_i32, [c_vp, C.POINTER(ApplyArgs)]),
+    "cbg_boost": (c_i32, [c_vp, C.POINTER(BoostArgs)]),
+    "cbg_profile_enable": (c_i32, [c_vp, C.c_int]),
+    "cbg_profile_read": (c_i32, [c_vp, C.c_int, C.POINTER(c_f64), C.POINTER(c_i64)]),
+    "cbg_tree_rows_histogrammed": (c_i32, [c_vp, C.POINTER(TreeShape), c_vp, C.c_int, C.POINTER(c_i64)]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build_if_stale: bool = True):
+    """Load libcbg.so (building it in-tree first when sources changed). Raises if the
+    library cannot be built or loaded."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_stale else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libcbg.so not found at {path}; run __graft_entry__.build()")
+            L = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(t):
+    """Device pointer of a tensor (or None)."""
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns a cbg_ctx on one device, bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, device: int = 0, stream=None, workspace_bytes: int = 0):
+        import torch
+        self.lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = c_vp()
+        st = self.lib.cbg_ctx_create(device, c_vp(stream.cuda_stream), workspace_bytes, C.byref(h))
+        if st != CBG_OK:
+            raise CbgError(st, "cbg_ctx_create failed")
+        self.h = h
+
+    def check(self, st: int, what: str = ""):
+        if st != CBG_OK:
+            raise CbgError(st, f"{what}: {self.lib.cbg_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cbg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---------------------------------------------------------------- entry points
+def cbg_version() -> str:
+    return load().cbg_version().decode()
+
+
+def cbg_sync(ctx: Context):
+    ctx.check(ctx.lib.cbg_sync(ctx.h), "cbg_sync")
+
+
+def cbg_num_sms(ctx: Context) -> int:
+    return int(ctx.lib.cbg_num_sms(ctx.h))
+
+
+def cbg_make_permutation(ctx: Context, seed: int, n: int, perm):
+    ctx.check(ctx.lib.cbg_make_permutation(ctx.h, seed, n, _p(perm)), "cbg_make_permutation")
+
+
+def cbg_prior(ctx: Context, y, n: int, label_kind: str, prior_out):
+    ctx.check(ctx.lib.cbg_prior(ctx.h, _p(y), n, LABEL[label_kind], _p(prior_out)), "cbg_prior")
+
+
+def cbg_ordered_ts(ctx: Context, cat, y, n: int, C_: int, perm, prior: float, a: float, label_kind: str, ts,
+                   cnt_before=None, sum_before=None):
+    ctx.check(ctx.lib.cbg_ordered_ts(ctx.h, _p(cat), _p(y), n, C_, _p(perm), prior, a, LABEL[label_kind],
+                                     _p(ts), _p(cnt_before), _p(sum_before)), "cbg_ordered_ts")
+
+
+def cbg_select_borders(ctx: Context, x, n: int, F: int, max_borders: int, borders, n_borders):
+    ctx.check(ctx.lib.cbg_select_borders(ctx.h, _p(x), n, F, max_borders, _p(borders), _p(n_borders)),
+              "cbg_select_borders")
+
+
+def cbg_quantize(ctx: Context, x, n: int, F: int, borders, n_borders, max_borders: int, bins, F_pad: int,
+                 f_offset: int = 0, bins_t=None):
+    ctx.check(ctx.lib.cbg_quantize(ctx.h, _p(x), n, F, _p(borders), _p(n_borders), max_borders, _p(bins),
+                                   F_pad, f_offset, _p(bins_t)), "cbg_quantize")
+
+
+def cbg_gradients(ctx: Context, loss: str, y, pred, n: int, gh_dtype: str, g, h):
+    ctx.check(ctx.lib.cbg_gradients(ctx.h, LOSS[loss], _p(y), _p(pred), n, DTYPE[gh_dtype], _p(g), _p(h)),
+              "cbg_gradients")
+
+
+def make_shape(n: int, F: int, F_pad: int, max_bins: int, max_depth: int, tiles: dict | None = None) -> TreeShape:
+    t = Tiles(**(tiles or {}))
+    return TreeShape(n, F, F_pad, max_bins, max_depth, t)
+
+
+def cbg_tree_state_bytes(shape: TreeShape) -> int:
+    out = C.c_size_t()
+    st = load().cbg_tree_state_bytes(C.byref(shape), C.byref(out))
+    if st != CBG_OK:
+        raise CbgError(st, "cbg_tree_state_bytes: invalid shape")
+    return int(out.value)
+
+
+def cbg_tree_begin(ctx: Context, shape: TreeShape, state, leaf):
+    ctx.check(ctx.lib.cbg_tree_begin(ctx.h, C.byref(shape), _p(state), state.numel() * state.element_size(),
+                                     _p(leaf)), "cbg_tree_begin")
+
+
+def cbg_build_level(ctx: Context, shape: TreeShape, state, bins, n_borders, g, h, gh_dtype: str, depth: int,
+                    l2: float, leaf, splits, child_totals, bins_t=None, force=None, hist_out=None,
+                    last_level: bool = False):
+    ff, fk = force if force is not None else (-1, -1)
+    a = LevelArgs(C.pointer(shape), _p(state), state.numel() * state.element_size(), _p(bins), _p(bins_t),
+                  _p(n_borders), _p(g), _p(h), DTYPE[gh_dtype], depth, l2, ff, fk, _p(leaf), _p(splits),
+                  _p(child_totals), _p(hist_out), int(last_level))
+    ctx.check(ctx.lib.cbg_build_level(ctx.h, C.byref(a)), "cbg_build_level")
+
+
+def cbg_apply_tree(ctx: Context, n: int, depth: int, pred, *, bins=None, F_pad: int = 32, splits=None,
+                   leaf_totals=None, leaf_values_in=None, l2: float = 0.0, lr: float = 1.0, leaf_in=None,
+                   leaf_out=None, leaf_values_out=None, y=None, loss: str = "rmse", gh_dtype: str = "f32",
+                   g=None, h=None):
+    a = ApplyArgs(_p(bins), n, F_pad, _p(splits), depth, _p(leaf_totals), _p(leaf_values_in), l2, lr,
+                  _p(leaf_in), _p(leaf_out), _p(pred), _p(leaf_values_out), _p(y), LOSS[loss],
+                  DTYPE[gh_dtype], _p(g), _p(h))
+    ctx.check(ctx.lib.cbg_apply_tree(ctx.h, C.byref(a)), "cbg_apply_tree")
+
+
+def cbg_boost(ctx: Context, shape: TreeShape, state, bins, n_borders, y, loss: str, gh_dtype: str, depth: int,
+              trees: int, lr: float, l2: float, pred, g, h, leaf, splits, leaf_values, child_totals,
+              bins_t=None, use_graph: bool = False):
+    a = BoostArgs(C.pointer(shape), _p(state), state.numel() * state.element_size(), _p(bins), _p(bins_t),
+                  _p(n_borders), _p(y), LOSS[loss], DTYPE[gh_dtype], depth, trees, lr, l2, _p(pred), _p(g),
+                  _p(h), _p(leaf), _p(splits), _p(leaf_values), _p(child_totals), int(use_graph))
+    ctx.check(ctx.lib.cbg_boost(ctx.h, C.byref(a)), "cbg_boost")
+
+
+def cbg_profile_enable(ctx: Context, enable: bool = True):
+    ctx.check(ctx.lib.cbg_profile_enable(ctx.h, int(enable)), "cbg_profile_enable")
+
+
+def cbg_profile_read(ctx: Context, reset: bool = True):
+    """-> (histogram device time in ms, histogram launches) since the last reset."""
+    ms, launches = c_f64(), c_i64()
+    ctx.check(ctx.lib.cbg_profile_read(ctx.h, int(reset), C.byref(ms), C.byref(launches)), "cbg_profile_read")
+    return float(ms.value), int(launches.value)
+
+
+def cbg_tree_rows_histogrammed(ctx: Context, shape: TreeShape, state, reset: bool = True) -> int:
+    rows = c_i64()
+    ctx.check(ctx.lib.cbg_tree_rows_histogrammed(ctx.h, C.byref(shape), _p(state), int(reset), C.byref(rows)),
+              "cbg_tree_rows_histogrammed")
+    return int(rows.value)

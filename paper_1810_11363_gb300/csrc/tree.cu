@@ -1,0 +1,1046 @@
+// Per-tree hot path: gradients, per-level histograms, split scoring, leaf update and row
+// partition, leaf values and prediction update (Sections 3 and 4 of the paper).
+//
+// Data layout in HBM
+//   bins      grouped uint8: feature f of row r at ((f/32)*n + r)*32 + f%32, so one
+//             32-feature group of one row is one 32-byte sector.
+//   order     uint32 [n]: rows grouped by leaf (stable), rebuilt every level.
+//   hist      FP64 [2^d][F][max_bins][2] (G, H) per level; the previous level's
+//             histogram is kept to obtain one sibling of each pair by subtraction.
+//   partials  FP32 [item][2][max_bins][32]: one shared-memory histogram per work item.
+#include "cbg_internal.cuh"
+#include "level_hist.cuh"
+
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+using namespace cbg;
+
+namespace {
+
+constexpr int PT = 2048;           // positions per partition tile (256 threads x 8)
+constexpr int PT_THREADS = 256;
+
+
+struct Segs {                       // row segments of the leaves of one level
+  int start[1 << MAX_DEPTH];
+  int cnt[1 << MAX_DEPTH];
+  int order[1 << MAX_DEPTH];        // leaf ids in memory order of their segments
+  unsigned ones[1 << MAX_DEPTH];    // rows of the leaf sent to the "1" side
+  unsigned ones_before[1 << MAX_DEPTH];
+};
+
+struct BestF {
+  double score;
+  int k;
+  int pad;
+};
+
+struct Layout {
+  int64_t n;
+  int F, F_pad, G, max_bins, nb_alloc, D;
+  int rows_per_item, threads, blocks_per_sm, cluster;
+  int64_t max_items;
+  int64_t n_ptiles;
+  size_t hist_elems;                // per hist buffer (doubles)
+  size_t part_elems_item;           // floats per partial item
+  size_t term_elems;
+  // byte offsets
+  size_t o_order_a, o_order_b, o_flags, o_tcnt, o_toff, o_seg_a, o_seg_b, o_plan, o_hist_a, o_hist_b,
+      o_part, o_term, o_best, o_misc, o_count, o_tot_a, o_tot_b, o_gsplit, o_gvals, total;
+};
+
+int pow2_at_least(int v) {
+  int p = 2;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+
+cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
+  CBG_REQUIRE(ctx, s != nullptr, "shape is NULL");
+  CBG_REQUIRE(ctx, s->n >= 1 && s->n <= INT32_MAX, "n must be in [1, 2^31-1]");
+  CBG_REQUIRE(ctx, s->F >= 1, "F must be >= 1");
+  CBG_REQUIRE(ctx, s->F_pad >= s->F && s->F_pad % GROUP == 0, "F_pad must be a multiple of 32 and >= F");
+  CBG_REQUIRE(ctx, s->max_bins >= 1 && s->max_bins <= 256, "max_bins must be in [1, 256]");
+  CBG_REQUIRE(ctx, s->max_depth >= 1 && s->max_depth <= MAX_DEPTH, "max_depth must be in [1, 10]");
+  const cbg_tiles& t = s->tiles;
+  CBG_REQUIRE(ctx, t.slab_chunks == 0 || t.slab_chunks == 2, "slab_chunks must be 0 (default) or 2");
+  CBG_REQUIRE(ctx, t.rows_per_item >= 0 && t.threads >= 0 && t.blocks_per_sm >= 0, "negative tile field");
+  CBG_REQUIRE(ctx, t.threads % 32 == 0 && t.threads <= 512, "threads must be a multiple of 32, <= 512");
+  L->n = s->n;
+  L->F = s->F;
+  L->F_pad = s->F_pad;
+  L->G = s->F_pad / GROUP;
+  L->max_bins = std::max(2, s->max_bins);
+  L->nb_alloc = pow2_at_least(L->max_bins);
+  L->D = s->max_depth;
+  CBG_REQUIRE(ctx, t.cluster >= 0 && t.cluster <= 16, "cluster must be in [0, 16]");
+  L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : 4096;
+  L->cluster = t.cluster > 0 ? t.cluster : 8;
+  L->threads = t.threads > 0 ? t.threads : 512;
+  const int fit = static_cast<int>((227 * 1024) / hist_smem_bytes(L->nb_alloc));
+  L->blocks_per_sm = std::max(1, std::min(t.blocks_per_sm > 0 ? t.blocks_per_sm : 3, fit));
+  const int hleaves = 1 << (L->D - 1);
+  L->max_items = static_cast<int64_t>(L->G) * (ceil_div(L->n, L->rows_per_item) + hleaves + 1);
+  L->n_ptiles = ceil_div(L->n, PT);
+  L->hist_elems = static_cast<size_t>(hleaves) * L->F * L->max_bins * 2;
+  L->part_elems_item = static_cast<size_t>(2) * L->max_bins * GROUP;
+  L->term_elems = static_cast<size_t>(hleaves) * L->F * (L->max_bins - 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) / 256 * 256;
+    size_t o = off;
+    off += bytes;
+    return o;
+  };
+  L->o_order_a = take(L->n * 4);
+  L->o_order_b = take(L->n * 4);
+  L->o_flags = take(L->n);
+  L->o_tcnt = take((L->n_ptiles + 1) * 4);
+  L->o_toff = take((L->n_ptiles + 1) * 4);
+  L->o_seg_a = take(sizeof(Segs));
+  L->o_seg_b = take(sizeof(Segs));
+  L->o_plan = take(sizeof(Plan));
+  L->o_hist_a = take(L->hist_elems * 8);
+  L->o_hist_b = take(L->hist_elems * 8);
+  L->o_part = take(static_cast<size_t>(L->max_items) * L->part_elems_item * 4);
+  L->o_term = take(L->term_elems * 4);
+  L->o_tot_a = take((static_cast<size_t>(2) << L->D) * 8);
+  L->o_tot_b = take((static_cast<size_t>(2) << L->D) * 8);
+  L->o_best = take(static_cast<size_t>(L->F) * sizeof(BestF) + 64);
+  L->o_misc = take(256);
+  L->o_count = take(256);
+  L->o_gsplit = take(sizeof(cbg_split) * MAX_DEPTH + 256);   // per-tree outputs while replaying a graph
+  L->o_gvals = take(sizeof(double) * (static_cast<size_t>(1) << L->D));
+  L->total = take(0) + 256;
+  return CBG_OK;
+}
+
+HistConfig hist_config(const Layout& L) {
+  HistConfig c;
+  c.n = L.n;
+  c.G = L.G;
+  c.F = L.F;
+  c.max_bins = L.max_bins;
+  c.nb_alloc = L.nb_alloc;
+  c.threads = L.threads;
+  c.cluster = L.cluster;
+  return c;
+}
+
+template <typename T>
+T* at(void* state, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(state) + off);
+}
+
+struct Misc {
+  unsigned done;        // blocks finished in the argmax kernel (reset by the last one)
+  unsigned done_part;   // blocks finished in the partition-flags kernel (reset by the last one)
+  double forced_score;
+};
+
+// ------------------------------------------------------------------ gradients
+template <typename GH>
+__global__ void gradients_kernel(int loss, const float* __restrict__ y, const float* __restrict__ pred, int64_t n,
+                                 GH* __restrict__ g, GH* __restrict__ h) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float p = pred[i], yi = y[i], gi, hi;
+    if (loss == CBG_LOSS_RMSE) {
+      gi = p - yi;
+      hi = 1.0f;
+    } else {
+      float s = 1.0f / (1.0f + expf(-p));
+      gi = s - yi;
+      hi = s * (1.0f - s);
+    }
+    cbgd::store_gh(g, i, gi);
+    cbgd::store_gh(h, i, hi);
+  }
+}
+
+unsigned grid_stride_blocks(int64_t n, int block) {
+  int64_t g = ceil_div(n, block);
+  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(g, 152LL * 64)));
+}
+
+// ------------------------------------------------------------------ tree begin
+__global__ void tree_begin_kernel(Plan* plan, Segs* seg, int n, int rows_per_item, int cs,
+                                  unsigned long long* rows_hist) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  *rows_hist += static_cast<unsigned long long>(n);
+  const int per_unit = rows_per_item * cs;
+  int chunks = (n + per_unit - 1) / per_unit;
+  if (chunks < 1) chunks = 1;
+  plan->n_small = 1;
+  plan->total_units = chunks;
+  plan->level_leaves = 1;
+  plan->small_leaf[0] = 0;
+  plan->large_leaf[0] = -1;
+  plan->parent[0] = -1;
+  plan->unit_begin[0] = 0;
+  plan->unit_begin[1] = chunks;
+  plan->chunk_rows[0] = (n + chunks * cs - 1) / (chunks * cs);
+  plan->seg_start[0] = 0;
+  plan->seg_cnt[0] = n;
+  seg->start[0] = 0;
+  seg->cnt[0] = n;
+  seg->order[0] = 0;
+}
+
+// ----------------------------------------------------------------- scoring
+// GB300 runs FP64 at a small fraction of the FP32 rate, so FP64 is kept to what the
+// precision needs: prefix sums over bins in FP64, then the candidate terms
+// G^2/(H + l2) in FP32 and their sum over leaves with compensated FP32 addition.
+
+__device__ __forceinline__ float score_term_f(float G, float H, float l2) {
+  const float den = H + l2;
+  return den == 0.0f ? 0.0f : G * G / den;
+}
+
+// Compensated FP32 pair (hi + lo): about 2^-44 relative precision on the FP32 pipe.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return DF{hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
+
+__device__ __forceinline__ DF df_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return DF{hi, __double2float_rn(x - static_cast<double>(hi))};
+}
+
+__device__ __forceinline__ DF df_shfl_up(DF v, int o) {
+  return DF{__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+}
+
+__device__ __forceinline__ DF df_shfl(DF v, int src) {
+  return DF{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+// One warp per (leaf l, feature f). Lane i owns bins [8i, 8i+8): compensated prefix sums
+// of the FP64 histogram give G_L(k), H_L(k); the leaf total is the last prefix, the right
+// side the rest. term[l][f][k] = G_L^2/(H_L+l2) + G_R^2/(H_R+l2) in FP32.
+constexpr int TERM_BINS_PER_LANE = 8;   // 32 lanes x 8 = 256 bins
+
+__global__ void leaf_terms_kernel(const double* __restrict__ hist, int level_leaves, int F, int max_bins,
+                                  const int32_t* __restrict__ n_borders, double l2, float* __restrict__ term) {
+  const int64_t wid = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= static_cast<int64_t>(level_leaves) * F) return;
+  const int l = static_cast<int>(wid / F), f = static_cast<int>(wid - static_cast<int64_t>(l) * F);
+  const int K = max_bins - 1;
+  const int nb = min(n_borders[f], K);
+  if (nb <= 0) return;
+  const double* hl = hist + (static_cast<int64_t>(l) * F + f) * max_bins * 2;
+  DF g[TERM_BINS_PER_LANE], h[TERM_BINS_PER_LANE];
+  DF sg{0.f, 0.f}, sh{0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < TERM_BINS_PER_LANE; ++i) {
+    const int b = lane * TERM_BINS_PER_LANE + i;
+    double2 v = b < max_bins ? reinterpret_cast<const double2*>(hl)[b] : make_double2(0.0, 0.0);
+    sg = df_add(sg, df_from_double(v.x));
+    sh = df_add(sh, df_from_double(v.y));
+    g[i] = sg;   // inclusive prefix within the lane
+    h[i] = sh;
+  }
+  // inclusive scan of lane totals
+  DF ig = sg, ih = sh;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const DF ug = df_shfl_up(ig, o), uh = df_shfl_up(ih, o);
+    if (lane >= o) {
+      ig = df_add(ug, ig);
+      ih = df_add(uh, ih);
+    }
+  }
+  const DF tg = df_shfl(ig, 31), th = df_shfl(ih, 31);
+  DF eg = df_shfl_up(ig, 1), eh = df_shfl_up(ih, 1);
+  if (lane == 0) eg = eh = DF{0.f, 0.f};
+  const float l2f = static_cast<float>(l2);
+  float* out = term + (static_cast<int64_t>(l) * F + f) * K;
+#pragma unroll
+  for (int i = 0; i < TERM_BINS_PER_LANE; ++i) {
+    const int k = lane * TERM_BINS_PER_LANE + i;
+    if (k < nb) {
+      const DF GL = df_add(eg, g[i]), HL = df_add(eh, h[i]);
+      const DF GR = df_sub(tg, GL), HR = df_sub(th, HL);
+      out[k] = score_term_f(GL.hi + GL.lo, HL.hi + HL.lo, l2f) + score_term_f(GR.hi + GR.lo, HR.hi + HR.lo, l2f);
+    }
+  }
+}
+
+__device__ __forceinline__ bool better(double s, int k, double bs, int bk) {
+  return s > bs || (s == bs && k < bk);
+}
+
+// Block per feature: score(f,k) = sum over leaves of term (compensated FP32); argmax over
+// k. The last block to finish picks the best feature (ties to the smallest f, then k),
+// writes the split and the child totals of every leaf.
+__global__ void argmax_kernel(const float* __restrict__ term, int level_leaves, int F, int max_bins,
+                              const int32_t* __restrict__ n_borders, BestF* __restrict__ best, Misc* misc,
+                              int force_f, int force_k, int depth, cbg_split* __restrict__ splits) {
+  __shared__ double s_sc[256];
+  __shared__ int s_k[256];
+  __shared__ bool is_last;
+  const int f = blockIdx.x, K = max_bins - 1;
+  const int nb = min(n_borders[f], K);
+  double bs = -INFINITY;
+  int bk = -1;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    float sum = 0.0f, comp = 0.0f;
+    for (int l = 0; l < level_leaves; ++l) {
+      const float y = term[(static_cast<int64_t>(l) * F + f) * K + k] - comp;
+      const float tsum = sum + y;
+      comp = (tsum - sum) - y;
+      sum = tsum;
+    }
+    const double s = static_cast<double>(sum) - static_cast<double>(comp);
+    if (f == force_f && k == force_k) misc->forced_score = s;
+    if (bk < 0 || better(s, k, bs, bk)) {
+      bs = s;
+      bk = k;
+    }
+  }
+  __threadfence();   // the forced-score store must be visible before this block is counted
+  s_sc[threadIdx.x] = bs;
+  s_k[threadIdx.x] = bk;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      int ok = s_k[threadIdx.x + o];
+      if (ok >= 0 && (s_k[threadIdx.x] < 0 || better(s_sc[threadIdx.x + o], ok, s_sc[threadIdx.x], s_k[threadIdx.x]))) {
+        s_sc[threadIdx.x] = s_sc[threadIdx.x + o];
+        s_k[threadIdx.x] = ok;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    best[f].score = s_sc[0];
+    best[f].k = s_k[0];
+    __threadfence();
+    unsigned ticket = atomicAdd(&misc->done, 1u);
+    is_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // last block: global argmax over features
+  double gbs = -INFINITY;
+  int gbf = -1, gbk = -1;
+  for (int ff = threadIdx.x; ff < F; ff += blockDim.x) {
+    double s = __ldcg(&best[ff].score);
+    int k = __ldcg(&best[ff].k);
+    if (k >= 0 && (gbf < 0 || s > gbs || (s == gbs && ff < gbf))) {
+      gbs = s;
+      gbf = ff;
+      gbk = k;
+    }
+  }
+  __shared__ double r_s[256];
+  __shared__ int r_f[256], r_k[256];
+  r_s[threadIdx.x] = gbs;
+  r_f[threadIdx.x] = gbf;
+  r_k[threadIdx.x] = gbk;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      int of = r_f[threadIdx.x + o];
+      double os = r_s[threadIdx.x + o];
+      int mf = r_f[threadIdx.x];
+      if (of >= 0 && (mf < 0 || os > r_s[threadIdx.x] || (os == r_s[threadIdx.x] && of < mf))) {
+        r_s[threadIdx.x] = os;
+        r_f[threadIdx.x] = of;
+        r_k[threadIdx.x] = r_k[threadIdx.x + o];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int cf = r_f[0], ck = r_k[0];
+    double cs = r_s[0];
+    if (force_f >= 0) {
+      cf = force_f;
+      ck = force_k;
+      cs = *(volatile double*)&misc->forced_score;
+    }
+    splits[depth].feature = cf;
+    splits[depth].border = cf >= 0 ? ck : -1;
+    splits[depth].score = cf >= 0 ? cs : -INFINITY;
+    misc->done = 0;
+  }
+}
+
+// Child totals of the chosen split, FP64: one warp per leaf of the level; leaf l keeps bins
+// <= k (child l), the rest go to child l + 2^d.
+__global__ void child_totals_kernel(const double* __restrict__ hist, int level_leaves, int F, int max_bins,
+                                    const cbg_split* __restrict__ splits, int depth,
+                                    double* __restrict__ child_totals, double* __restrict__ tot_next) {
+  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= level_leaves) return;
+  const int sf = splits[depth].feature, sk = splits[depth].border;
+  const int cf = sf >= 0 ? sf : 0;
+  const double2* hl = reinterpret_cast<const double2*>(hist + (static_cast<int64_t>(l) * F + cf) * max_bins * 2);
+  double g0 = 0.0, h0 = 0.0, g1 = 0.0, h1 = 0.0;
+  for (int b = lane; b < max_bins; b += 32) {
+    const double2 v = hl[b];
+    if (sf < 0 || b <= sk) {
+      g0 += v.x;
+      h0 += v.y;
+    } else {
+      g1 += v.x;
+      h1 += v.y;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    g0 += __shfl_down_sync(0xffffffffu, g0, o);
+    h0 += __shfl_down_sync(0xffffffffu, h0, o);
+    g1 += __shfl_down_sync(0xffffffffu, g1, o);
+    h1 += __shfl_down_sync(0xffffffffu, h1, o);
+  }
+  if (lane == 0) {
+    child_totals[2 * l] = g0;
+    child_totals[2 * l + 1] = h0;
+    child_totals[2 * (l + level_leaves)] = g1;
+    child_totals[2 * (l + level_leaves) + 1] = h1;
+    tot_next[2 * l] = g0;
+    tot_next[2 * l + 1] = h0;
+    tot_next[2 * (l + level_leaves)] = g1;
+    tot_next[2 * (l + level_leaves) + 1] = h1;
+  }
+}
+
+// ---------------------------------------------------------------- partition
+__device__ __forceinline__ int split_bit(const uint8_t* bins, const uint8_t* bins_t, int64_t n, uint32_t row,
+                                         int f, int k) {
+  if (f < 0) return 0;
+  uint8_t b = bins_t ? bins_t[static_cast<int64_t>(f) * n + row]
+                     : bins[(static_cast<int64_t>(f >> 5) * n + row) * GROUP + (f & 31)];
+  return b > k ? 1 : 0;
+}
+
+// Plan of the next level, run by one block: exclusive scan of the tile ones, ones before
+// every segment, the child segments, and the work units of the next level (the smaller
+// child of each pair is histogrammed directly, the other by subtraction).
+__device__ void plan_next_level(uint32_t* __restrict__ tile_cnt, int64_t n_ptiles, Segs* __restrict__ cur,
+                                Segs* __restrict__ nxt, Plan* __restrict__ plan, int depth, int rows_per_item,
+                                int cs, unsigned long long* __restrict__ rows_hist) {
+  __shared__ uint32_t sh[PT_THREADS / 32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < n_ptiles; b0 += blockDim.x) {
+    const int64_t idx = b0 + threadIdx.x;
+    uint32_t v = idx < n_ptiles ? __ldcg(tile_cnt + idx) : 0u;
+    uint32_t x = v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < PT_THREADS / 32; ++w) {
+        uint32_t t = sh[w];
+        sh[w] = run;
+        run += t;
+      }
+    }
+    __syncthreads();
+    uint32_t excl = carry + sh[warp] + x - v;
+    __syncthreads();
+    if (idx < n_ptiles) tile_cnt[idx] = excl;   // now the tile offsets
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int L = 1 << depth;
+  uint32_t run = 0;
+  for (int i = 0; i < L; ++i) {
+    const int l = cur->order[i];
+    cur->ones_before[l] = run;
+    run += __ldcg(&cur->ones[l]);
+  }
+  int units = 0;
+  for (int i = 0; i < L; ++i) {
+    const int l = cur->order[i];
+    const int s = cur->start[l], c = cur->cnt[l];
+    const int c1 = static_cast<int>(__ldcg(&cur->ones[l]));
+    const int c0 = c - c1;
+    nxt->start[l] = s;
+    nxt->cnt[l] = c0;
+    nxt->start[l + L] = s + c0;
+    nxt->cnt[l + L] = c1;
+    nxt->order[2 * i] = l;
+    nxt->order[2 * i + 1] = l + L;
+    nxt->ones[l] = 0;
+    nxt->ones[l + L] = 0;
+  }
+  // pair p = children p and p + L of parent p
+  unsigned long long rows = 0;
+  for (int p = 0; p < L; ++p) {
+    const int a = p, b = p + L;
+    const int small = nxt->cnt[a] <= nxt->cnt[b] ? a : b;
+    const int large = small == a ? b : a;
+    const int m = nxt->cnt[small];
+    const int per_unit = rows_per_item * cs;
+    int chunks = (m + per_unit - 1) / per_unit;
+    if (chunks < 1) chunks = 1;
+    plan->small_leaf[p] = small;
+    plan->large_leaf[p] = large;
+    plan->parent[p] = p;
+    plan->unit_begin[p] = units;
+    plan->chunk_rows[p] = m > 0 ? (m + chunks * cs - 1) / (chunks * cs) : 1;
+    plan->seg_start[p] = nxt->start[small];
+    plan->seg_cnt[p] = m;
+    units += chunks;
+    rows += static_cast<unsigned long long>(m);
+  }
+  *rows_hist += rows;
+  plan->unit_begin[L] = units;
+  plan->n_small = L;
+  plan->total_units = units;
+  plan->level_leaves = 2 * L;
+}
+
+// A: per position (8 consecutive positions per thread), the split bit of its row; leaf +=
+// 2^d * bit. Unless this is the last level: ones per tile and per leaf (run-length counted
+// in shared memory, since positions are grouped by leaf), and the last block to finish
+// plans the next level.
+__global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_t* __restrict__ bins_t, int64_t n,
+                                  const uint32_t* __restrict__ order, const cbg_split* __restrict__ splits, int depth,
+                                  uint16_t* __restrict__ leaf, uint8_t* __restrict__ flags,
+                                  uint32_t* __restrict__ tile_cnt, Segs* seg, int write_flags, int64_t n_ptiles,
+                                  Segs* __restrict__ nxt, Plan* __restrict__ plan, int rows_per_item, int cs,
+                                  unsigned long long* __restrict__ rows_hist, Misc* misc) {
+  __shared__ uint32_t wsum[PT_THREADS / 32];
+  __shared__ uint32_t sh_ones[1 << MAX_DEPTH];
+  __shared__ bool is_last;
+  const int L = 1 << depth;
+  if (write_flags) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) sh_ones[i] = 0;
+    __syncthreads();
+  }
+  const int f = splits[depth].feature, k = splits[depth].border;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
+  uint32_t cnt = 0, run = 0;
+  int cur = -1;
+#pragma unroll
+  for (int i = 0; i < PT / PT_THREADS; ++i) {
+    const int64_t pos = base + i;
+    if (pos < n) {
+      const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
+      const int bit = split_bit(bins, bins_t, n, row, f, k);
+      const int lf = leaf[row] & (L - 1);
+      if (bit) leaf[row] = static_cast<uint16_t>(lf + L);
+      if (write_flags) {
+        flags[pos] = static_cast<uint8_t>(bit);
+        if (lf != cur) {
+          if (run) atomicAdd(&sh_ones[cur], run);
+          cur = lf;
+          run = 0;
+        }
+        run += bit;
+        cnt += bit;
+      }
+    }
+  }
+  if (!write_flags) return;
+  if (run) atomicAdd(&sh_ones[cur], run);
+  const int lane = threadIdx.x & 31;
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if (lane == 0) wsum[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int w = 0; w < PT_THREADS / 32; ++w) s += wsum[w];
+    tile_cnt[blockIdx.x] = s;
+  }
+  for (int i = threadIdx.x; i < L; i += blockDim.x)
+    if (sh_ones[i]) atomicAdd(&seg->ones[i], sh_ones[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(&misc->done_part, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  plan_next_level(tile_cnt, n_ptiles, seg, nxt, plan, depth, rows_per_item, cs, rows_hist);
+  if (threadIdx.x == 0) misc->done_part = 0;
+}
+
+// C: stable partition of every segment: the row at position i moves to
+// start + (zeros before it) or start + zeros + (ones before it).
+__global__ void part_scatter_kernel(const uint32_t* __restrict__ order, const uint8_t* __restrict__ flags, int64_t n,
+                                    const uint32_t* __restrict__ tile_off, const uint16_t* __restrict__ leaf,
+                                    const Segs* __restrict__ cur, int depth, uint32_t* __restrict__ order_out) {
+  __shared__ uint32_t sh[PT_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
+  uint8_t fl[PT / PT_THREADS];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < PT / PT_THREADS; ++i) {
+    fl[i] = (base + i < n) ? flags[base + i] : 0;
+    s += fl[i];
+  }
+  uint32_t x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < PT_THREADS / 32; ++w) {
+      uint32_t t = sh[w];
+      sh[w] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  uint32_t ones_before = tile_off[blockIdx.x] + sh[warp] + x - s;
+  const int mask = (1 << depth) - 1;
+#pragma unroll
+  for (int i = 0; i < PT / PT_THREADS; ++i) {
+    const int64_t pos = base + i;
+    if (pos < n) {
+      const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
+      const int l = leaf[row] & mask;
+      const int start = cur->start[l];
+      const uint32_t ob = ones_before - cur->ones_before[l];       // ones of leaf l before pos
+      const int zeros_total = cur->cnt[l] - static_cast<int>(cur->ones[l]);
+      int dst;
+      if (fl[i])
+        dst = start + zeros_total + static_cast<int>(ob);
+      else
+        dst = start + static_cast<int>(pos - start) - static_cast<int>(ob);
+      if (dst >= 0 && dst < n) order_out[dst] = row;
+    }
+    ones_before += fl[i];
+  }
+}
+
+// ------------------------------------------------------------------- apply
+template <typename GH>
+__global__ void apply_kernel(const uint8_t* __restrict__ bins, int64_t n, int groups, const cbg_split* __restrict__ splits,
+                             int depth, const double* __restrict__ leaf_totals, const double* __restrict__ values_in,
+                             double l2, double lr, const uint16_t* __restrict__ leaf_in, uint16_t* __restrict__ leaf_out,
+                             float* __restrict__ pred, double* __restrict__ values_out, const float* __restrict__ y,
+                             int loss, GH* __restrict__ g, GH* __restrict__ h) {
+  __shared__ float lrv[1 << MAX_DEPTH];
+  __shared__ int sf[MAX_DEPTH], sk[MAX_DEPTH];
+  const int L = 1 << depth;
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    double v;
+    if (leaf_totals) {
+      const double den = leaf_totals[2 * l + 1] + l2;
+      v = den == 0.0 ? 0.0 : -leaf_totals[2 * l] / den;
+    } else {
+      v = values_in[l];
+    }
+    lrv[l] = static_cast<float>(lr * v);
+    if (values_out && blockIdx.x == 0) values_out[l] = v;
+  }
+  if (threadIdx.x < depth) {
+    sf[threadIdx.x] = splits[threadIdx.x].feature;
+    sk[threadIdx.x] = splits[threadIdx.x].border;
+  }
+  __syncthreads();
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int l;
+    if (leaf_in) {
+      l = leaf_in[r] & (L - 1);
+    } else {
+      l = 0;
+      for (int i = 0; i < depth; ++i) {
+        const int f = sf[i];
+        if (f >= 0 && (f >> 5) < groups && bins[(static_cast<int64_t>(f >> 5) * n + r) * GROUP + (f & 31)] > sk[i])
+          l += 1 << i;
+      }
+    }
+    if (leaf_out) leaf_out[r] = static_cast<uint16_t>(l);
+    const float p = pred[r] + lrv[l];
+    pred[r] = p;
+    if (g) {
+      const float yi = y[r];
+      float gi, hi;
+      if (loss == CBG_LOSS_RMSE) {
+        gi = p - yi;
+        hi = 1.0f;
+      } else {
+        const float s = 1.0f / (1.0f + expf(-p));
+        gi = s - yi;
+        hi = s * (1.0f - s);
+      }
+      cbgd::store_gh(g, r, gi);
+      cbgd::store_gh(h, r, hi);
+    }
+  }
+}
+
+// ------------------------------------------------------------- host helpers
+// Copies one tree's splits and leaf values from the graph's fixed scratch to tree slot t of
+// the model (t read from, then advanced in, a device counter), so one captured tree can be
+// replayed for every tree of the run.
+__global__ void record_tree_kernel(const cbg_split* __restrict__ sp_tmp, const double* __restrict__ v_tmp, int depth,
+                                   cbg_split* __restrict__ splits, double* __restrict__ values,
+                                   unsigned* __restrict__ counter, int trees) {
+  __shared__ unsigned t;
+  if (threadIdx.x == 0) t = *counter;
+  __syncthreads();
+  if (t < static_cast<unsigned>(trees)) {
+    const int L = 1 << depth;
+    for (int i = threadIdx.x; i < depth; i += blockDim.x) splits[static_cast<int64_t>(t) * depth + i] = sp_tmp[i];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) values[static_cast<int64_t>(t) * L + i] = v_tmp[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = t + 1;
+}
+
+cbg_status check_state(cbg_ctx* ctx, const Layout& L, void* state, size_t bytes) {
+  CBG_REQUIRE(ctx, state != nullptr, "state is NULL");
+  CBG_REQUIRE(ctx, reinterpret_cast<uintptr_t>(state) % 256 == 0, "state must be 256-byte aligned");
+  if (bytes < L.total) return fail(ctx, CBG_ENOMEM, "tree state of %zu bytes is smaller than the %zu needed", bytes, L.total);
+  return CBG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cbg_status cbg_gradients(cbg_ctx* ctx, int loss, const float* y, const float* pred, int64_t n, int gh_dtype,
+                         void* g, void* h) {
+  if (!ctx) return CBG_EINVAL;
+  CBG_REQUIRE(ctx, n >= 1 && n <= INT32_MAX, "n must be in [1, 2^31-1]");
+  CBG_REQUIRE(ctx, loss == CBG_LOSS_RMSE || loss == CBG_LOSS_LOGLOSS, "bad loss");
+  CBG_REQUIRE(ctx, gh_dtype == CBG_F32 || gh_dtype == CBG_BF16, "bad gh_dtype");
+  CBG_REQUIRE(ctx, y && pred && g && h, "NULL argument");
+  DeviceGuard guard(ctx->device);
+  const unsigned grid = grid_stride_blocks(n, 256);
+  if (gh_dtype == CBG_F32)
+    gradients_kernel<float><<<grid, 256, 0, ctx->stream>>>(loss, y, pred, n, static_cast<float*>(g), static_cast<float*>(h));
+  else
+    gradients_kernel<__nv_bfloat16><<<grid, 256, 0, ctx->stream>>>(loss, y, pred, n, static_cast<__nv_bfloat16*>(g),
+                                                                   static_cast<__nv_bfloat16*>(h));
+  CBG_CHECK_LAUNCH(ctx);
+  return CBG_OK;
+}
+
+cbg_status cbg_tree_state_bytes(const cbg_tree_shape* shape, size_t* bytes) {
+  if (!bytes) return CBG_EINVAL;
+  Layout L;
+  cbg_status st = make_layout(nullptr, shape, &L);
+  if (st != CBG_OK) return st;
+  *bytes = L.total;
+  return CBG_OK;
+}
+
+cbg_status cbg_tree_begin(cbg_ctx* ctx, const cbg_tree_shape* shape, void* state, size_t state_bytes, uint16_t* leaf) {
+  if (!ctx) return CBG_EINVAL;
+  Layout L;
+  cbg_status st = make_layout(ctx, shape, &L);
+  if (st != CBG_OK) return st;
+  st = check_state(ctx, L, state, state_bytes);
+  if (st != CBG_OK) return st;
+  CBG_REQUIRE(ctx, leaf != nullptr, "leaf is NULL");
+  DeviceGuard guard(ctx->device);
+  CBG_CUDA(ctx, cudaMemsetAsync(leaf, 0, L.n * sizeof(uint16_t), ctx->stream));
+  CBG_CUDA(ctx, cudaMemsetAsync(at<char>(state, L.o_seg_a), 0, sizeof(Segs), ctx->stream));
+  CBG_CUDA(ctx, cudaMemsetAsync(at<char>(state, L.o_misc), 0, sizeof(Misc), ctx->stream));
+  int cs = 1;
+  st = hist_cluster_size(ctx, hist_config(L), &cs);
+  if (st != CBG_OK) return st;
+  tree_begin_kernel<<<1, 32, 0, ctx->stream>>>(at<Plan>(state, L.o_plan), at<Segs>(state, L.o_seg_a),
+                                               static_cast<int>(L.n), L.rows_per_item, cs,
+                                               at<unsigned long long>(state, L.o_count));
+  CBG_CHECK_LAUNCH(ctx);
+  return CBG_OK;
+}
+
+cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
+  if (!ctx) return CBG_EINVAL;
+  CBG_REQUIRE(ctx, a != nullptr, "args is NULL");
+  Layout L;
+  cbg_status st = make_layout(ctx, a->shape, &L);
+  if (st != CBG_OK) return st;
+  st = check_state(ctx, L, a->state, a->state_bytes);
+  if (st != CBG_OK) return st;
+  const int d = a->depth;
+  CBG_REQUIRE(ctx, d >= 0 && d < L.D, "depth %d outside [0, max_depth)", d);
+  CBG_REQUIRE(ctx, a->bins && a->n_borders && a->g && a->h && a->leaf && a->splits && a->child_totals, "NULL argument");
+  CBG_REQUIRE(ctx, a->gh_dtype == CBG_F32 || a->gh_dtype == CBG_BF16, "bad gh_dtype");
+  CBG_REQUIRE(ctx, a->l2 >= 0.0 && std::isfinite(a->l2), "l2 must be finite and >= 0");
+  CBG_REQUIRE(ctx, a->force_feature < L.F, "force_feature out of range");
+  CBG_REQUIRE(ctx, a->force_feature < 0 || (a->force_border >= 0 && a->force_border < L.max_bins - 1),
+              "force_border out of range");
+  DeviceGuard guard(ctx->device);
+  void* S = a->state;
+  Plan* plan = at<Plan>(S, L.o_plan);
+  Segs* seg_cur = at<Segs>(S, d % 2 == 0 ? L.o_seg_a : L.o_seg_b);
+  Segs* seg_nxt = at<Segs>(S, d % 2 == 0 ? L.o_seg_b : L.o_seg_a);
+  const uint32_t* order_cur = d == 0 ? nullptr : at<uint32_t>(S, d % 2 == 1 ? L.o_order_a : L.o_order_b);
+  uint32_t* order_nxt = at<uint32_t>(S, (d + 1) % 2 == 1 ? L.o_order_a : L.o_order_b);
+  double* hist_cur = at<double>(S, d % 2 == 0 ? L.o_hist_a : L.o_hist_b);
+  const double* hist_prev = at<double>(S, d % 2 == 0 ? L.o_hist_b : L.o_hist_a);
+  float* partials = at<float>(S, L.o_part);
+  float* term = at<float>(S, L.o_term);
+  double* tot_nxt = at<double>(S, d % 2 == 0 ? L.o_tot_b : L.o_tot_a);
+  BestF* best = at<BestF>(S, L.o_best);
+  Misc* misc = at<Misc>(S, L.o_misc);
+  uint8_t* flags = at<uint8_t>(S, L.o_flags);
+  uint32_t* tcnt = at<uint32_t>(S, L.o_tcnt);
+
+  // 1. histogram of the directly computed leaves
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  CBG_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &capturing));
+  if (capturing == cudaStreamCaptureStatusNone) st = prof_begin(ctx, &ev0, &ev1);
+  if (st != CBG_OK) return st;
+  st = a->gh_dtype == CBG_F32 ? launch_hist<float>(ctx, hist_config(L), a->bins, order_cur, a->g, a->h, plan, partials)
+                              : launch_hist<__nv_bfloat16>(ctx, hist_config(L), a->bins, order_cur, a->g, a->h, plan, partials);
+  if (st != CBG_OK) return st;
+  st = prof_end(ctx, ev1);
+  if (st != CBG_OK) return st;
+  // 2. FP64 reduction of the partials + sibling subtraction
+  {
+    const int per_leaf = L.G * 2 * L.max_bins * GROUP;
+    dim3 grid(static_cast<unsigned>(ceil_div(per_leaf, 256)), static_cast<unsigned>(d == 0 ? 1 : (1 << (d - 1))));
+    reduce_kernel<<<grid, 256, 0, ctx->stream>>>(plan, partials, L.G, L.F, L.max_bins, hist_prev, hist_cur,
+                                                 a->splits, d);
+    CBG_CHECK_LAUNCH(ctx);
+  }
+  // 3. split scores and argmax
+  const int level_leaves = 1 << d;
+  {
+    const int64_t threads = static_cast<int64_t>(level_leaves) * L.F;
+    leaf_terms_kernel<<<static_cast<unsigned>(ceil_div(threads * 32, 256)), 256, 0, ctx->stream>>>(
+        hist_cur, level_leaves, L.F, L.max_bins, a->n_borders, a->l2, term);
+    CBG_CHECK_LAUNCH(ctx);
+    argmax_kernel<<<L.F, 256, 0, ctx->stream>>>(term, level_leaves, L.F, L.max_bins, a->n_borders, best, misc,
+                                                a->force_feature, a->force_border, d, a->splits);
+    CBG_CHECK_LAUNCH(ctx);
+    child_totals_kernel<<<static_cast<unsigned>(ceil_div(static_cast<int64_t>(level_leaves) * 32, 256)), 256, 0,
+                          ctx->stream>>>(hist_cur, level_leaves, L.F, L.max_bins, a->splits, d, a->child_totals,
+                                         tot_nxt);
+    CBG_CHECK_LAUNCH(ctx);
+  }
+  if (a->hist_out)
+    CBG_CUDA(ctx, cudaMemcpyAsync(a->hist_out, hist_cur,
+                                  static_cast<size_t>(level_leaves) * L.F * L.max_bins * 2 * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  // 4. leaf update and (unless this is the last level) the row partition of the next level
+  const bool last = a->last_level || d == L.D - 1;
+  int cs = 1;
+  if (!last) {
+    st = hist_cluster_size(ctx, hist_config(L), &cs);
+    if (st != CBG_OK) return st;
+  }
+  part_flags_kernel<<<static_cast<unsigned>(L.n_ptiles), PT_THREADS, 0, ctx->stream>>>(
+      a->bins, a->bins_t, L.n, order_cur, a->splits, d, a->leaf, flags, tcnt, seg_cur, last ? 0 : 1, L.n_ptiles,
+      seg_nxt, plan, L.rows_per_item, cs, at<unsigned long long>(S, L.o_count), misc);
+  CBG_CHECK_LAUNCH(ctx);
+  if (!last) {
+    part_scatter_kernel<<<static_cast<unsigned>(L.n_ptiles), PT_THREADS, 0, ctx->stream>>>(
+        order_cur, flags, L.n, tcnt, a->leaf, seg_cur, d, order_nxt);
+    CBG_CHECK_LAUNCH(ctx);
+  }
+  return CBG_OK;
+}
+
+cbg_status cbg_tree_rows_histogrammed(cbg_ctx* ctx, const cbg_tree_shape* shape, void* state, int reset,
+                                      int64_t* rows) {
+  if (!ctx) return CBG_EINVAL;
+  Layout L;
+  cbg_status st = make_layout(ctx, shape, &L);
+  if (st != CBG_OK) return st;
+  CBG_REQUIRE(ctx, state != nullptr && rows != nullptr, "NULL argument");
+  DeviceGuard guard(ctx->device);
+  unsigned long long v = 0;
+  CBG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  CBG_CUDA(ctx, cudaMemcpy(&v, at<char>(state, L.o_count), sizeof(v), cudaMemcpyDeviceToHost));
+  *rows = static_cast<int64_t>(v);
+  if (reset) CBG_CUDA(ctx, cudaMemset(at<char>(state, L.o_count), 0, sizeof(v)));
+  return CBG_OK;
+}
+
+cbg_status cbg_apply_tree(cbg_ctx* ctx, const cbg_apply_args* a) {
+  if (!ctx) return CBG_EINVAL;
+  CBG_REQUIRE(ctx, a != nullptr, "args is NULL");
+  CBG_REQUIRE(ctx, a->n >= 1 && a->n <= INT32_MAX, "n must be in [1, 2^31-1]");
+  CBG_REQUIRE(ctx, a->depth >= 1 && a->depth <= MAX_DEPTH, "depth must be in [1, 10]");
+  CBG_REQUIRE(ctx, a->pred != nullptr, "pred is NULL");
+  CBG_REQUIRE(ctx, a->leaf_totals || a->leaf_values_in, "need leaf_totals or leaf_values_in");
+  CBG_REQUIRE(ctx, a->leaf_in || (a->bins && a->splits), "need leaf_in or bins + splits");
+  CBG_REQUIRE(ctx, a->leaf_in || (a->F_pad >= 32 && a->F_pad % 32 == 0), "F_pad must be a multiple of 32");
+  CBG_REQUIRE(ctx, a->l2 >= 0.0, "l2 must be >= 0");
+  const bool grads = a->g != nullptr;
+  CBG_REQUIRE(ctx, !grads || (a->h && a->y), "fused gradients need y, g and h");
+  CBG_REQUIRE(ctx, !grads || a->loss == CBG_LOSS_RMSE || a->loss == CBG_LOSS_LOGLOSS, "bad loss");
+  CBG_REQUIRE(ctx, !grads || a->gh_dtype == CBG_F32 || a->gh_dtype == CBG_BF16, "bad gh_dtype");
+  DeviceGuard guard(ctx->device);
+  const unsigned grid = grid_stride_blocks(a->n, 256);
+  if (!grads || a->gh_dtype == CBG_F32)
+    apply_kernel<float><<<grid, 256, 0, ctx->stream>>>(a->bins, a->n, a->F_pad / GROUP, a->splits, a->depth, a->leaf_totals,
+                                                       a->leaf_values_in, a->l2, a->lr, a->leaf_in, a->leaf_out,
+                                                       a->pred, a->leaf_values_out, a->y, a->loss,
+                                                       static_cast<float*>(a->g), static_cast<float*>(a->h));
+  else
+    apply_kernel<__nv_bfloat16><<<grid, 256, 0, ctx->stream>>>(
+        a->bins, a->n, a->F_pad / GROUP, a->splits, a->depth, a->leaf_totals, a->leaf_values_in, a->l2, a->lr, a->leaf_in,
+        a->leaf_out, a->pred, a->leaf_values_out, a->y, a->loss, static_cast<__nv_bfloat16*>(a->g),
+        static_cast<__nv_bfloat16*>(a->h));
+  CBG_CHECK_LAUNCH(ctx);
+  return CBG_OK;
+}
+
+namespace {
+
+// One boosting iteration: tree_begin, D levels, leaf values + prediction update + next
+// gradients. Splits go to sp, leaf values to vals.
+cbg_status boost_one_tree(cbg_ctx* ctx, const cbg_boost_args* a, cbg_split* sp, double* vals) {
+  const int D = a->depth;
+  cbg_status st = cbg_tree_begin(ctx, a->shape, a->state, a->state_bytes, a->leaf);
+  if (st != CBG_OK) return st;
+  for (int d = 0; d < D; ++d) {
+    cbg_level_args la{};
+    la.shape = a->shape;
+    la.state = a->state;
+    la.state_bytes = a->state_bytes;
+    la.bins = a->bins;
+    la.bins_t = a->bins_t;
+    la.n_borders = a->n_borders;
+    la.g = a->g;
+    la.h = a->h;
+    la.gh_dtype = a->gh_dtype;
+    la.depth = d;
+    la.l2 = a->l2;
+    la.force_feature = -1;
+    la.force_border = -1;
+    la.leaf = a->leaf;
+    la.splits = sp;
+    la.child_totals = a->child_totals;
+    la.hist_out = nullptr;
+    la.last_level = d == D - 1;
+    st = cbg_build_level(ctx, &la);
+    if (st != CBG_OK) return st;
+  }
+  cbg_apply_args aa{};
+  aa.bins = a->bins;
+  aa.n = a->shape->n;
+  aa.F_pad = a->shape->F_pad;
+  aa.splits = sp;
+  aa.depth = D;
+  aa.leaf_totals = a->child_totals;
+  aa.l2 = a->l2;
+  aa.lr = a->lr;
+  aa.leaf_in = a->leaf;
+  aa.pred = a->pred;
+  aa.leaf_values_out = vals;
+  aa.y = a->y;
+  aa.loss = a->loss;
+  aa.gh_dtype = a->gh_dtype;
+  aa.g = a->g;
+  aa.h = a->h;
+  return cbg_apply_tree(ctx, &aa);
+}
+
+}  // namespace
+
+cbg_status cbg_boost(cbg_ctx* ctx, const cbg_boost_args* a) {
+  if (!ctx) return CBG_EINVAL;
+  CBG_REQUIRE(ctx, a != nullptr && a->shape != nullptr, "args is NULL");
+  CBG_REQUIRE(ctx, a->depth >= 1 && a->depth <= a->shape->max_depth, "depth outside [1, max_depth]");
+  CBG_REQUIRE(ctx, a->trees >= 0, "trees must be >= 0");
+  CBG_REQUIRE(ctx, a->pred && a->y && a->g && a->h && a->leaf && a->splits && a->leaf_values && a->child_totals,
+              "NULL argument");
+  DeviceGuard guard(ctx->device);
+  const int D = a->depth;
+  const int64_t n = a->shape->n;
+  cbg_status st = cbg_gradients(ctx, a->loss, a->y, a->pred, n, a->gh_dtype, a->g, a->h);
+  if (st != CBG_OK) return st;
+  if (!a->use_graph || a->trees <= 1) {
+    for (int t = 0; t < a->trees; ++t) {
+      st = boost_one_tree(ctx, a, a->splits + static_cast<int64_t>(t) * D,
+                          a->leaf_values + static_cast<int64_t>(t) * (1 << D));
+      if (st != CBG_OK) return st;
+    }
+    return CBG_OK;
+  }
+  // Graph replay: capture one tree (outputs to fixed scratch + a record kernel) and launch
+  // it once per tree. Launch-geometry queries are made before the capture begins.
+  Layout L;
+  st = make_layout(ctx, a->shape, &L);
+  if (st != CBG_OK) return st;
+  st = check_state(ctx, L, a->state, a->state_bytes);
+  if (st != CBG_OK) return st;
+  HistGeom geom;
+  st = a->gh_dtype == CBG_F32 ? hist_geom<float>(ctx, hist_config(L), &geom) : hist_geom<__nv_bfloat16>(ctx, hist_config(L), &geom);
+  if (st != CBG_OK) return st;
+  int cs = 1;
+  st = hist_cluster_size(ctx, hist_config(L), &cs);
+  if (st != CBG_OK) return st;
+  cbg_split* sp_tmp = at<cbg_split>(a->state, L.o_gsplit);
+  double* v_tmp = at<double>(a->state, L.o_gvals);
+  unsigned* counter = reinterpret_cast<unsigned*>(at<char>(a->state, L.o_gsplit) + sizeof(cbg_split) * MAX_DEPTH);
+  CBG_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned), ctx->stream));
+  // The caller's stream may be the legacy default stream, which cannot be captured: the
+  // tree is captured on a library-owned stream and the graph is launched on the caller's.
+  if (!ctx->capture_stream) CBG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+  cudaStream_t user_stream = ctx->stream;
+  ctx->stream = ctx->capture_stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) {
+    ctx->stream = user_stream;
+    return fail(ctx, CBG_ECUDA, "cudaStreamBeginCapture failed: %s", cudaGetErrorString(ce));
+  }
+  st = boost_one_tree(ctx, a, sp_tmp, v_tmp);
+  if (st == CBG_OK) {
+    record_tree_kernel<<<1, 256, 0, ctx->stream>>>(sp_tmp, v_tmp, D, a->splits, a->leaf_values, counter, a->trees);
+    if (cudaGetLastError() != cudaSuccess) st = fail(ctx, CBG_ECUDA, "record kernel launch failed during capture");
+  }
+  ce = cudaStreamEndCapture(ctx->stream, &graph);
+  ctx->stream = user_stream;
+  if (st != CBG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ce != cudaSuccess) return fail(ctx, CBG_ECUDA, "stream capture of a tree failed: %s", cudaGetErrorString(ce));
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return fail(ctx, CBG_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+  for (int t = 0; t < a->trees; ++t) {
+    ce = cudaGraphLaunch(exec, ctx->stream);
+    if (ce != cudaSuccess) break;
+  }
+  cudaGraphExecDestroy(exec);   // freed once the queued launches complete
+  if (ce != cudaSuccess) return fail(ctx, CBG_ECUDA, "graph launch failed: %s", cudaGetErrorString(ce));
+  return CBG_OK;
+}
+
+}  // extern "C"

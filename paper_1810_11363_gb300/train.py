@@ -1,0 +1,142 @@
+"""Training driver: sequences the library's C-ABI calls over torch-owned device memory.
+
+preprocess(): permutation sigma, prior, ordered target statistics (Section 2, Eq. 1),
+quantile borders and uint8 quantisation of float and TS columns (Section 4).
+fit(): classic boosting of oblivious trees through cbg_boost (Sections 3-4).
+All arithmetic runs in libcbg's kernels; this module only allocates and marshals.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import cbg
+
+SPLIT_DTYPE = np.dtype([("feature", "<i4"), ("border", "<i4"), ("score", "<f8")])
+
+
+def f_pad_for(F: int) -> int:
+    return max(32, (F + 31) // 32 * 32)
+
+
+def decode_splits(t) -> np.ndarray:
+    """cbg_split records held in a float64 tensor [..., 2] -> numpy structured array."""
+    raw = t.detach().cpu().contiguous().numpy()
+    return raw.view(SPLIT_DTYPE).reshape(raw.shape[:-1])
+
+
+@dataclass
+class Prepared:
+    n: int
+    F: int
+    F_float: int
+    F_pad: int
+    perm: object
+    prior: float
+    ts: object
+    borders: object
+    n_borders: object
+    bins: object
+    bins_t: object
+    max_bins: int
+
+
+def preprocess(ctx: cbg.Context, x, cat, y, label_kind: str, max_borders: int, a: float = 1.0,
+               seed: int = 0, prior: float | None = None, with_bins_t: bool = True) -> Prepared:
+    """x: float32 [F_float][n], cat: int32/uint32 bits [C][n], y: float32 [n], all on ctx's device."""
+    import torch
+    dev = y.device
+    n = int(y.numel())
+    Ff = int(x.shape[0])
+    Cc = int(cat.shape[0]) if cat is not None else 0
+    F = Ff + Cc
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    cbg.cbg_make_permutation(ctx, seed, n, perm)
+    if prior is None:
+        pr = torch.empty(1, dtype=torch.float64, device=dev)
+        cbg.cbg_prior(ctx, y, n, label_kind, pr)
+        cbg.cbg_sync(ctx)
+        prior = float(pr.item())
+    ts = torch.empty((Cc, n), dtype=torch.float32, device=dev)
+    if Cc:
+        cbg.cbg_ordered_ts(ctx, cat, y, n, Cc, perm, prior, a, label_kind, ts)
+    borders = torch.empty((F, max_borders), dtype=torch.float32, device=dev)
+    nb = torch.empty(F, dtype=torch.int32, device=dev)
+    if Ff:
+        cbg.cbg_select_borders(ctx, x, n, Ff, max_borders, borders[:Ff], nb[:Ff])
+    if Cc:
+        cbg.cbg_select_borders(ctx, ts, n, Cc, max_borders, borders[Ff:], nb[Ff:])
+    F_pad = f_pad_for(F)
+    bins = torch.zeros(F_pad * n, dtype=torch.uint8, device=dev)
+    bins_t = torch.empty((F, n), dtype=torch.uint8, device=dev) if with_bins_t else None
+    if Ff:
+        cbg.cbg_quantize(ctx, x, n, Ff, borders[:Ff], nb[:Ff], max_borders, bins, F_pad, 0, bins_t)
+    if Cc:
+        cbg.cbg_quantize(ctx, ts, n, Cc, borders[Ff:], nb[Ff:], max_borders, bins, F_pad, Ff, bins_t)
+    cbg.cbg_sync(ctx)
+    max_bins = int(nb.max().item()) + 1
+    return Prepared(n, F, Ff, F_pad, perm, prior, ts, borders, nb, bins, bins_t, max_bins)
+
+
+@dataclass
+class Model:
+    splits: object        # float64 tensor [T][D][2] holding cbg_split records
+    leaf_values: object   # float64 [T][2^D], Newton values before the learning rate
+    pred: object          # float32 [n] training predictions
+    depth: int
+    lr: float
+
+    def host_splits(self) -> np.ndarray:
+        return decode_splits(self.splits)
+
+
+@dataclass
+class FitBuffers:
+    shape: object
+    state: object
+    pred: object
+    g: object
+    h: object
+    leaf: object
+    splits: object
+    leaf_values: object
+    child_totals: object
+
+
+def alloc_fit(prep: Prepared, depth: int, trees: int, gh_dtype: str = "f32", tiles: dict | None = None,
+              max_depth: int | None = None) -> FitBuffers:
+    import torch
+    dev = prep.bins.device
+    shape = cbg.make_shape(prep.n, prep.F, prep.F_pad, prep.max_bins, max_depth or depth, tiles)
+    state = torch.empty(cbg.cbg_tree_state_bytes(shape), dtype=torch.uint8, device=dev)
+    tdt = torch.float32 if gh_dtype == "f32" else torch.bfloat16
+    return FitBuffers(
+        shape=shape, state=state,
+        pred=torch.zeros(prep.n, dtype=torch.float32, device=dev),
+        g=torch.empty(prep.n, dtype=tdt, device=dev), h=torch.empty(prep.n, dtype=tdt, device=dev),
+        leaf=torch.empty(prep.n, dtype=torch.int16, device=dev),
+        splits=torch.empty((max(trees, 1), depth, 2), dtype=torch.float64, device=dev),
+        leaf_values=torch.empty((max(trees, 1), 1 << depth), dtype=torch.float64, device=dev),
+        child_totals=torch.empty((1 << depth, 2), dtype=torch.float64, device=dev))
+
+
+def fit(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, trees: int, lr: float, l2: float,
+        gh_dtype: str = "f32", tiles: dict | None = None, bufs: FitBuffers | None = None,
+        use_graph: bool = False) -> Model:
+    if bufs is None:
+        bufs = alloc_fit(prep, depth, trees, gh_dtype, tiles)
+    cbg.cbg_boost(ctx, bufs.shape, bufs.state, prep.bins, prep.n_borders, y, loss, gh_dtype, depth, trees, lr,
+                  l2, bufs.pred, bufs.g, bufs.h, bufs.leaf, bufs.splits, bufs.leaf_values, bufs.child_totals,
+                  bins_t=prep.bins_t, use_graph=use_graph)
+    return Model(bufs.splits[:trees], bufs.leaf_values[:trees], bufs.pred, depth, lr)
+
+
+def grouped_from_rowmajor(bins_rm: np.ndarray) -> np.ndarray:
+    """[n][F_pad] row-major bins -> the library's grouped layout (flat uint8)."""
+    n, F_pad = bins_rm.shape
+    return np.ascontiguousarray(bins_rm.reshape(n, F_pad // 32, 32).transpose(1, 0, 2)).reshape(-1)
+
+
+def rowmajor_from_grouped(flat: np.ndarray, n: int, F_pad: int) -> np.ndarray:
+    return np.ascontiguousarray(flat.reshape(F_pad // 32, n, 32).transpose(1, 0, 2)).reshape(n, F_pad)

@@ -1,0 +1,282 @@
+"""GPU parity of the per-tree path against the oracle: gradients, per-level FP64
+histograms (FP32 shared-memory accumulation), split search, leaf index, child totals,
+leaf values and prediction update, and whole boosting runs.
+
+Tolerances: bins, leaf indices and splits exact; histograms |gpu - fp64| <= 1e-5 times
+the sum of |g| (|h|) of the bin's rows (bit-exact with integer gradients); splits
+compared wherever the oracle's best and runner-up differ by more than 1e-6 relative;
+predictions after all trees within 1e-4 absolute."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import hist_tolerance_ok, to_dev, to_host
+from paper_1810_11363_gb300 import cbg, synth, train
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = cbg.Context(0)
+    yield c
+    c.close()
+
+
+def _bf16(v):
+    import torch
+    return torch.from_numpy(np.asarray(v, np.float32)).to(torch.bfloat16).float().numpy()
+
+
+@pytest.mark.parametrize("loss", ["rmse", "logloss"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_gradients(ctx, loss, dtype):
+    import torch
+    rng = np.random.default_rng(1)
+    n = 10007
+    pred = (rng.normal(size=n) * 3).astype(np.float32)
+    y = ((rng.random(n) < 0.4) if loss == "logloss" else rng.normal(size=n)).astype(np.float32)
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    g = torch.empty(n, dtype=tdt, device="cuda")
+    h = torch.empty(n, dtype=tdt, device="cuda")
+    cbg.cbg_gradients(ctx, loss, to_dev(y), to_dev(pred), n, dtype, g, h)
+    cbg.cbg_sync(ctx)
+    g_ref, h_ref = oracle.gradients(loss, y, pred.astype(np.float64), dtype)
+    gg, hh = g.float().cpu().numpy(), h.float().cpu().numpy()
+    if loss == "rmse":
+        assert np.array_equal(gg, g_ref.astype(np.float32))
+        assert np.all(hh == 1.0)
+    else:
+        # p = 1/(1+exp(-pred)) in FP32 is good to a few ulp of p (<= 1), and g = p - y
+        # cancels, so the bound is absolute; BF16 storage adds one BF16 ulp (2^-7 relative).
+        abs_err = 4 * 2.0**-24
+        rel = 2.0**-7 if dtype == "bf16" else 0.0
+        assert np.all(np.abs(gg - g_ref) <= rel * np.abs(g_ref) + abs_err)
+        assert np.all(np.abs(hh - h_ref) <= rel * np.abs(h_ref) + abs_err)
+
+
+class Tree:
+    """Device buffers for driving cbg_build_level level by level."""
+
+    def __init__(self, ctx, bins_rm, nb, g, h, max_depth, dtype="f32", tiles=None, with_bins_t=True):
+        import torch
+        n, F_pad = bins_rm.shape
+        self.ctx, self.n, self.F, self.F_pad = ctx, n, nb.shape[0], F_pad
+        self.max_bins = int(nb.max()) + 1 if nb.size else 1
+        self.shape = cbg.make_shape(n, self.F, F_pad, self.max_bins, max_depth, tiles)
+        self.state = torch.empty(cbg.cbg_tree_state_bytes(self.shape), dtype=torch.uint8, device="cuda")
+        self.bins = to_dev(train.grouped_from_rowmajor(bins_rm))
+        self.bins_t = to_dev(np.ascontiguousarray(bins_rm[:, :self.F].T)) if with_bins_t else None
+        self.nb = to_dev(nb.astype(np.int32))
+        tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+        self.dtype = dtype
+        self.g = torch.from_numpy(np.asarray(g, np.float32)).to(tdt).cuda()
+        self.h = torch.from_numpy(np.asarray(h, np.float32)).to(tdt).cuda()
+        self.leaf = torch.empty(n, dtype=torch.int16, device="cuda")
+        self.splits = torch.empty((max_depth, 2), dtype=torch.float64, device="cuda")
+        self.child = torch.empty((1 << max_depth, 2), dtype=torch.float64, device="cuda")
+        self.D = max_depth
+        cbg.cbg_tree_begin(ctx, self.shape, self.state, self.leaf)
+
+    def level(self, d, l2, force=None, last=False):
+        import torch
+        hist = torch.empty(((1 << d), self.F, self.max_bins, 2), dtype=torch.float64, device="cuda")
+        cbg.cbg_build_level(self.ctx, self.shape, self.state, self.bins, self.nb, self.g, self.h, self.dtype, d, l2,
+                            self.leaf, self.splits, self.child, bins_t=self.bins_t, force=force, hist_out=hist,
+                            last_level=last)
+        cbg.cbg_sync(self.ctx)
+        sp = train.decode_splits(self.splits)[d]
+        return to_host(hist), int(sp["feature"]), int(sp["border"]), float(sp["score"]), \
+            to_host(self.leaf, np.uint16).copy(), to_host(self.child)[: 2 << d].copy()
+
+
+LEVEL_CASES = [
+    # n, F, F_pad, max_bins, depth, integer_grads, dtype, bins_t
+    (5003, 40, 64, 255, 6, True, "f32", True),
+    (5003, 40, 64, 255, 6, False, "f32", False),
+    (777, 1, 32, 2, 3, False, "f32", True),
+    (20000, 70, 96, 129, 6, False, "bf16", True),
+    (3001, 33, 64, 33, 10, True, "f32", True),
+    (50000, 20, 32, 17, 4, False, "f32", True),
+    (1, 3, 32, 5, 2, False, "f32", True),
+]
+
+
+@pytest.mark.parametrize("case", LEVEL_CASES)
+def test_forced_levels_match_oracle(ctx, case):
+    n, F, F_pad, max_bins, depth, intg, dtype, bt = case
+    bins, nb, g, h, forced = synth.random_level_case(n + F, n, F, F_pad, max_bins, depth, integer_grads=intg,
+                                                     const_features=(F - 1,) if F > 2 else ())
+    if dtype == "bf16":
+        g, h = _bf16(g), _bf16(h)
+    t = Tree(ctx, bins, nb, g, h, depth, dtype, with_bins_t=bt)
+    g64, h64 = g.astype(np.float64), h.astype(np.float64)
+    leaf = np.zeros(n, np.uint16)
+    mb = t.max_bins
+    root_abs = None
+    for d in range(depth):
+        f, k = forced[d]
+        hist, sf, sk, ss, gl, child = t.level(d, 3.0, force=(f, k), last=(d == depth - 1))
+        ref = oracle.histogram(bins, F, g64, h64, leaf, 1 << d, mb)
+        ref_abs = oracle.histogram(bins, F, np.abs(g64), np.abs(h64), leaf, 1 << d, mb)
+        if root_abs is None:
+            root_abs = ref_abs[0]
+        # One sibling of every pair is parent - other sibling, recursively up to the root,
+        # so its rounding error is bounded by the root's rows of the bin (sum of |g|).
+        bound = np.maximum(ref_abs, root_abs[None])
+        if intg:
+            assert np.array_equal(hist, ref), d
+        else:
+            err = np.abs(hist - ref) - 1e-5 * bound
+            worst = np.unravel_index(np.argmax(err), err.shape)
+            assert hist_tolerance_ok(hist, ref, bound), (d, worst, hist[worst], ref[worst], ref_abs[worst],
+                                                         root_abs[worst[1:]])
+        scores, *_ = oracle.split_scores(ref, nb, 3.0)
+        assert (sf, sk) == (f, k)
+        # the score is derived from FP32-accumulated histograms: a loose check only
+        assert ss == pytest.approx(scores[f, k], rel=1e-4)
+        leaf = oracle.update_leaf(bins, f, k, d, leaf)
+        assert np.array_equal(gl, leaf), d
+        tot = oracle.leaf_totals(g64, h64, leaf, 2 << d)
+        tot_abs = oracle.leaf_totals(np.abs(g64), np.abs(h64), leaf, 2 << d)
+        assert np.all(np.abs(child - tot) <= 1e-5 * tot_abs + 1e-12), d
+
+
+@pytest.mark.parametrize("seed,n,F,max_bins,depth", [(0, 20000, 24, 65, 6), (1, 4000, 10, 255, 8),
+                                                     (2, 100000, 50, 255, 6)])
+def test_split_search_matches_oracle(ctx, seed, n, F, max_bins, depth):
+    bins, nb, g, h, _ = synth.random_level_case(seed, n, F, ((F + 31) // 32) * 32, max_bins, depth)
+    # make the gradients depend on a few features so that splits are well separated
+    g = (g * 0.5 + (bins[:, 1] > nb[1] // 2) * 1.5 - (bins[:, 3] > nb[3] // 3) * 0.8).astype(np.float32)
+    t = Tree(ctx, bins, nb, g, h, depth)
+    leaf = np.zeros(n, np.uint16)
+    g64, h64 = g.astype(np.float64), h.astype(np.float64)
+    compared = 0
+    for d in range(depth):
+        ref = oracle.histogram(bins, F, g64, h64, leaf, 1 << d, t.max_bins)
+        _, bf, bk, bs, s2 = oracle.split_scores(ref, nb, 3.0)
+        _, sf, sk, ss, gl, _ = t.level(d, 3.0, last=(d == depth - 1))
+        if (bs - s2) <= 1e-6 * abs(bs):
+            break                     # near-tie: the oracle cannot fix the choice
+        assert (sf, sk) == (bf, bk), d
+        assert ss == pytest.approx(bs, rel=1e-6)
+        leaf = oracle.update_leaf(bins, bf, bk, d, leaf)
+        assert np.array_equal(gl, leaf)
+        compared += 1
+    assert compared >= 2
+
+
+def test_apply_from_bins_reproduces_build_and_updates_pred(ctx):
+    import torch
+    n, F, depth, lr, l2 = 30011, 12, 5, 0.1, 3.0
+    bins, nb, g, h, forced = synth.random_level_case(9, n, F, 32, 64, depth)
+    t = Tree(ctx, bins, nb, g, h, depth)
+    for d in range(depth):
+        t.level(d, l2, force=forced[d], last=(d == depth - 1))
+    leaf_build = to_host(t.leaf, np.uint16)
+    pred0 = np.random.default_rng(2).normal(size=n).astype(np.float32)
+    pred = to_dev(pred0)
+    leaf_out = torch.empty(n, dtype=torch.int16, device="cuda")
+    vals = torch.empty(1 << depth, dtype=torch.float64, device="cuda")
+    cbg.cbg_apply_tree(ctx, n, depth, pred, bins=t.bins, F_pad=32, splits=t.splits, leaf_totals=t.child, l2=l2,
+                       lr=lr, leaf_out=leaf_out, leaf_values_out=vals)
+    cbg.cbg_sync(ctx)
+    assert np.array_equal(to_host(leaf_out, np.uint16), leaf_build)
+    fk = [f for f, _ in forced]
+    kk = [k for _, k in forced]
+    leaf_ref = oracle.tree_leaf_index(bins, fk, kk)
+    assert np.array_equal(leaf_build, leaf_ref)
+    tot = oracle.leaf_totals(g.astype(np.float64), h.astype(np.float64), leaf_ref, 1 << depth)
+    v = oracle.leaf_values(tot, l2)
+    assert np.allclose(to_host(vals), v, rtol=1e-5, atol=1e-9)
+    want = oracle.apply_leaf_values(leaf_ref, v, lr, pred0.astype(np.float64))
+    assert np.all(np.abs(to_host(pred) - want) <= 1e-6 * np.maximum(1, np.abs(want)))
+
+
+def _compare_fit(res_ref, splits_gpu, pred_gpu, trees, depth, atol=1e-4):
+    """Splits identical up to the first near-tie of the oracle; final predictions within
+    atol when no near-tie happened. Returns the number of levels compared."""
+    compared = 0
+    for t in range(trees):
+        for d in range(depth):
+            bs, s2 = res_ref["score"][t, d], res_ref["second"][t, d]
+            if res_ref["split_f"][t, d] >= 0 and (bs - s2) <= 1e-6 * abs(bs):
+                return compared, False
+            assert splits_gpu[t, d]["feature"] == res_ref["split_f"][t, d], (t, d)
+            if res_ref["split_f"][t, d] >= 0:
+                assert splits_gpu[t, d]["border"] == res_ref["split_k"][t, d], (t, d)
+            compared += 1
+    assert np.all(np.abs(pred_gpu - res_ref["pred"]) <= atol), np.abs(pred_gpu - res_ref["pred"]).max()
+    return compared, True
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_boost_rmse_10k_end_to_end(ctx, dtype):
+    w = synth.rmse_10k()
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "real", w.max_borders, a=w.a, seed=w.seed)
+    ref_prep = oracle.preprocess(w, prep.F_pad)
+    bins_gpu = train.rowmajor_from_grouped(to_host(prep.bins), w.n, prep.F_pad)
+    assert np.array_equal(to_host(prep.n_borders), ref_prep["n_borders"])
+    assert np.array_equal(bins_gpu, ref_prep["bins"])
+    model = train.fit(ctx, prep, to_dev(w.y), w.loss, w.depth, w.trees, w.lr, w.l2, gh_dtype=dtype)
+    cbg.cbg_sync(ctx)
+    res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, w.depth, w.trees, w.lr,
+                     w.l2, dtype=dtype)
+    compared, full = _compare_fit(res, model.host_splits(), to_host(model.pred), w.trees, w.depth)
+    assert full and compared == w.trees * w.depth
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_boost_logloss_end_to_end(ctx, use_graph):
+    w = synth.logloss_1m(n=60000, trees=30)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    ref_prep = oracle.preprocess(w, prep.F_pad)
+    bins_gpu = train.rowmajor_from_grouped(to_host(prep.bins), w.n, prep.F_pad)
+    assert np.array_equal(bins_gpu, ref_prep["bins"])
+    model = train.fit(ctx, prep, to_dev(w.y), w.loss, w.depth, w.trees, w.lr, w.l2, use_graph=use_graph)
+    cbg.cbg_sync(ctx)
+    res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, w.depth, w.trees, w.lr,
+                     w.l2)
+    compared, full = _compare_fit(res, model.host_splits(), to_host(model.pred), w.trees, w.depth)
+    assert compared >= 6 * w.depth
+    lv = to_host(model.leaf_values)
+    assert np.allclose(lv[:6], res["leaf_values"][:6], rtol=1e-4, atol=1e-7)
+    losses = res["losses"]
+    assert losses[-1] < losses[0]
+
+
+@pytest.mark.slow
+def test_full_size_logloss_1m_first_trees(ctx):
+    """The benchmark's 1M x 110 workload, depth 6: the first two trees (every level's
+    split, leaf values, predictions) against the oracle on the same bins."""
+    w = synth.logloss_1m(trees=2)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    ref_prep = oracle.preprocess(w, prep.F_pad)
+    bins_gpu = train.rowmajor_from_grouped(to_host(prep.bins), w.n, prep.F_pad)
+    assert np.array_equal(bins_gpu, ref_prep["bins"])
+    model = train.fit(ctx, prep, to_dev(w.y), w.loss, w.depth, w.trees, w.lr, w.l2)
+    cbg.cbg_sync(ctx)
+    res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, w.depth, w.trees, w.lr,
+                     w.l2)
+    compared, full = _compare_fit(res, model.host_splits(), to_host(model.pred), w.trees, w.depth)
+    assert compared >= w.depth
+    if full:
+        lv = to_host(model.leaf_values)
+        assert np.allclose(lv, res["leaf_values"], rtol=1e-5, atol=1e-9)
+
+
+def test_invalid_level_arguments_are_rejected(ctx):
+    import torch
+    bins, nb, g, h, _ = synth.random_level_case(0, 100, 4, 32, 9, 2)
+    t = Tree(ctx, bins, nb, g, h, 2)
+    with pytest.raises(cbg.CbgError) as e:
+        t.level(2, 3.0)                   # depth beyond max_depth
+    assert e.value.status == cbg.CBG_EINVAL
+    small = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(cbg.CbgError) as e:
+        cbg.cbg_build_level(ctx, t.shape, small, t.bins, t.nb, t.g, t.h, "f32", 0, 3.0, t.leaf, t.splits, t.child)
+    assert e.value.status == cbg.CBG_ENOMEM
