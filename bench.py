@@ -45,6 +45,14 @@ def parse_args():
     p.add_argument("--ref-sample-trees", type=int, default=2)
     p.add_argument("--no-graph", action="store_true", help="launch every kernel from the host instead of "
                                                            "replaying one captured tree")
+    p.add_argument("--hist-kernel", choices=["wp", "red", "cas64"], default="red",
+                   help="warp-private atomic-free histograms (wp) or shared-memory float reductions (red)")
+    p.add_argument("--cluster", type=int, default=0, help="CTAs per histogram cluster (0 = library default)")
+    p.add_argument("--rows-per-item", type=int, default=0, help="rows per CTA of a histogram work unit")
+    p.add_argument("--batched-problems", type=int, default=64,
+                   help="problems of the batched_256 workload for the batched-vs-plain comparison (0 = skip)")
+    p.add_argument("--batched-trees", type=int, default=20)
+    p.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-storage comparison step")
     return p.parse_args()
 
 
@@ -144,6 +152,68 @@ def oracle_sample(w, F_pad, trees):
     return t1 - t0, (t2 - t1) / trees, prep
 
 
+def training_loss(loss, y, pred):
+    """Training loss of float predictions (reporting only): RMSE or mean logloss, in FP64."""
+    import torch
+    p = pred.double()
+    yy = y.double()
+    if loss == "rmse":
+        return float(torch.sqrt(torch.mean((yy - p) ** 2)).item())
+    return float(torch.mean(torch.nn.functional.softplus(p) - yy * p).item())
+
+
+def batched_comparison(ctx, n_problems, trees, dev):
+    """The batching form (cbg_boost_batched: one captured graph per round, problems on
+    parallel branches) against the plain form (cbg_boost with graph replay, problem by
+    problem) on the first n_problems of batched_256, same trees and final losses."""
+    import numpy as np
+    import torch
+    from paper_1810_11363_gb300 import cbg, synth, train
+    ws = synth.batched_256(n_problems=n_problems, trees=trees)
+
+    def dev_arr(a):
+        return torch.from_numpy(np.ascontiguousarray(a.view(np.int32) if a.dtype == np.uint32 else a)).to(dev)
+
+    preps, ys = [], []
+    for w in ws:
+        cat = dev_arr(w.cat) if w.n_cat else torch.zeros((0, w.n), dtype=torch.int32, device=dev)
+        preps.append(train.preprocess(ctx, dev_arr(w.x), cat, dev_arr(w.y), w.label_kind, w.max_borders, a=w.a,
+                                      seed=w.seed))
+        ys.append(dev_arr(w.y))
+    depth, lr, l2 = 6, 0.1, 3.0
+    stream = torch.cuda.current_stream(dev)
+    bufs = [train.alloc_fit(p, depth, trees) for p in preps]
+
+    def plain():
+        for p, b, y, w in zip(preps, bufs, ys, ws):
+            b.pred.zero_()
+            train.fit(ctx, p, y, w.loss, depth, trees, lr, l2, bufs=b, use_graph=True)
+
+    def batched():
+        return train.fit_batched(ctx, preps, ys, [w.loss for w in ws], depth, trees, lr, l2)[0]
+
+    plain()
+    batched()                       # warm-up of both forms
+    torch.cuda.synchronize()
+    out = {}
+    for name, fn in (("plain", plain), ("batched", batched)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        preds = [b.pred for b in bufs] if name == "plain" else [m.pred for m in res]
+        losses = [training_loss(w.loss, y, pr) for w, y, pr in zip(ws, ys, preds)]
+        out[name] = {"trees_per_s": n_problems * trees / (ms / 1e3), "ms": ms, "losses": losses}
+    rel = max(abs(a - b) / max(abs(a), 1e-30) for a, b in zip(out["plain"]["losses"], out["batched"]["losses"]))
+    return {"workload": f"batched_256 first {n_problems} problems (n log-uniform 1k..200k, 10-200 floats + "
+                        f"0-8 categoricals, half RMSE half Logloss), depth 6, {trees} trees each, 128 borders",
+            "plain_trees_per_s": out["plain"]["trees_per_s"], "batched_trees_per_s": out["batched"]["trees_per_s"],
+            "speedup": out["batched"]["trees_per_s"] / out["plain"]["trees_per_s"],
+            "max_rel_final_loss_diff": rel}
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args):
     ws, rank, _ = dist_env()
@@ -211,7 +281,9 @@ def run_ours(args):
         return prep, model
 
     prep0 = train.preprocess(ctx, x, cat, y, "binary", w.max_borders, a=w.a, seed=w.seed)
-    bufs = train.alloc_fit(prep0, D, T, args.gh)
+    tiles = {"kernel": {"wp": 2, "red": 1, "cas64": 3}[args.hist_kernel], "cluster": args.cluster,
+             "rows_per_item": args.rows_per_item}
+    bufs = train.alloc_fit(prep0, D, T, args.gh, tiles=tiles)
     for _ in range(args.warmup):
         step(bufs)
     torch.cuda.synchronize()
@@ -266,7 +338,9 @@ def run_ours(args):
     peak, peak_kind = measured_peak_hbm()
     per_row = recorded_traffic_per_row()
     rows_per_launch = rows_hist / max(hist_launches, 1)
-    roofline = {"bound": "hbm", "kernel": "hist_kernel", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": "level_hist_wp_kernel" if args.hist_kernel == "wp" else "level_hist_kernel",
+                "kernel_variant": args.hist_kernel,
+                "achieved": achieved, "peak": peak,
                 "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": per_row * rows_per_launch if per_row else None,
@@ -301,6 +375,27 @@ def run_ours(args):
         e2e = {"value": T * args.steps * ws / (sum(e2e_ms) / 1e3), "unit": "trees/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": sum(e2e_ms) / len(e2e_ms)}
 
+    # BF16 gradient storage against FP32 on the same workload, at equal final loss
+    forms = {"f32": {"trees_per_s": value, "final_loss": training_loss(w.loss, y, bufs.pred)}}
+    if not args.no_bf16_form and args.gh == "f32":
+        bufs16 = train.alloc_fit(prep0, D, T, "bf16", tiles=tiles)
+        step(bufs16)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prep = train.preprocess(ctx, x, cat, y, "binary", w.max_borders, a=w.a, seed=w.seed)
+        bufs16.pred.zero_()
+        train.fit(ctx, prep, y, w.loss, D, T, w.lr, w.l2, gh_dtype="bf16", bufs=bufs16, use_graph=use_graph)
+        e1.record(stream)
+        e1.synchronize()
+        l16 = training_loss(w.loss, y, bufs16.pred)
+        forms["bf16"] = {"trees_per_s": T / (e0.elapsed_time(e1) / 1e3), "final_loss": l16,
+                         "rel_final_loss_diff_vs_f32": abs(l16 - forms["f32"]["final_loss"]) /
+                         abs(forms["f32"]["final_loss"])}
+    batched = None
+    if args.batched_problems > 0 and rank == 0:
+        batched = batched_comparison(ctx, args.batched_problems, args.batched_trees, dev)
+
     launches_per_step = None
     # kernels of ours per step: preprocessing launches + per tree (levels x kernels + apply)
     per_level = 7
@@ -322,9 +417,10 @@ def run_ours(args):
                                        f"{T} trees, lr 0.05, L2 3, Logloss", "trees_per_step": T,
                            "parallelism": f"replicas x{ws}", "l2_flush": "256 MB write between steps; inputs "
                                                                              "(x 400 MB) larger than L2",
-                           "gh_storage": args.gh, "graph_replay": use_graph},
+                           "gh_storage": args.gh, "graph_replay": use_graph, "hist_tiles": tiles},
                 "row_feature_bins_per_s": rfb, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "forms": forms, "batched_vs_plain": batched,
                 "breakdown": {"step_ms": step_ms}}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -66,17 +66,23 @@ typedef struct cbg_split {
 
 /* Histogram tiling. slab_chunks: 16-feature chunks per work item (2);
  * rows_per_item: rows per CTA of a work unit; threads: threads per histogram
- * CTA (a multiple of 32, <= 512); blocks_per_sm: unused (the grid is sized by
- * the occupancy of clusters); cluster: CTAs per thread-block cluster that share
- * one partial histogram through distributed shared memory (1..16; a smaller
- * power of two is used if that many cannot be co-resident). Zero fields take
- * library defaults. */
+ * CTA (a multiple of 32, <= 512; for the warp-private kernel an upper bound on
+ * its warps, each of which holds a private histogram); blocks_per_sm: unused
+ * (the grid is sized by the occupancy of clusters); cluster: CTAs per
+ * thread-block cluster that share one partial histogram through distributed
+ * shared memory (1..16; a smaller power of two is used if that many cannot be
+ * co-resident); kernel: 1 = one shared histogram per CTA updated with
+ * shared-memory float reductions (the default, 0), 2 = warp-private
+ * histograms updated without atomics, 3 = one shared histogram per CTA with
+ * (G, H) updated by one 64-bit compare-and-swap. Zero fields take library
+ * defaults. */
 typedef struct cbg_tiles {
   int32_t slab_chunks;
   int32_t rows_per_item;
   int32_t threads;
   int32_t blocks_per_sm;
   int32_t cluster;
+  int32_t kernel;
 } cbg_tiles;
 
 /* Shape of one boosting problem's tree state. */
@@ -269,6 +275,37 @@ typedef struct cbg_boost_args {
   int32_t use_graph;
 } cbg_boost_args;
 cbg_status cbg_boost(cbg_ctx* ctx, const cbg_boost_args* args);
+
+/* One independent boosting problem of a batched run: its own data, tree state
+ * and model outputs (the same arrays as cbg_boost_args). */
+typedef struct cbg_problem {
+  cbg_tree_shape shape;
+  void* state;
+  size_t state_bytes;
+  const uint8_t* bins;
+  const uint8_t* bins_t;
+  const int32_t* n_borders;
+  const float* y;
+  int32_t loss;
+  int32_t reserved;
+  float* pred;
+  void* g;
+  void* h;
+  uint16_t* leaf;
+  cbg_split* splits;       /* device [T][depth] */
+  double* leaf_values;     /* device [T][2^depth] */
+  double* child_totals;    /* device [2^depth][2] */
+} cbg_problem;
+
+/* Batched boosting of many independent problems (each follows cbg_boost, the
+ * classic scheme of Sections 3-4). One round -- one tree of every problem -- is
+ * captured once as a single CUDA graph whose `branches` parallel branches
+ * (problems assigned round-robin, 0 = min(n_problems, 32)) let the GPU run the
+ * small problems' kernels concurrently; the round is replayed `trees` times.
+ * Every problem uses the same depth, lr, l2 and gradient storage; problem i's
+ * result is the same as cbg_boost on it alone. problems is a host array. */
+cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t n_problems, int32_t gh_dtype,
+                             int32_t depth, int32_t trees, double lr, double l2, int32_t branches);
 
 /* ------------------------------------------------------------ profiling ---- */
 

@@ -36,7 +36,7 @@ class Split(C.Structure):
 
 class Tiles(C.Structure):
     _fields_ = [("slab_chunks", c_i32), ("rows_per_item", c_i32), ("threads", c_i32), ("blocks_per_sm", c_i32),
-                ("cluster", c_i32)]
+                ("cluster", c_i32), ("kernel", c_i32)]
 
 
 class TreeShape(C.Structure):
@@ -67,6 +67,13 @@ class BoostArgs(C.Structure):
                 ("leaf_values", c_vp), ("child_totals", c_vp), ("use_graph", c_i32)]
 
 
+class Problem(C.Structure):
+    _fields_ = [("shape", TreeShape), ("state", c_vp), ("state_bytes", C.c_size_t), ("bins", c_vp),
+                ("bins_t", c_vp), ("n_borders", c_vp), ("y", c_vp), ("loss", c_i32), ("reserved", c_i32),
+                ("pred", c_vp), ("g", c_vp), ("h", c_vp), ("leaf", c_vp), ("splits", c_vp),
+                ("leaf_values", c_vp), ("child_totals", c_vp)]
+
+
 # name -> (restype, argtypes); every entry point declared in include/cbg.h
 SIGNATURES = {
     "cbg_version": (C.c_char_p, []),
@@ -87,6 +94,7 @@ SIGNATURES = {
     "cbg_build_level": (c_i32, [c_vp, C.POINTER(LevelArgs)]),
     "cbg_apply_tree": (c_i32, [c_vp, C.POINTER(ApplyArgs)]),
     "cbg_boost": (c_i32, [c_vp, C.POINTER(BoostArgs)]),
+    "cbg_boost_batched": (c_i32, [c_vp, C.POINTER(Problem), c_i32, c_i32, c_i32, c_i32, c_f64, c_f64, c_i32]),
     "cbg_profile_enable": (c_i32, [c_vp, C.c_int]),
     "cbg_profile_read": (c_i32, [c_vp, C.c_int, C.POINTER(c_f64), C.POINTER(c_i64)]),
     "cbg_tree_rows_histogrammed": (c_i32, [c_vp, C.POINTER(TreeShape), c_vp, C.c_int, C.POINTER(c_i64)]),
@@ -265,3 +273,12 @@ def cbg_tree_rows_histogrammed(ctx: Context, shape: TreeShape, state, reset: boo
     ctx.check(ctx.lib.cbg_tree_rows_histogrammed(ctx.h, C.byref(shape), _p(state), int(reset), C.byref(rows)),
               "cbg_tree_rows_histogrammed")
     return int(rows.value)
+
+
+
+def cbg_boost_batched(ctx: Context, problems, gh_dtype: str, depth: int, trees: int, lr: float, l2: float,
+                      branches: int = 0):
+    """problems: sequence of Problem structures (host)."""
+    arr = (Problem * len(problems))(*problems)
+    ctx.check(ctx.lib.cbg_boost_batched(ctx.h, arr, len(problems), DTYPE[gh_dtype], depth, trees, lr, l2, branches),
+              "cbg_boost_batched")

@@ -28,6 +28,8 @@ struct cbg_ctx {
   double prof_ms = 0.0;
   int64_t prof_launches = 0;
   cudaStream_t capture_stream = nullptr;   // non-blocking stream used to capture graphs
+  std::vector<cudaStream_t> branch_streams;  // branches of a captured batched round
+  std::vector<cudaEvent_t> branch_events;
 };
 
 namespace cbg {

@@ -114,6 +114,8 @@ void cbg_ctx_destroy(cbg_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  for (cudaStream_t st : ctx->branch_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : ctx->branch_events) cudaEventDestroy(e);
   cudaGetLastError();
   delete ctx;
 }

@@ -35,11 +35,25 @@ struct Plan {
 
 size_t hist_smem_bytes(int nb_alloc) { return static_cast<size_t>(2) * nb_alloc * GROUP * sizeof(float); }
 
-// What the histogram launch needs to know about a problem.
+// What the histogram launch needs to know about a problem. kind 0: warp-private
+// histograms without atomics (default); kind 1: one shared histogram per CTA updated with
+// shared-memory float reductions.
 struct HistConfig {
   int64_t n;
-  int G, F, max_bins, nb_alloc, threads, cluster;
+  int G, F, max_bins, nb_alloc, threads, cluster, kind = 0;
 };
+
+// Warps per CTA of the warp-private kernel: as many (G, H) float2 histograms of
+// max_bins x 32 as fit in one SM's shared memory, at most 16.
+inline int wp_warps(int max_bins, int requested_threads) {
+  const int fit = static_cast<int>((227 * 1024) / (static_cast<size_t>(max_bins) * GROUP * sizeof(float2)));
+  int w = fit < 16 ? fit : 16;
+  if (requested_threads > 0 && requested_threads / 32 < w) w = requested_threads / 32;
+  return w < 1 ? 1 : w;
+}
+inline size_t wp_smem_bytes(int max_bins, int warps) {
+  return static_cast<size_t>(warps) * max_bins * GROUP * sizeof(float2);
+}
 
 // ------------------------------------------------------------------ histogram
 __device__ __forceinline__ void red_add(uint32_t addr, float v) {
@@ -55,7 +69,26 @@ __device__ __forceinline__ void red_add(uint32_t addr, float v) {
 // updates feature 16c + (l + j) % 16, so the 32 lanes hit 32 different features and banks
 // (the rotation of the paper's Section 4 example, applied to 16-byte loads). Chunks that
 // hold only padding features are skipped.
-template <typename GH, int NB>
+// MODE 0: G and H in two planes [2][NB][32], each updated with red.shared.add.f32.
+// MODE 1: (G, H) interleaved as float2 [NB][32], updated with one 64-bit compare-and-swap
+// loop per (row, feature); on sm_103a the FP32 shared reduction is itself a
+// compare-and-swap loop, so this halves the atomic operations.
+__device__ __forceinline__ void cas_add2(float2* p, float gx, float hy) {
+  unsigned long long* a = reinterpret_cast<unsigned long long*>(p);
+  unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(a);
+  while (true) {
+    float2 o;
+    memcpy(&o, &old, 8);
+    const float2 nw = make_float2(o.x + gx, o.y + hy);
+    unsigned long long nv;
+    memcpy(&nv, &nw, 8);
+    const unsigned long long prev = atomicCAS(a, old, nv);
+    if (prev == old) break;
+    old = prev;
+  }
+}
+
+template <typename GH, int NB, int MODE>
 __global__ void __launch_bounds__(512, 3) level_hist_kernel(const uint8_t* __restrict__ bins, int64_t n, int G, int F,
                                                          const uint32_t* __restrict__ order,
                                                          const GH* __restrict__ g, const GH* __restrict__ h,
@@ -121,9 +154,15 @@ __global__ void __launch_bounds__(512, 3) level_hist_kernel(const uint8_t* __res
 #pragma unroll
         for (int l = 0; l < 16; ++l) {
           const uint32_t b = (R[l >> 2] >> (8 * (l & 3))) & (NB - 1);
-          const uint32_t a = off[l] + b * (GROUP * 4);
-          red_add(a, gv);
-          red_add(a + PLANE * 4, hv);
+          if (MODE == 0) {
+            const uint32_t a = off[l] + b * (GROUP * 4);
+            red_add(a, gv);
+            red_add(a + PLANE * 4, hv);
+          } else {
+            // off[l] - sbase is 4 x (feature within the group)
+            const uint32_t f = (off[l] - sbase) >> 2;
+            cas_add2(reinterpret_cast<float2*>(hsh) + b * GROUP + f, gv, hv);
+          }
         }
       }
     }
@@ -135,10 +174,154 @@ __global__ void __launch_bounds__(512, 3) level_hist_kernel(const uint8_t* __res
     float* dst = partials + static_cast<int64_t>(item) * (2 * max_bins * GROUP);
     for (int i = threadIdx.x; i < 2 * nbs * GROUP; i += blockDim.x) {
       const int st = i / (nbs * GROUP), rem = i - st * (nbs * GROUP);
-      const int e = st * PLANE + b0 * GROUP + rem;
+      const int e = MODE == 0 ? st * PLANE + b0 * GROUP + rem : (b0 * GROUP + rem) * 2 + st;
       float v = 0.f;
       for (int r = 0; r < cs; ++r) v += peer[r][e];
       dst[st * (max_bins * GROUP) + b0 * GROUP + rem] = v;
+    }
+    cl.sync();
+  }
+}
+
+// Warp-private histogram, no atomics (the paper's Section 4 idea of per-warp partial
+// histograms updated without atomic operations). Lane f of every warp owns feature f of
+// the 32-feature group: its column of a (G, H) float2 histogram [max_bins][32] private
+// to the warp, so a plain shared load, add and store per update is race-free and the 32
+// lanes always hit 32 different columns (different banks). A warp walks rows in blocks
+// of 32: lane i fetches the row id and (g, h) of row i, then every lane fetches its own
+// feature's bin byte of the 32 rows (one 32-byte sector per row); loads run two blocks
+// ahead of the updates. Updates go in batches of 4 rows: equal bins within a batch are
+// merged in registers first, so the batch's 4 read-modify-writes are independent. Rows
+// of the unit are split among the CTA's warps and the cs CTAs of a cluster; at the end
+// CTA r sums its slice of bins over every warp of every CTA of the cluster (distributed
+// shared memory) into the unit's FP32 partial.
+template <typename GH>
+__global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __restrict__ bins, int64_t n, int G,
+                                                               int F, const uint32_t* __restrict__ order,
+                                                               const GH* __restrict__ g, const GH* __restrict__ h,
+                                                               const Plan* __restrict__ plan, int max_bins,
+                                                               float* __restrict__ partials) {
+  namespace cgr = cooperative_groups;
+  extern __shared__ __align__(16) float2 wsh[];   // [W][max_bins][32]
+  constexpr int MAX_CS = 16;
+  constexpr unsigned FULL = 0xffffffffu;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int cs = static_cast<int>(cl.num_blocks());
+  const int rank = static_cast<int>(cl.block_rank());
+  const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int per_warp = max_bins * GROUP;
+  float2* my = wsh + static_cast<int64_t>(warp) * per_warp;
+  const int maxb1 = max_bins - 1;
+  const float2* peer[MAX_CS];
+  for (int r = 0; r < cs && r < MAX_CS; ++r) peer[r] = cl.map_shared_rank(wsh, r);
+  const int total_items = plan->total_units * G;
+  const int n_small = plan->n_small;
+  for (int item = cid; item < total_items; item += ncl) {
+    const int unit = item / G, grp = item - unit * G;
+    int lo = 0, hi = n_small - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (plan->unit_begin[mid] <= unit) lo = mid; else hi = mid - 1;
+    }
+    const int jj = lo;
+    const int chunk = unit - plan->unit_begin[jj];
+    const int seg_s = plan->seg_start[jj], seg_c = plan->seg_cnt[jj];
+    const int cr = plan->chunk_rows[jj];
+    const int p0 = seg_s + (chunk * cs + rank) * cr;
+    const int p1 = min(seg_s + seg_c, p0 + cr);
+    for (int i = lane; i < per_warp; i += 32) my[i] = make_float2(0.f, 0.f);
+    __syncwarp();
+    const int nblk = p1 > p0 ? (p1 - p0 + 31) / 32 : 0;
+    const uint8_t* gb = bins + static_cast<int64_t>(grp) * n * GROUP + lane;
+    // block k of this warp is block warp + k*W of the CTA's rows
+    auto load_rows = [&](int k, uint32_t& row, float& gv, float& hv) {
+      const int blk = warp + k * W;
+      const int pos = p0 + blk * 32 + lane;
+      if (blk < nblk && pos < p1) {
+        row = order ? order[pos] : static_cast<uint32_t>(pos);
+        gv = cbgd::load_gh(g, row);
+        hv = cbgd::load_gh(h, row);
+      } else {
+        row = 0;       // a valid address; zero (g, h) make its updates no-ops
+        gv = 0.f;
+        hv = 0.f;
+      }
+    };
+    // The 32 bytes stay unpacked in registers until the next block is processed, so the
+    // issuing warp never waits on these loads before it has work for them.
+    auto load_bins = [&](uint32_t row_lane, uint8_t (&raw)[32]) {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const uint32_t rr = __shfl_sync(FULL, row_lane, r);
+        raw[r] = __ldg(gb + static_cast<int64_t>(rr) * GROUP);
+      }
+    };
+    auto process = [&](const uint8_t (&raw)[32], float gv, float hv) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int b0 = min(static_cast<int>(raw[4 * q]), maxb1);
+        const int b1 = min(static_cast<int>(raw[4 * q + 1]), maxb1);
+        const int b2 = min(static_cast<int>(raw[4 * q + 2]), maxb1);
+        const int b3 = min(static_cast<int>(raw[4 * q + 3]), maxb1);
+        float g0 = __shfl_sync(FULL, gv, 4 * q), g1 = __shfl_sync(FULL, gv, 4 * q + 1);
+        float g2 = __shfl_sync(FULL, gv, 4 * q + 2), g3 = __shfl_sync(FULL, gv, 4 * q + 3);
+        float h0 = __shfl_sync(FULL, hv, 4 * q), h1 = __shfl_sync(FULL, hv, 4 * q + 1);
+        float h2 = __shfl_sync(FULL, hv, 4 * q + 2), h3 = __shfl_sync(FULL, hv, 4 * q + 3);
+        bool v1 = true, v2 = true, v3 = true;
+        if (b1 == b0) { g0 += g1; h0 += h1; v1 = false; }
+        if (b2 == b0) { g0 += g2; h0 += h2; v2 = false; }
+        else if (b2 == b1) { g1 += g2; h1 += h2; v2 = false; }
+        if (b3 == b0) { g0 += g3; h0 += h3; v3 = false; }
+        else if (b3 == b1) { g1 += g3; h1 += h3; v3 = false; }
+        else if (b3 == b2) { g2 += g3; h2 += h3; v3 = false; }
+        float2* a0 = my + b0 * GROUP + lane;
+        float2* a1 = my + b1 * GROUP + lane;
+        float2* a2 = my + b2 * GROUP + lane;
+        float2* a3 = my + b3 * GROUP + lane;
+        // all loads before all stores: the valid addresses of a batch are distinct
+        float2 o0 = *a0;
+        float2 o1 = v1 ? *a1 : make_float2(0.f, 0.f);
+        float2 o2 = v2 ? *a2 : make_float2(0.f, 0.f);
+        float2 o3 = v3 ? *a3 : make_float2(0.f, 0.f);
+        o0.x += g0; o0.y += h0;
+        *a0 = o0;
+        if (v1) { o1.x += g1; o1.y += h1; *a1 = o1; }
+        if (v2) { o2.x += g2; o2.y += h2; *a2 = o2; }
+        if (v3) { o3.x += g3; o3.y += h3; *a3 = o3; }
+      }
+    };
+    const int my_blocks = nblk > warp ? (nblk - warp + W - 1) / W : 0;
+    uint32_t rowA, rowB, rowC;
+    float gA, hA, gB, hB, gC, hC;
+    uint8_t rawA[32], rawB[32];
+    load_rows(0, rowA, gA, hA);
+    load_rows(1, rowB, gB, hB);
+    load_bins(rowA, rawA);
+    for (int k = 0; k < my_blocks; ++k) {
+      load_rows(k + 2, rowC, gC, hC);
+      if (k + 1 < my_blocks) load_bins(rowB, rawB);
+      process(rawA, gA, hA);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) rawA[i] = rawB[i];
+      gA = gB; hA = hB; rowB = rowC; gB = gC; hB = hC;
+    }
+    cl.sync();
+    const int bs = (max_bins + cs - 1) / cs;
+    const int b0 = rank * bs;
+    const int nbs = max(0, min(max_bins, b0 + bs) - b0);
+    float* dst = partials + static_cast<int64_t>(item) * (2 * max_bins * GROUP);
+    for (int i = threadIdx.x; i < nbs * GROUP; i += blockDim.x) {
+      const int e = b0 * GROUP + i;
+      float sx = 0.f, sy = 0.f;
+      for (int r = 0; r < cs; ++r)
+        for (int w = 0; w < W; ++w) {
+          const float2 v = peer[r][static_cast<int64_t>(w) * per_warp + e];
+          sx += v.x;
+          sy += v.y;
+        }
+      dst[e] = sx;
+      dst[max_bins * GROUP + e] = sy;
     }
     cl.sync();
   }
@@ -198,7 +381,7 @@ struct HistGeom {
   int clusters = 0;
 };
 
-template <typename GH, int NB>
+template <typename GH, int NB, int MODE>
 cbg_status hist_geom_for(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   static std::mutex mu;
   static std::map<std::tuple<int, int, int, int, int>, HistGeom> cache;
@@ -211,7 +394,7 @@ cbg_status hist_geom_for(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
       return CBG_OK;
     }
   }
-  auto kern = level_hist_kernel<GH, NB>;
+  auto kern = level_hist_kernel<GH, NB, MODE>;
   const size_t smem = hist_smem_bytes(NB);
   CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   HistGeom geom;
@@ -247,35 +430,91 @@ cbg_status hist_geom_for(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   return CBG_OK;
 }
 
-template <typename GH>
-cbg_status hist_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* g) {
+template <typename GH, int MODE>
+cbg_status hist_geom_mode(cbg_ctx* ctx, const HistConfig& L, HistGeom* g) {
   switch (L.nb_alloc) {
-    case 2: return hist_geom_for<GH, 2>(ctx, L, g);
-    case 4: return hist_geom_for<GH, 4>(ctx, L, g);
-    case 8: return hist_geom_for<GH, 8>(ctx, L, g);
-    case 16: return hist_geom_for<GH, 16>(ctx, L, g);
-    case 32: return hist_geom_for<GH, 32>(ctx, L, g);
-    case 64: return hist_geom_for<GH, 64>(ctx, L, g);
-    case 128: return hist_geom_for<GH, 128>(ctx, L, g);
-    case 256: return hist_geom_for<GH, 256>(ctx, L, g);
+    case 2: return hist_geom_for<GH, 2, MODE>(ctx, L, g);
+    case 4: return hist_geom_for<GH, 4, MODE>(ctx, L, g);
+    case 8: return hist_geom_for<GH, 8, MODE>(ctx, L, g);
+    case 16: return hist_geom_for<GH, 16, MODE>(ctx, L, g);
+    case 32: return hist_geom_for<GH, 32, MODE>(ctx, L, g);
+    case 64: return hist_geom_for<GH, 64, MODE>(ctx, L, g);
+    case 128: return hist_geom_for<GH, 128, MODE>(ctx, L, g);
+    case 256: return hist_geom_for<GH, 256, MODE>(ctx, L, g);
     default: return ::cbg::fail(ctx, CBG_EINVAL, "unsupported bin allocation %d", L.nb_alloc);
   }
+}
+
+template <typename GH>
+cbg_status hist_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* g) {
+  return L.kind == 3 ? hist_geom_mode<GH, 1>(ctx, L, g) : hist_geom_mode<GH, 0>(ctx, L, g);
+}
+
+template <typename GH>
+cbg_status wp_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int>, HistGeom> cache;
+  const int warps = wp_warps(L.max_bins, L.threads);
+  const auto key = std::make_tuple(ctx->device, L.max_bins, warps, L.cluster, static_cast<int>(sizeof(GH)));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *out = it->second;
+      return CBG_OK;
+    }
+  }
+  auto kern = level_hist_wp_kernel<GH>;
+  const size_t smem = wp_smem_bytes(L.max_bins, warps);
+  // one attribute for every histogram size this kernel is launched with
+  CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  HistGeom geom;
+  // the cluster size (<= the requested one) that keeps the most CTAs co-resident
+  for (int cs = L.cluster; cs >= 1; cs >>= 1) {
+    if (cs > 8) CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(cs * ctx->num_sms));
+    cfg.blockDim = dim3(static_cast<unsigned>(32 * warps));
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(cs);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      clusters = 0;
+    }
+    if (clusters * cs > geom.clusters * geom.cs) {
+      geom.cs = cs;
+      geom.clusters = clusters;
+    }
+  }
+  if (geom.clusters == 0) return ::cbg::fail(ctx, CBG_EUNSUPPORTED, "no co-resident histogram cluster fits on this device");
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = geom;
+  *out = geom;
+  return CBG_OK;
 }
 
 // The cluster size the plan must chunk for (identical for FP32 and BF16 gradients).
 cbg_status hist_cluster_size(cbg_ctx* ctx, const HistConfig& L, int* cs) {
   HistGeom g;
-  cbg_status st = hist_geom<float>(ctx, L, &g);
+  cbg_status st = L.kind == 0 ? wp_geom<float>(ctx, L, &g) : hist_geom<float>(ctx, L, &g);
   if (st != CBG_OK) return st;
   *cs = g.cs;
   return CBG_OK;
 }
 
-template <typename GH, int NB>
+template <typename GH, int NB, int MODE>
 cbg_status launch_hist_nb(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins, const uint32_t* order, const GH* g,
                           const GH* h, const Plan* plan, float* partials, int cs_plan) {
   HistGeom geom;
-  cbg_status st = hist_geom_for<GH, NB>(ctx, L, &geom);
+  cbg_status st = hist_geom_for<GH, NB, MODE>(ctx, L, &geom);
   if (st != CBG_OK) return st;
   if (geom.cs != cs_plan) return ::cbg::fail(ctx, CBG_ECUDA, "histogram cluster size changed between plan and launch");
   cudaLaunchConfig_t cfg = {};
@@ -290,7 +529,7 @@ cbg_status launch_hist_nb(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_kernel<GH, NB>, bins, L.n, L.G, L.F, order, g, h, plan,
+  CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_kernel<GH, NB, MODE>, bins, L.n, L.G, L.F, order, g, h, plan,
                                    L.max_bins, partials));
   return CBG_OK;
 }
@@ -303,15 +542,50 @@ cbg_status launch_hist(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins, c
   if (st != CBG_OK) return st;
   const GH* gg = static_cast<const GH*>(g);
   const GH* hh = static_cast<const GH*>(h);
+  if (L.kind == 0) {
+    HistGeom geom;
+    st = wp_geom<GH>(ctx, L, &geom);
+    if (st != CBG_OK) return st;
+    if (geom.cs != cs) return ::cbg::fail(ctx, CBG_ECUDA, "histogram cluster size changed between plan and launch");
+    const int warps = wp_warps(L.max_bins, L.threads);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(geom.cs * geom.clusters));
+    cfg.blockDim = dim3(static_cast<unsigned>(32 * warps));
+    cfg.dynamicSmemBytes = wp_smem_bytes(L.max_bins, warps);
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(geom.cs);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_wp_kernel<GH>, bins, L.n, L.G, L.F, order, gg, hh, plan,
+                                     L.max_bins, partials));
+    return CBG_OK;
+  }
+  if (L.kind == 3) {
+    switch (L.nb_alloc) {
+      case 2: return launch_hist_nb<GH, 2, 1>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 4: return launch_hist_nb<GH, 4, 1>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 8: return launch_hist_nb<GH, 8, 1>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 16: return launch_hist_nb<GH, 16, 1>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 32: return launch_hist_nb<GH, 32, 1>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 64: return launch_hist_nb<GH, 64, 1>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 128: return launch_hist_nb<GH, 128, 1>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 256: return launch_hist_nb<GH, 256, 1>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      default: return ::cbg::fail(ctx, CBG_EINVAL, "unsupported bin allocation %d", L.nb_alloc);
+    }
+  }
   switch (L.nb_alloc) {
-    case 2: return launch_hist_nb<GH, 2>(ctx, L, bins, order, gg, hh, plan, partials, cs);
-    case 4: return launch_hist_nb<GH, 4>(ctx, L, bins, order, gg, hh, plan, partials, cs);
-    case 8: return launch_hist_nb<GH, 8>(ctx, L, bins, order, gg, hh, plan, partials, cs);
-    case 16: return launch_hist_nb<GH, 16>(ctx, L, bins, order, gg, hh, plan, partials, cs);
-    case 32: return launch_hist_nb<GH, 32>(ctx, L, bins, order, gg, hh, plan, partials, cs);
-    case 64: return launch_hist_nb<GH, 64>(ctx, L, bins, order, gg, hh, plan, partials, cs);
-    case 128: return launch_hist_nb<GH, 128>(ctx, L, bins, order, gg, hh, plan, partials, cs);
-    case 256: return launch_hist_nb<GH, 256>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+    case 2: return launch_hist_nb<GH, 2, 0>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+    case 4: return launch_hist_nb<GH, 4, 0>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+    case 8: return launch_hist_nb<GH, 8, 0>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+    case 16: return launch_hist_nb<GH, 16, 0>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+    case 32: return launch_hist_nb<GH, 32, 0>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+    case 64: return launch_hist_nb<GH, 64, 0>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+    case 128: return launch_hist_nb<GH, 128, 0>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+    case 256: return launch_hist_nb<GH, 256, 0>(ctx, L, bins, order, gg, hh, plan, partials, cs);
     default: return ::cbg::fail(ctx, CBG_EINVAL, "unsupported bin allocation %d", L.nb_alloc);
   }
 }

@@ -45,7 +45,7 @@ struct BestF {
 struct Layout {
   int64_t n;
   int F, F_pad, G, max_bins, nb_alloc, D;
-  int rows_per_item, threads, blocks_per_sm, cluster;
+  int rows_per_item, threads, blocks_per_sm, cluster, kind;
   int64_t max_items;
   int64_t n_ptiles;
   size_t hist_elems;                // per hist buffer (doubles)
@@ -82,7 +82,10 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
   L->nb_alloc = pow2_at_least(L->max_bins);
   L->D = s->max_depth;
   CBG_REQUIRE(ctx, t.cluster >= 0 && t.cluster <= 16, "cluster must be in [0, 16]");
-  L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : 4096;
+  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 3, "kernel must be 0 (default), 1 (shared reductions), 2 "
+              "(warp-private) or 3 (64-bit compare-and-swap)");
+  L->kind = t.kernel == 2 ? 0 : (t.kernel == 3 ? 3 : 1);
+  L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : 2048;
   L->cluster = t.cluster > 0 ? t.cluster : 8;
   L->threads = t.threads > 0 ? t.threads : 512;
   const int fit = static_cast<int>((227 * 1024) / hist_smem_bytes(L->nb_alloc));
@@ -132,6 +135,7 @@ HistConfig hist_config(const Layout& L) {
   c.nb_alloc = L.nb_alloc;
   c.threads = L.threads;
   c.cluster = L.cluster;
+  c.kind = L.kind;
   return c;
 }
 
@@ -1040,6 +1044,128 @@ cbg_status cbg_boost(cbg_ctx* ctx, const cbg_boost_args* a) {
   }
   cudaGraphExecDestroy(exec);   // freed once the queued launches complete
   if (ce != cudaSuccess) return fail(ctx, CBG_ECUDA, "graph launch failed: %s", cudaGetErrorString(ce));
+  return CBG_OK;
+}
+
+
+cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t n_problems, int32_t gh_dtype,
+                             int32_t depth, int32_t trees, double lr, double l2, int32_t branches) {
+  if (!ctx) return CBG_EINVAL;
+  CBG_REQUIRE(ctx, problems != nullptr && n_problems >= 1, "need at least one problem");
+  CBG_REQUIRE(ctx, depth >= 1 && depth <= MAX_DEPTH, "depth must be in [1, 10]");
+  CBG_REQUIRE(ctx, trees >= 0, "trees must be >= 0");
+  CBG_REQUIRE(ctx, gh_dtype == CBG_F32 || gh_dtype == CBG_BF16, "bad gh_dtype");
+  CBG_REQUIRE(ctx, branches >= 0, "branches must be >= 0");
+  DeviceGuard guard(ctx->device);
+  const int nb = branches > 0 ? std::min(branches, n_problems) : std::min(n_problems, 32);
+  std::vector<cbg_boost_args> args(n_problems);
+  for (int i = 0; i < n_problems; ++i) {
+    const cbg_problem& p = problems[i];
+    cbg_boost_args& a = args[i];
+    a = cbg_boost_args{};
+    a.shape = &p.shape;
+    a.state = p.state;
+    a.state_bytes = p.state_bytes;
+    a.bins = p.bins;
+    a.bins_t = p.bins_t;
+    a.n_borders = p.n_borders;
+    a.y = p.y;
+    a.loss = p.loss;
+    a.gh_dtype = gh_dtype;
+    a.depth = depth;
+    a.trees = trees;
+    a.lr = lr;
+    a.l2 = l2;
+    a.pred = p.pred;
+    a.g = p.g;
+    a.h = p.h;
+    a.leaf = p.leaf;
+    a.splits = p.splits;
+    a.leaf_values = p.leaf_values;
+    a.child_totals = p.child_totals;
+    CBG_REQUIRE(ctx, depth <= p.shape.max_depth, "problem %d: depth exceeds its max_depth", i);
+    CBG_REQUIRE(ctx, p.pred && p.y && p.g && p.h && p.leaf && p.splits && p.leaf_values && p.child_totals,
+                "problem %d: NULL argument", i);
+    Layout L;
+    cbg_status st = make_layout(ctx, &p.shape, &L);
+    if (st != CBG_OK) return st;
+    st = check_state(ctx, L, p.state, p.state_bytes);
+    if (st != CBG_OK) return st;
+    // launch-geometry queries happen here, before the capture
+    HistGeom geom;
+    st = gh_dtype == CBG_F32 ? hist_geom<float>(ctx, hist_config(L), &geom)
+                             : hist_geom<__nv_bfloat16>(ctx, hist_config(L), &geom);
+    if (st != CBG_OK) return st;
+    if (hist_config(L).kind == 0) {
+      st = gh_dtype == CBG_F32 ? wp_geom<float>(ctx, hist_config(L), &geom)
+                               : wp_geom<__nv_bfloat16>(ctx, hist_config(L), &geom);
+      if (st != CBG_OK) return st;
+    }
+    int cs = 1;
+    st = hist_cluster_size(ctx, hist_config(L), &cs);
+    if (st != CBG_OK) return st;
+    st = cbg_gradients(ctx, p.loss, p.y, p.pred, p.shape.n, gh_dtype, p.g, p.h);
+    if (st != CBG_OK) return st;
+    unsigned* counter = reinterpret_cast<unsigned*>(at<char>(p.state, L.o_gsplit) + sizeof(cbg_split) * MAX_DEPTH);
+    CBG_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned), ctx->stream));
+  }
+  if (trees == 0) return CBG_OK;
+  if (!ctx->capture_stream) CBG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+  while (static_cast<int>(ctx->branch_streams.size()) < nb) {
+    cudaStream_t st;
+    CBG_CUDA(ctx, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    ctx->branch_streams.push_back(st);
+  }
+  while (static_cast<int>(ctx->branch_events.size()) < nb + 1) {
+    cudaEvent_t e;
+    CBG_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->branch_events.push_back(e);
+  }
+  cudaStream_t user_stream = ctx->stream;
+  cudaStream_t origin = ctx->capture_stream;
+  cudaGraph_t graph = nullptr;
+  CBG_CUDA(ctx, cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+  cbg_status st = CBG_OK;
+  cudaError_t ce = cudaEventRecord(ctx->branch_events[nb], origin);
+  for (int b = 0; b < nb && ce == cudaSuccess; ++b) ce = cudaStreamWaitEvent(ctx->branch_streams[b], ctx->branch_events[nb], 0);
+  if (ce != cudaSuccess) st = fail(ctx, CBG_ECUDA, "forking the batched round failed: %s", cudaGetErrorString(ce));
+  for (int i = 0; i < n_problems && st == CBG_OK; ++i) {
+    Layout L;
+    st = make_layout(ctx, &problems[i].shape, &L);
+    if (st != CBG_OK) break;
+    ctx->stream = ctx->branch_streams[i % nb];
+    cbg_split* sp_tmp = at<cbg_split>(problems[i].state, L.o_gsplit);
+    double* v_tmp = at<double>(problems[i].state, L.o_gvals);
+    unsigned* counter = reinterpret_cast<unsigned*>(at<char>(problems[i].state, L.o_gsplit) + sizeof(cbg_split) * MAX_DEPTH);
+    st = boost_one_tree(ctx, &args[i], sp_tmp, v_tmp);
+    if (st != CBG_OK) break;
+    record_tree_kernel<<<1, 256, 0, ctx->stream>>>(sp_tmp, v_tmp, depth, problems[i].splits, problems[i].leaf_values,
+                                                   counter, trees);
+    if (cudaGetLastError() != cudaSuccess) st = fail(ctx, CBG_ECUDA, "record kernel launch failed during capture");
+  }
+  for (int b = 0; b < nb && st == CBG_OK; ++b) {
+    ce = cudaEventRecord(ctx->branch_events[b], ctx->branch_streams[b]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(origin, ctx->branch_events[b], 0);
+    if (ce != cudaSuccess) st = fail(ctx, CBG_ECUDA, "joining the batched round failed: %s", cudaGetErrorString(ce));
+  }
+  ctx->stream = origin;
+  ce = cudaStreamEndCapture(origin, &graph);
+  ctx->stream = user_stream;
+  if (st != CBG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ce != cudaSuccess) return fail(ctx, CBG_ECUDA, "capture of the batched round failed: %s", cudaGetErrorString(ce));
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return fail(ctx, CBG_ECUDA, "instantiating the batched round failed: %s", cudaGetErrorString(ce));
+  for (int t = 0; t < trees; ++t) {
+    ce = cudaGraphLaunch(exec, user_stream);
+    if (ce != cudaSuccess) break;
+  }
+  cudaGraphExecDestroy(exec);
+  if (ce != cudaSuccess) return fail(ctx, CBG_ECUDA, "batched round launch failed: %s", cudaGetErrorString(ce));
   return CBG_OK;
 }
 

@@ -140,3 +140,31 @@ def grouped_from_rowmajor(bins_rm: np.ndarray) -> np.ndarray:
 
 def rowmajor_from_grouped(flat: np.ndarray, n: int, F_pad: int) -> np.ndarray:
     return np.ascontiguousarray(flat.reshape(F_pad // 32, n, 32).transpose(1, 0, 2)).reshape(n, F_pad)
+
+
+def fit_batched(ctx: cbg.Context, preps, ys, losses, depth: int, trees: int, lr: float, l2: float,
+                gh_dtype: str = "f32", tiles: dict | None = None, branches: int = 0):
+    """Boost many independent problems together (cbg_boost_batched): one captured graph per
+    round of trees, with the problems on parallel branches. Returns one Model per problem."""
+    bufs = [alloc_fit(p, depth, trees, gh_dtype, tiles) for p in preps]
+    probs = []
+    for p, b, y, loss in zip(preps, bufs, ys, losses):
+        pr = cbg.Problem()
+        pr.shape = b.shape
+        pr.state = b.state.data_ptr()
+        pr.state_bytes = b.state.numel()
+        pr.bins = p.bins.data_ptr()
+        pr.bins_t = p.bins_t.data_ptr() if p.bins_t is not None else None
+        pr.n_borders = p.n_borders.data_ptr()
+        pr.y = y.data_ptr()
+        pr.loss = cbg.LOSS[loss]
+        pr.pred = b.pred.data_ptr()
+        pr.g = b.g.data_ptr()
+        pr.h = b.h.data_ptr()
+        pr.leaf = b.leaf.data_ptr()
+        pr.splits = b.splits.data_ptr()
+        pr.leaf_values = b.leaf_values.data_ptr()
+        pr.child_totals = b.child_totals.data_ptr()
+        probs.append(pr)
+    cbg.cbg_boost_batched(ctx, probs, gh_dtype, depth, trees, lr, l2, branches)
+    return [Model(b.splits[:trees], b.leaf_values[:trees], b.pred, depth, lr) for b in bufs], bufs

@@ -280,3 +280,62 @@ def test_invalid_level_arguments_are_rejected(ctx):
     with pytest.raises(cbg.CbgError) as e:
         cbg.cbg_build_level(ctx, t.shape, small, t.bins, t.nb, t.g, t.h, "f32", 0, 3.0, t.leaf, t.splits, t.child)
     assert e.value.status == cbg.CBG_ENOMEM
+
+
+def test_batched_matches_problem_by_problem(ctx):
+    """cbg_boost_batched on uneven problems (both losses, with and without categoricals)
+    gives the same trees and predictions as cbg_boost on each problem alone, and both
+    match the oracle up to its first near-tie."""
+    ws = synth.batched_256(n_problems=6, n_max=20000, trees=8)
+    preps, ys = [], []
+    for w in ws:
+        cat = to_dev(w.cat) if w.n_cat else None
+        if cat is None:
+            import torch
+            cat = torch.zeros((0, w.n), dtype=torch.int32, device="cuda")
+        preps.append(train.preprocess(ctx, to_dev(w.x), cat, to_dev(w.y), w.label_kind, w.max_borders, a=w.a,
+                                      seed=w.seed))
+        ys.append(to_dev(w.y))
+    depth, trees, lr, l2 = 6, 8, 0.1, 3.0
+    models, _ = train.fit_batched(ctx, preps, ys, [w.loss for w in ws], depth, trees, lr, l2, branches=4)
+    cbg.cbg_sync(ctx)
+    for i, (w, p, y) in enumerate(zip(ws, preps, ys)):
+        alone = train.fit(ctx, p, y, w.loss, depth, trees, lr, l2, use_graph=True)
+        cbg.cbg_sync(ctx)
+        a_sp, b_sp = alone.host_splits(), models[i].host_splits()
+        assert np.array_equal(a_sp["feature"], b_sp["feature"]), i
+        assert np.array_equal(a_sp["border"], b_sp["border"]), i
+        assert np.allclose(to_host(alone.pred), to_host(models[i].pred), rtol=0, atol=1e-6), i
+        ref_prep = oracle.preprocess(w, p.F_pad)
+        res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, depth, trees, lr, l2)
+        compared, _ = _compare_fit(res, b_sp, to_host(models[i].pred), trees, depth)
+        assert compared >= depth, i
+
+
+@pytest.mark.parametrize("case", [LEVEL_CASES[0], LEVEL_CASES[3], LEVEL_CASES[5]])
+@pytest.mark.parametrize("cluster", [1, 4])
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_histogram_kernel_variants_match_oracle(ctx, case, cluster, kernel):
+    """The other histogram kernels -- warp-private without atomics (tiles.kernel = 2) and
+    64-bit compare-and-swap on interleaved (G, H) (tiles.kernel = 3) -- with and without
+    thread-block clusters, on forced levels against the oracle."""
+    n, F, F_pad, max_bins, depth, intg, dtype, bt = case
+    bins, nb, g, h, forced = synth.random_level_case(n + F + 7, n, F, F_pad, max_bins, depth, integer_grads=intg)
+    if dtype == "bf16":
+        g, h = _bf16(g), _bf16(h)
+    t = Tree(ctx, bins, nb, g, h, depth, dtype, tiles={"kernel": kernel, "cluster": cluster}, with_bins_t=bt)
+    g64, h64 = g.astype(np.float64), h.astype(np.float64)
+    leaf = np.zeros(n, np.uint16)
+    root_abs = None
+    for d in range(depth):
+        hist, sf, sk, _, gl, _ = t.level(d, 3.0, force=forced[d], last=(d == depth - 1))
+        ref = oracle.histogram(bins, F, g64, h64, leaf, 1 << d, t.max_bins)
+        ref_abs = oracle.histogram(bins, F, np.abs(g64), np.abs(h64), leaf, 1 << d, t.max_bins)
+        if root_abs is None:
+            root_abs = ref_abs[0]
+        if intg:
+            assert np.array_equal(hist, ref), d
+        else:
+            assert hist_tolerance_ok(hist, ref, np.maximum(ref_abs, root_abs[None])), d
+        leaf = oracle.update_leaf(bins, forced[d][0], forced[d][1], d, leaf)
+        assert np.array_equal(gl, leaf), d
