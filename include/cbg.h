@@ -307,6 +307,35 @@ typedef struct cbg_problem {
 cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t n_problems, int32_t gh_dtype,
                              int32_t depth, int32_t trees, double lr, double l2, int32_t branches);
 
+/* ---------------------------------------------------- allocation-free ---- */
+
+/* Histogram of the root leaf (every row) without allocating anything; the paper
+ * has no counterpart of this call. It is for callers that cannot allocate device
+ * memory: code running inside a host application that owns the whole device
+ * memory budget (a framework's caching allocator or a fixed arena) and plugin
+ * code that may not call cudaMalloc. cbg_build_level needs a caller-allocated
+ * tree state; this call needs only its inputs and its output and makes no
+ * cudaMalloc, cudaFree or other allocating call.
+ *
+ * Result: hist_out (device double [F][max_bins][2]) holds, for every feature f
+ * and bin b, the FP64 sums of g and h over all rows whose bin of f is b, the
+ * same values cbg_build_level writes to hist_out at depth 0. bins, g, h are as
+ * for cbg_build_level (grouped bins layout; g, h of gh_dtype).
+ *
+ * Scratch: a file-scope device array of 16 MiB (the work plan and the FP32
+ * partial histograms), held by every GPU that loads the library until the
+ * process exits. One work unit needs F_pad/32 * max_bins * 256 bytes, so
+ * F_pad * max_bins beyond about 2 million is rejected with CBG_EINVAL; larger n
+ * only makes each unit longer. The first call on a device looks up the array's
+ * device address (once per device, with that device current): make that first
+ * call before any stream capture. Every call shares the array and overwrites
+ * what the previous call left there, so calls that can overlap on the GPU (on
+ * different streams, or from different contexts on the same device) race: order
+ * them on one stream or serialise them. */
+cbg_status cbg_histogram_noalloc(cbg_ctx* ctx, const uint8_t* bins, int64_t n, int32_t F, int32_t F_pad,
+                                 int32_t max_bins, const void* g, const void* h, int32_t gh_dtype,
+                                 double* hist_out);
+
 /* ------------------------------------------------------------ profiling ---- */
 
 /* Device-time accounting of the histogram kernel: while enabled, a pair of CUDA

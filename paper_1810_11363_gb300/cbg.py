@@ -95,6 +95,7 @@ SIGNATURES = {
     "cbg_apply_tree": (c_i32, [c_vp, C.POINTER(ApplyArgs)]),
     "cbg_boost": (c_i32, [c_vp, C.POINTER(BoostArgs)]),
     "cbg_boost_batched": (c_i32, [c_vp, C.POINTER(Problem), c_i32, c_i32, c_i32, c_i32, c_f64, c_f64, c_i32]),
+    "cbg_histogram_noalloc": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_vp, c_vp, c_i32, c_vp]),
     "cbg_profile_enable": (c_i32, [c_vp, C.c_int]),
     "cbg_profile_read": (c_i32, [c_vp, C.c_int, C.POINTER(c_f64), C.POINTER(c_i64)]),
     "cbg_tree_rows_histogrammed": (c_i32, [c_vp, C.POINTER(TreeShape), c_vp, C.c_int, C.POINTER(c_i64)]),
@@ -274,6 +275,13 @@ def cbg_tree_rows_histogrammed(ctx: Context, shape: TreeShape, state, reset: boo
               "cbg_tree_rows_histogrammed")
     return int(rows.value)
 
+
+def cbg_histogram_noalloc(ctx: Context, bins, n: int, F: int, F_pad: int, max_bins: int, g, h, gh_dtype: str,
+                          hist_out):
+    """Root-leaf FP64 histogram into hist_out [F][max_bins][2] without any device allocation
+    (scratch is a fixed 16 MiB device array inside the library; see include/cbg.h)."""
+    ctx.check(ctx.lib.cbg_histogram_noalloc(ctx.h, _p(bins), n, F, F_pad, max_bins, _p(g), _p(h), DTYPE[gh_dtype],
+                                            _p(hist_out)), "cbg_histogram_noalloc")
 
 
 def cbg_boost_batched(ctx: Context, problems, gh_dtype: str, depth: int, trees: int, lr: float, l2: float,
