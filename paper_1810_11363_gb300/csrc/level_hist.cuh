@@ -45,14 +45,18 @@ struct HistConfig {
 
 // Warps per CTA of the warp-private kernel: as many (G, H) float2 histograms of
 // max_bins x 32 as fit in one SM's shared memory, at most 16.
+// Every warp of the warp-private kernel holds a (G, H) float2 histogram of 16 features x
+// max_bins; warps come in pairs (the two halves of a 32-feature group).
+constexpr int WP_FEATS = 16;
 inline int wp_warps(int max_bins, int requested_threads) {
-  const int fit = static_cast<int>((227 * 1024) / (static_cast<size_t>(max_bins) * GROUP * sizeof(float2)));
+  const int fit = static_cast<int>((227 * 1024) / (static_cast<size_t>(max_bins) * WP_FEATS * sizeof(float2)));
   int w = fit < 16 ? fit : 16;
   if (requested_threads > 0 && requested_threads / 32 < w) w = requested_threads / 32;
-  return w < 1 ? 1 : w;
+  w &= ~1;
+  return w < 2 ? 2 : w;
 }
 inline size_t wp_smem_bytes(int max_bins, int warps) {
-  return static_cast<size_t>(warps) * max_bins * GROUP * sizeof(float2);
+  return static_cast<size_t>(warps) * max_bins * WP_FEATS * sizeof(float2);
 }
 
 // ------------------------------------------------------------------ histogram
@@ -183,18 +187,22 @@ __global__ void __launch_bounds__(512, 3) level_hist_kernel(const uint8_t* __res
   }
 }
 
-// Warp-private histogram, no atomics (the paper's Section 4 idea of per-warp partial
-// histograms updated without atomic operations). Lane f of every warp owns feature f of
-// the 32-feature group: its column of a (G, H) float2 histogram [max_bins][32] private
-// to the warp, so a plain shared load, add and store per update is race-free and the 32
-// lanes always hit 32 different columns (different banks). A warp walks rows in blocks
-// of 32: lane i fetches the row id and (g, h) of row i, then every lane fetches its own
-// feature's bin byte of the 32 rows (one 32-byte sector per row); loads run two blocks
-// ahead of the updates. Updates go in batches of 4 rows: equal bins within a batch are
-// merged in registers first, so the batch's 4 read-modify-writes are independent. Rows
-// of the unit are split among the CTA's warps and the cs CTAs of a cluster; at the end
-// CTA r sums its slice of bins over every warp of every CTA of the cluster (distributed
-// shared memory) into the unit's FP32 partial.
+// Warp-private histogram, no atomics (the paper's Section 4 scheme: per-warp partial
+// histograms of a few features, updated without atomic operations; here 16 features and
+// two rows per warp instruction). A warp owns half of a 32-feature group: a (G, H) float2
+// histogram [max_bins][16] in shared memory that no other warp touches. Lane (r, f)
+// handles feature f of row 2p + r of each row pair p, so one instruction updates 32
+// (row, feature) cells with plain shared loads and stores. The two lanes of a feature
+// may hit the same bin: the r = 1 lane then hands its (g, h) to the r = 0 lane (one
+// shuffle) and skips, so the 32 addresses of an instruction are distinct and the
+// update is race-free; successive row pairs are ordered by the warp's program order.
+// Both lanes of a feature share a bank pair, but a 64-bit access is served per half
+// warp, so there is no conflict. A warp walks rows in blocks of 32: lane i fetches the
+// row id and (g, h) of row i, every lane its feature's bin byte of its 16 rows; the bytes
+// of the next block are in flight while the current block is applied. Warp 2s + h takes
+// half h of the group on the s-th share of the CTA's rows; the CTAs of a cluster split
+// the unit's rows, and at the end CTA r sums its slice of bins over every warp of every
+// CTA of the cluster (distributed shared memory) into the unit's FP32 partial.
 template <typename GH>
 __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __restrict__ bins, int64_t n, int G,
                                                                int F, const uint32_t* __restrict__ order,
@@ -202,7 +210,7 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
                                                                const Plan* __restrict__ plan, int max_bins,
                                                                float* __restrict__ partials) {
   namespace cgr = cooperative_groups;
-  extern __shared__ __align__(16) float2 wsh[];   // [W][max_bins][32]
+  extern __shared__ __align__(16) float2 wsh[];   // [W][max_bins][16]
   constexpr int MAX_CS = 16;
   constexpr unsigned FULL = 0xffffffffu;
   cgr::cluster_group cl = cgr::this_cluster();
@@ -210,11 +218,13 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
   const int rank = static_cast<int>(cl.block_rank());
   const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const int per_warp = max_bins * GROUP;
+  const int half = warp & 1, share = warp >> 1, shares = W >> 1;
+  const int r = lane >> 4, f = lane & 15;
+  const int per_warp = max_bins * WP_FEATS;
   float2* my = wsh + static_cast<int64_t>(warp) * per_warp;
   const int maxb1 = max_bins - 1;
   const float2* peer[MAX_CS];
-  for (int r = 0; r < cs && r < MAX_CS; ++r) peer[r] = cl.map_shared_rank(wsh, r);
+  for (int c = 0; c < cs && c < MAX_CS; ++c) peer[c] = cl.map_shared_rank(wsh, c);
   const int total_items = plan->total_units * G;
   const int n_small = plan->n_small;
   for (int item = cid; item < total_items; item += ncl) {
@@ -233,10 +243,10 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
     for (int i = lane; i < per_warp; i += 32) my[i] = make_float2(0.f, 0.f);
     __syncwarp();
     const int nblk = p1 > p0 ? (p1 - p0 + 31) / 32 : 0;
-    const uint8_t* gb = bins + static_cast<int64_t>(grp) * n * GROUP + lane;
-    // block k of this warp is block warp + k*W of the CTA's rows
+    const bool active = grp * GROUP + half * WP_FEATS < F;   // a half holding only padding is skipped
+    const uint8_t* gb = bins + static_cast<int64_t>(grp) * n * GROUP + half * WP_FEATS + f;
     auto load_rows = [&](int k, uint32_t& row, float& gv, float& hv) {
-      const int blk = warp + k * W;
+      const int blk = share + k * shares;
       const int pos = p0 + blk * 32 + lane;
       if (blk < nblk && pos < p1) {
         row = order ? order[pos] : static_cast<uint32_t>(pos);
@@ -248,63 +258,52 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
         hv = 0.f;
       }
     };
-    // The 32 bytes stay unpacked in registers until the next block is processed, so the
-    // issuing warp never waits on these loads before it has work for them.
-    auto load_bins = [&](uint32_t row_lane, uint8_t (&raw)[32]) {
+    auto load_bins = [&](uint32_t row_lane, uint8_t (&raw)[16]) {
 #pragma unroll
-      for (int r = 0; r < 32; ++r) {
-        const uint32_t rr = __shfl_sync(FULL, row_lane, r);
-        raw[r] = __ldg(gb + static_cast<int64_t>(rr) * GROUP);
+      for (int p = 0; p < 16; ++p) {
+        const uint32_t rr = __shfl_sync(FULL, row_lane, 2 * p + r);
+        raw[p] = __ldg(gb + static_cast<int64_t>(rr) * GROUP);
       }
     };
-    auto process = [&](const uint8_t (&raw)[32], float gv, float hv) {
+    auto process = [&](const uint8_t (&raw)[16], float gl, float hl) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int b0 = min(static_cast<int>(raw[4 * q]), maxb1);
-        const int b1 = min(static_cast<int>(raw[4 * q + 1]), maxb1);
-        const int b2 = min(static_cast<int>(raw[4 * q + 2]), maxb1);
-        const int b3 = min(static_cast<int>(raw[4 * q + 3]), maxb1);
-        float g0 = __shfl_sync(FULL, gv, 4 * q), g1 = __shfl_sync(FULL, gv, 4 * q + 1);
-        float g2 = __shfl_sync(FULL, gv, 4 * q + 2), g3 = __shfl_sync(FULL, gv, 4 * q + 3);
-        float h0 = __shfl_sync(FULL, hv, 4 * q), h1 = __shfl_sync(FULL, hv, 4 * q + 1);
-        float h2 = __shfl_sync(FULL, hv, 4 * q + 2), h3 = __shfl_sync(FULL, hv, 4 * q + 3);
-        bool v1 = true, v2 = true, v3 = true;
-        if (b1 == b0) { g0 += g1; h0 += h1; v1 = false; }
-        if (b2 == b0) { g0 += g2; h0 += h2; v2 = false; }
-        else if (b2 == b1) { g1 += g2; h1 += h2; v2 = false; }
-        if (b3 == b0) { g0 += g3; h0 += h3; v3 = false; }
-        else if (b3 == b1) { g1 += g3; h1 += h3; v3 = false; }
-        else if (b3 == b2) { g2 += g3; h2 += h3; v3 = false; }
-        float2* a0 = my + b0 * GROUP + lane;
-        float2* a1 = my + b1 * GROUP + lane;
-        float2* a2 = my + b2 * GROUP + lane;
-        float2* a3 = my + b3 * GROUP + lane;
-        // all loads before all stores: the valid addresses of a batch are distinct
-        float2 o0 = *a0;
-        float2 o1 = v1 ? *a1 : make_float2(0.f, 0.f);
-        float2 o2 = v2 ? *a2 : make_float2(0.f, 0.f);
-        float2 o3 = v3 ? *a3 : make_float2(0.f, 0.f);
-        o0.x += g0; o0.y += h0;
-        *a0 = o0;
-        if (v1) { o1.x += g1; o1.y += h1; *a1 = o1; }
-        if (v2) { o2.x += g2; o2.y += h2; *a2 = o2; }
-        if (v3) { o3.x += g3; o3.y += h3; *a3 = o3; }
+      for (int p = 0; p < 16; ++p) {
+        const int b = min(static_cast<int>(raw[p]), maxb1);
+        const int bp = __shfl_xor_sync(FULL, b, 16);
+        float gv = __shfl_sync(FULL, gl, 2 * p + r);
+        float hv = __shfl_sync(FULL, hl, 2 * p + r);
+        const float gp = __shfl_xor_sync(FULL, gv, 16);
+        const float hp = __shfl_xor_sync(FULL, hv, 16);
+        const bool dup = b == bp;
+        if (dup && r == 0) {
+          gv += gp;
+          hv += hp;
+        }
+        if (!(dup && r == 1)) {
+          float2* a = my + b * WP_FEATS + f;
+          float2 o = *a;
+          o.x += gv;
+          o.y += hv;
+          *a = o;
+        }
       }
     };
-    const int my_blocks = nblk > warp ? (nblk - warp + W - 1) / W : 0;
-    uint32_t rowA, rowB, rowC;
-    float gA, hA, gB, hB, gC, hC;
-    uint8_t rawA[32], rawB[32];
-    load_rows(0, rowA, gA, hA);
-    load_rows(1, rowB, gB, hB);
-    load_bins(rowA, rawA);
-    for (int k = 0; k < my_blocks; ++k) {
-      load_rows(k + 2, rowC, gC, hC);
-      if (k + 1 < my_blocks) load_bins(rowB, rawB);
-      process(rawA, gA, hA);
+    const int my_blocks = nblk > share ? (nblk - share + shares - 1) / shares : 0;
+    if (active && my_blocks > 0) {
+      uint32_t rowA, rowB, rowC;
+      float gA, hA, gB, hB, gC, hC;
+      uint8_t rawA[16], rawB[16];
+      load_rows(0, rowA, gA, hA);
+      load_rows(1, rowB, gB, hB);
+      load_bins(rowA, rawA);
+      for (int k = 0; k < my_blocks; ++k) {
+        load_rows(k + 2, rowC, gC, hC);
+        if (k + 1 < my_blocks) load_bins(rowB, rawB);
+        process(rawA, gA, hA);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) rawA[i] = rawB[i];
-      gA = gB; hA = hB; rowB = rowC; gB = gC; hB = hC;
+        for (int i = 0; i < 16; ++i) rawA[i] = rawB[i];
+        gA = gB; hA = hB; rowB = rowC; gB = gC; hB = hC;
+      }
     }
     cl.sync();
     const int bs = (max_bins + cs - 1) / cs;
@@ -312,16 +311,18 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
     const int nbs = max(0, min(max_bins, b0 + bs) - b0);
     float* dst = partials + static_cast<int64_t>(item) * (2 * max_bins * GROUP);
     for (int i = threadIdx.x; i < nbs * GROUP; i += blockDim.x) {
-      const int e = b0 * GROUP + i;
+      const int b = b0 + i / GROUP, f32 = i % GROUP;
+      const int hw = f32 / WP_FEATS, fl = f32 % WP_FEATS;
+      const int64_t e = static_cast<int64_t>(b) * WP_FEATS + fl;
       float sx = 0.f, sy = 0.f;
-      for (int r = 0; r < cs; ++r)
-        for (int w = 0; w < W; ++w) {
-          const float2 v = peer[r][static_cast<int64_t>(w) * per_warp + e];
+      for (int c = 0; c < cs; ++c)
+        for (int sh = 0; sh < shares; ++sh) {
+          const float2 v = peer[c][static_cast<int64_t>(2 * sh + hw) * per_warp + e];
           sx += v.x;
           sy += v.y;
         }
-      dst[e] = sx;
-      dst[max_bins * GROUP + e] = sy;
+      dst[b * GROUP + f32] = sx;
+      dst[max_bins * GROUP + b * GROUP + f32] = sy;
     }
     cl.sync();
   }
