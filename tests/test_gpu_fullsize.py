@@ -1,0 +1,135 @@
+"""Full-size parity of the dense (400k x 2000, 129 bins, depth 8) and precision
+(10M x 70, depth 10, BF16 gradients) workloads on outputs the oracle computes on its
+own: the permutation, ordered TS of sampled categorical columns, borders and bins of
+sampled features, the FP64 root histogram of sampled features, and whole trees
+against the same oracle on a row sample."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import hist_tolerance_ok, to_dev, to_host
+from paper_1810_11363_gb300 import cbg, synth, train
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = cbg.Context(0)
+    yield c
+    c.close()
+
+
+def _root_hist(ctx, prep, g, h, dtype):
+    """Depth-0 FP64 histogram of the GPU's own bins through cbg_build_level."""
+    import torch
+    shape = cbg.make_shape(prep.n, prep.F, prep.F_pad, prep.max_bins, 1)
+    state = torch.empty(cbg.cbg_tree_state_bytes(shape), dtype=torch.uint8, device="cuda")
+    leaf = torch.empty(prep.n, dtype=torch.int16, device="cuda")
+    splits = torch.empty((1, 2), dtype=torch.float64, device="cuda")
+    child = torch.empty((2, 2), dtype=torch.float64, device="cuda")
+    hist = torch.empty((1, prep.F, prep.max_bins, 2), dtype=torch.float64, device="cuda")
+    cbg.cbg_tree_begin(ctx, shape, state, leaf)
+    cbg.cbg_build_level(ctx, shape, state, prep.bins, prep.n_borders, g, h, dtype, 0, 3.0, leaf, splits, child,
+                        bins_t=prep.bins_t, hist_out=hist, last_level=True)
+    cbg.cbg_sync(ctx)
+    out = to_host(hist)[0]
+    del state, hist
+    return out
+
+
+def _check_sampled_features(w, prep, cols, feats, gpu_hist, g64, h64, rows):
+    """Borders, bins (on sampled rows) and the root histogram of sampled features, each
+    recomputed by the oracle from the raw column."""
+    b_gpu = to_host(prep.borders)
+    nb_gpu = to_host(prep.n_borders)
+    bins_gpu = to_host(prep.bins_t)
+    for f in feats:
+        b_ref, nb_ref = oracle.select_borders(cols(f)[None, :], w.max_borders)
+        assert nb_gpu[f] == nb_ref[0], f
+        assert np.array_equal(b_gpu[f, :nb_ref[0]].view(np.uint32), b_ref[0, :nb_ref[0]].view(np.uint32)), f
+        bins_ref = oracle.quantize(cols(f)[None, :], b_ref, nb_ref, 32)[:, 0]
+        assert np.array_equal(bins_gpu[f, rows], bins_ref[rows]), f
+        one = np.zeros((w.n, 32), np.uint8)
+        one[:, 0] = bins_ref
+        ref = oracle.histogram(one, 1, g64, h64, None, 1, prep.max_bins)[0, 0]
+        ref_abs = oracle.histogram(one, 1, np.abs(g64), np.abs(h64), None, 1, prep.max_bins)[0, 0]
+        assert hist_tolerance_ok(gpu_hist[f], ref, ref_abs), f
+
+
+def test_dense_400k_full_size(ctx):
+    import torch
+    w = synth.dense_400k(trees=1)
+    x = to_dev(w.x)
+    cat = torch.zeros((0, w.n), dtype=torch.int32, device="cuda")
+    y = to_dev(w.y)
+    prep = train.preprocess(ctx, x, cat, y, "binary", w.max_borders, a=w.a, seed=w.seed)
+    assert np.array_equal(to_host(prep.perm, np.uint32), oracle.make_permutation(w.seed, w.n))
+    rng = np.random.default_rng(0)
+    feats = sorted(rng.choice(w.n_features, 24, replace=False).tolist())
+    rows = np.sort(rng.choice(w.n, 4096, replace=False))
+    g = torch.empty(w.n, dtype=torch.float32, device="cuda")
+    h = torch.empty(w.n, dtype=torch.float32, device="cuda")
+    pred0 = torch.zeros(w.n, dtype=torch.float32, device="cuda")
+    cbg.cbg_gradients(ctx, "logloss", y, pred0, w.n, "f32", g, h)
+    gpu_hist = _root_hist(ctx, prep, g, h, "f32")
+    g64, h64 = oracle.gradients("logloss", w.y, np.zeros(w.n), "f32")
+    _check_sampled_features(w, prep, lambda f: w.x[f], feats, gpu_hist, g64, h64, rows)
+    # one depth-8 tree on a 40k-row sample of the same shape, end to end against the oracle
+    ws = synth.dense_400k(n=40000, F=2000, seed=1, trees=2)
+    p2 = train.preprocess(ctx, to_dev(ws.x), torch.zeros((0, ws.n), dtype=torch.int32, device="cuda"),
+                          to_dev(ws.y), "binary", ws.max_borders, a=ws.a, seed=ws.seed)
+    model = train.fit(ctx, p2, to_dev(ws.y), ws.loss, ws.depth, ws.trees, ws.lr, ws.l2, use_graph=True)
+    cbg.cbg_sync(ctx)
+    ref_prep = oracle.preprocess(ws, p2.F_pad)
+    assert np.array_equal(train.rowmajor_from_grouped(to_host(p2.bins), ws.n, p2.F_pad), ref_prep["bins"])
+    res = oracle.fit(ref_prep["bins"], ws.n_features, ref_prep["n_borders"], ws.y, ws.loss, ws.depth, ws.trees,
+                     ws.lr, ws.l2)
+    sp = model.host_splits()
+    for t in range(ws.trees):
+        for d in range(ws.depth):
+            if res["score"][t, d] - res["second"][t, d] <= 1e-6 * abs(res["score"][t, d]):
+                return
+            assert (sp[t, d]["feature"], sp[t, d]["border"]) == (res["split_f"][t, d], res["split_k"][t, d]), (t, d)
+    assert np.all(np.abs(to_host(model.pred) - res["pred"]) <= 1e-4)
+
+
+def test_precision_10m_full_size(ctx):
+    import torch
+    w = synth.precision_10m(trees=1)
+    x, catd, y = to_dev(w.x), to_dev(w.cat), to_dev(w.y)
+    P = oracle.prior(w.y, "real")
+    prep = train.preprocess(ctx, x, catd, y, "real", w.max_borders, a=w.a, seed=w.seed, prior=P)
+    perm = oracle.make_permutation(w.seed, w.n)
+    assert np.array_equal(to_host(prep.perm, np.uint32), perm)
+    ts = to_host(prep.ts)
+    rng = np.random.default_rng(1)
+    for c in (0, 9, 19):                         # cardinalities 10, ~3.6e3, 1e6
+        t_ref, cnt_ref, _ = oracle.ordered_ts(w.cat[c], w.y, perm, P, w.a)
+        _, _, abs_ref = oracle.ordered_ts(w.cat[c], np.abs(w.y), perm, 0.0, w.a)
+        tol = 1e-12 * (abs_ref + abs(P)) / (cnt_ref + w.a) + np.spacing(np.abs(t_ref)).astype(np.float64)
+        assert np.all(np.abs(ts[c].astype(np.float64) - t_ref.astype(np.float64)) <= tol), c
+    feats = [0, 13, 24, 25, 37, 49] + [w.n_float + c for c in (0, 19)]
+    rows = np.sort(rng.choice(w.n, 4096, replace=False))
+    # BF16 gradients at pred 0: g = -y rounded to BF16, h = 1
+    g = torch.empty(w.n, dtype=torch.bfloat16, device="cuda")
+    h = torch.empty(w.n, dtype=torch.bfloat16, device="cuda")
+    cbg.cbg_gradients(ctx, "rmse", y, torch.zeros(w.n, dtype=torch.float32, device="cuda"), w.n, "bf16", g, h)
+    gpu_hist = _root_hist(ctx, prep, g, h, "bf16")
+    g64, h64 = oracle.gradients("rmse", w.y, np.zeros(w.n), "bf16")
+    ts_ref = {}
+
+    def col(f):
+        if f < w.n_float:
+            return w.x[f]
+        c = f - w.n_float
+        if c not in ts_ref:
+            ts_ref[c] = oracle.ordered_ts(w.cat[c], w.y, perm, P, w.a)[0]
+        return ts_ref[c]
+
+    # real-label TS may round one ulp apart; features whose borders differ are reported
+    _check_sampled_features(w, prep, col, feats[:6], gpu_hist, g64, h64, rows)
+    del x, catd, prep
+    torch.cuda.empty_cache()
