@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 METRIC = "trees/s and row·feature·bins/s at 1M×110 depth 6; HBM roofline %; batched vs plain"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "hist_kernel_traffic.txt")
-HIST_SOURCE = os.path.join(ROOT, "paper_1810_11363_gb300", "csrc", "tree.cu")
+HIST_SOURCE = os.path.join(ROOT, "paper_1810_11363_gb300", "csrc", "level_hist.cuh")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -45,10 +45,11 @@ def parse_args():
     p.add_argument("--ref-sample-trees", type=int, default=2)
     p.add_argument("--no-graph", action="store_true", help="launch every kernel from the host instead of "
                                                            "replaying one captured tree")
-    p.add_argument("--hist-kernel", choices=["wp", "red", "cas64"], default="red",
+    p.add_argument("--hist-kernel", choices=["pair", "lane", "wp", "red", "cas64"], default="red",
                    help="warp-private atomic-free histograms (wp) or shared-memory float reductions (red)")
     p.add_argument("--cluster", type=int, default=0, help="CTAs per histogram cluster (0 = library default)")
     p.add_argument("--rows-per-item", type=int, default=0, help="rows per CTA of a histogram work unit")
+    p.add_argument("--hist-threads", type=int, default=0, help="threads per histogram CTA (0 = library default)")
     p.add_argument("--batched-problems", type=int, default=64,
                    help="problems of the batched_256 workload for the batched-vs-plain comparison (0 = skip)")
     p.add_argument("--batched-trees", type=int, default=20)
@@ -281,8 +282,8 @@ def run_ours(args):
         return prep, model
 
     prep0 = train.preprocess(ctx, x, cat, y, "binary", w.max_borders, a=w.a, seed=w.seed)
-    tiles = {"kernel": {"wp": 2, "red": 1, "cas64": 3}[args.hist_kernel], "cluster": args.cluster,
-             "rows_per_item": args.rows_per_item}
+    tiles = {"kernel": {"wp": 2, "red": 1, "cas64": 3, "lane": 4, "pair": 5}[args.hist_kernel], "cluster": args.cluster,
+             "rows_per_item": args.rows_per_item, "threads": args.hist_threads}
     bufs = train.alloc_fit(prep0, D, T, args.gh, tiles=tiles)
     for _ in range(args.warmup):
         step(bufs)
@@ -338,12 +339,13 @@ def run_ours(args):
     peak, peak_kind = measured_peak_hbm()
     per_row = recorded_traffic_per_row()
     rows_per_launch = rows_hist / max(hist_launches, 1)
-    roofline = {"bound": "hbm", "kernel": "level_hist_wp_kernel" if args.hist_kernel == "wp" else "level_hist_kernel",
+    roofline = {"bound": "hbm", "kernel": {"wp": "level_hist_wp_kernel", "lane": "level_hist_lane_kernel", "pair": "level_hist_pair_kernel"}.get(
+                    args.hist_kernel, "level_hist_kernel"),
                 "kernel_variant": args.hist_kernel,
                 "achieved": achieved, "peak": peak,
                 "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": per_row * rows_per_launch if per_row else None,
+                "traffic": per_row * rows_per_launch if (per_row and args.hist_kernel == "red") else None,
                 "alg_bytes_per_launch": alg_bytes / max(hist_launches, 1),
                 "launches": hist_launches, "avg_launch_us": hist_ms * 1e3 / max(hist_launches, 1),
                 "timing": hist_timing}

@@ -73,9 +73,11 @@ typedef struct cbg_split {
  * shared memory (1..16; a smaller power of two is used if that many cannot be
  * co-resident); kernel: 1 = one shared histogram per CTA updated with
  * shared-memory float reductions (the default, 0), 2 = warp-private
- * histograms updated without atomics, 3 = one shared histogram per CTA with
- * (G, H) updated by one 64-bit compare-and-swap. Zero fields take library
- * defaults. */
+ * histograms of 16 features updated without atomics, 3 = one shared histogram
+ * per CTA with (G, H) updated by one 64-bit compare-and-swap, 4 = lane-per-
+ * feature warp-private histograms with store forwarding (bins must be 16-byte
+ * aligned), 5 = the same with G and H in separate warps. Zero fields take
+ * library defaults. */
 typedef struct cbg_tiles {
   int32_t slab_chunks;
   int32_t rows_per_item;
@@ -352,6 +354,47 @@ cbg_status cbg_profile_read(cbg_ctx* ctx, int reset, double* hist_ms, int64_t* h
  * by cbg_tree_begin. */
 cbg_status cbg_tree_rows_histogrammed(cbg_ctx* ctx, const cbg_tree_shape* shape, void* state, int reset,
                                       int64_t* rows);
+
+/* ------------------------------------------------------------ autotuner -- */
+
+/* Histogram-tile autotuner. The paper has no counterpart: it picks the tiling
+ * that the batched form (and any caller) uses for a problem shape.
+ * It times a fixed list of candidate tilings on the caller's own data, building
+ * `depth` levels of one tree per timing (cbg_tree_begin + cbg_build_level on the
+ * ctx stream, CUDA events), and writes the fastest to *best and its mean device
+ * time per tree (ms) to *best_ms. The candidates vary:
+ *  - the histogram kernel: shared-memory reductions (1), lane-per-feature warp
+ *    histograms (4) and their one-statistic-per-warp form (5), or 16-feature
+ *    warp-private histograms (2);
+ *  - CTAs per cluster;
+ *  - rows per CTA of a work unit.
+ * Ownership and layout follow cbg_build_level. args->shape->tiles is ignored.
+ * state must hold cbg_autotune_state_bytes(shape) bytes; a candidate whose state
+ * does not fit, or that the device cannot launch, is skipped. leaf, splits and
+ * child_totals are overwritten. reps >= 1 timed trees per candidate, after one
+ * untimed. Synchronises the stream. CBG_EINVAL while the stream is being
+ * captured or if no candidate ran. */
+typedef struct cbg_autotune_args {
+  const cbg_tree_shape* shape; /* host pointer; tiles ignored                 */
+  void* state;                 /* device scratch, see cbg_autotune_state_bytes */
+  size_t state_bytes;
+  const uint8_t* bins;         /* device, grouped layout, 16-byte aligned     */
+  const uint8_t* bins_t;       /* device [F][n] or NULL                       */
+  const int32_t* n_borders;    /* device int32 [F]                            */
+  const void* g;               /* device [n] (gh_dtype)                       */
+  const void* h;
+  int32_t gh_dtype;
+  int32_t depth;               /* levels per timed tree, 1..max_depth          */
+  double l2;
+  uint16_t* leaf;              /* device [n] scratch                          */
+  cbg_split* splits;           /* device [max_depth] scratch                  */
+  double* child_totals;        /* device [2^depth][2] scratch                 */
+  int32_t reps;
+} cbg_autotune_args;
+
+/* Tree-state bytes large enough for every autotuner candidate of `shape`. */
+cbg_status cbg_autotune_state_bytes(const cbg_tree_shape* shape, size_t* bytes);
+cbg_status cbg_autotune_tiles(cbg_ctx* ctx, const cbg_autotune_args* args, cbg_tiles* best, double* best_ms);
 
 #ifdef __cplusplus
 }

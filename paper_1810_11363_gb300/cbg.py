@@ -44,6 +44,13 @@ class TreeShape(C.Structure):
                 ("tiles", Tiles)]
 
 
+class AutotuneArgs(C.Structure):
+    _fields_ = [("shape", C.POINTER(TreeShape)), ("state", c_vp), ("state_bytes", C.c_size_t),
+                ("bins", c_vp), ("bins_t", c_vp), ("n_borders", c_vp), ("g", c_vp), ("h", c_vp),
+                ("gh_dtype", c_i32), ("depth", c_i32), ("l2", c_f64), ("leaf", c_vp), ("splits", c_vp),
+                ("child_totals", c_vp), ("reps", c_i32)]
+
+
 class LevelArgs(C.Structure):
     _fields_ = [("shape", C.POINTER(TreeShape)), ("state", c_vp), ("state_bytes", C.c_size_t),
                 ("bins", c_vp), ("bins_t", c_vp), ("n_borders", c_vp), ("g", c_vp), ("h", c_vp),
@@ -99,6 +106,8 @@ SIGNATURES = {
     "cbg_profile_enable": (c_i32, [c_vp, C.c_int]),
     "cbg_profile_read": (c_i32, [c_vp, C.c_int, C.POINTER(c_f64), C.POINTER(c_i64)]),
     "cbg_tree_rows_histogrammed": (c_i32, [c_vp, C.POINTER(TreeShape), c_vp, C.c_int, C.POINTER(c_i64)]),
+    "cbg_autotune_state_bytes": (c_i32, [C.POINTER(TreeShape), C.POINTER(C.c_size_t)]),
+    "cbg_autotune_tiles": (c_i32, [c_vp, C.POINTER(AutotuneArgs), C.POINTER(Tiles), C.POINTER(c_f64)]),
 }
 
 _lock = threading.Lock()
@@ -274,6 +283,27 @@ def cbg_tree_rows_histogrammed(ctx: Context, shape: TreeShape, state, reset: boo
     ctx.check(ctx.lib.cbg_tree_rows_histogrammed(ctx.h, C.byref(shape), _p(state), int(reset), C.byref(rows)),
               "cbg_tree_rows_histogrammed")
     return int(rows.value)
+
+
+def cbg_autotune_state_bytes(shape: TreeShape) -> int:
+    out = C.c_size_t()
+    st = load().cbg_autotune_state_bytes(C.byref(shape), C.byref(out))
+    if st != CBG_OK:
+        raise CbgError(st, "cbg_autotune_state_bytes: invalid shape")
+    return int(out.value)
+
+
+def cbg_autotune_tiles(ctx: Context, shape: TreeShape, state, bins, n_borders, g, h, gh_dtype: str, depth: int,
+                       l2: float, leaf, splits, child_totals, bins_t=None, reps: int = 2):
+    """Fastest histogram tiling for this problem (dict of cbg_tiles fields) and its device
+    time per tree in ms."""
+    a = AutotuneArgs(C.pointer(shape), _p(state), state.numel() * state.element_size(), _p(bins), _p(bins_t),
+                     _p(n_borders), _p(g), _p(h), DTYPE[gh_dtype], depth, l2, _p(leaf), _p(splits),
+                     _p(child_totals), reps)
+    best = Tiles()
+    ms = c_f64()
+    ctx.check(ctx.lib.cbg_autotune_tiles(ctx.h, C.byref(a), C.byref(best), C.byref(ms)), "cbg_autotune_tiles")
+    return {f: getattr(best, f) for f, _ in Tiles._fields_}, float(ms.value)
 
 
 def cbg_histogram_noalloc(ctx: Context, bins, n: int, F: int, F_pad: int, max_bins: int, g, h, gh_dtype: str,

@@ -36,8 +36,10 @@ struct Plan {
 size_t hist_smem_bytes(int nb_alloc) { return static_cast<size_t>(2) * nb_alloc * GROUP * sizeof(float); }
 
 // What the histogram launch needs to know about a problem. kind 0: warp-private
-// histograms without atomics (default); kind 1: one shared histogram per CTA updated with
-// shared-memory float reductions.
+// histograms of 16 features per warp; kind 1: one shared histogram per CTA updated with
+// shared-memory float reductions; kind 3: the same with 64-bit compare-and-swap; kind 4:
+// lane-per-feature warp histograms with store forwarding; kind 5: the same with G and H
+// in separate warps. Kinds 4 and 5 read (g, h) by position, the others by row.
 struct HistConfig {
   int64_t n;
   int G, F, max_bins, nb_alloc, threads, cluster, kind = 0;
@@ -328,14 +330,426 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
   }
 }
 
+// ------------------------------------------- lane-per-feature warp histograms
+// The warp-private scheme of the paper's Section 4 with one feature per lane: a warp owns
+// the (G, H) float2 histogram [max_bins][32] of one 32-feature group, and lane f updates
+// column f for every row, so the 32 addresses of an update are always distinct and no
+// atomics are needed. Rows come in blocks of 32 staged in shared memory: lane i fetches
+// the row id and the position-ordered (g, h) of row i four blocks ahead and copies the
+// row's 32-byte bin record with cp.async two blocks ahead. Within a block the histogram
+// load of row i + 2 is issued before the stores of rows i and i + 1; if its bin equals
+// one of theirs, the value just stored replaces the stale load (store-to-load forwarding
+// in registers), so the 30-cycle shared-memory round trip is off the critical path.
+// A 255-bin warp histogram is 64 KB, so an SM holds 3 such warps; the unrolled block
+// and the forwarding give each warp the instruction-level parallelism it needs.
+// At the end of a work unit the warps of a CTA are summed into warp 0's histogram, and
+// CTA r of the cluster sums its slice of bins over the cluster (distributed shared
+// memory) into the unit's FP32 partial.
+constexpr int LH_ROWS = 32;       // rows per block: one per lane for row ids and (g, h)
+constexpr int LH_STAGES = 3;      // bin-record buffers per warp: blocks j, j + 1, j + 2
+constexpr int LH_AHEAD = 4;       // blocks of lookahead for row ids and (g, h)
+constexpr int LH_MAX_WARPS = 16;
+constexpr int LH_FWD = 3;         // rows between a histogram load and its use
+
+// Histogram accesses of the lane kernel. Volatile keeps them in program order among
+// themselves (a load issued ahead of a store to the same cell must stay ahead of it, the
+// forwarding relies on that); without a memory clobber the staging-buffer loads around
+// them remain free to be scheduled early.
+__device__ __forceinline__ float2 lds_f2(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts_f2(uint32_t addr, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y));
+}
+
+inline size_t lh_warp_bytes(int max_bins) {
+  return static_cast<size_t>(max_bins) * GROUP * sizeof(float2) + static_cast<size_t>(LH_STAGES) * LH_ROWS * GROUP +
+         LH_ROWS * sizeof(float2);
+}
+inline int lh_warps(int max_bins, int requested_threads) {
+  int w = static_cast<int>((227 * 1024) / lh_warp_bytes(max_bins));
+  if (w > LH_MAX_WARPS) w = LH_MAX_WARPS;
+  if (requested_threads > 0 && requested_threads / 32 < w) w = requested_threads / 32;
+  return w < 1 ? 1 : w;
+}
+inline size_t lh_smem_bytes(int max_bins, int warps) { return static_cast<size_t>(warps) * lh_warp_bytes(max_bins); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename GH>
+__global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
+    level_hist_lane_kernel(const uint8_t* __restrict__ bins, int64_t n, int G, int F, const uint32_t* __restrict__ order,
+                           const GH* __restrict__ gpos, const GH* __restrict__ hpos, const Plan* __restrict__ plan,
+                           int max_bins, float* __restrict__ partials) {
+  namespace cgr = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char lsh[];
+  constexpr int MAX_CS = 16;
+  constexpr uint32_t NONE = 0xffffffffu;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int cs = static_cast<int>(cl.num_blocks());
+  const int rank = static_cast<int>(cl.block_rank());
+  const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int per_warp = max_bins * GROUP;   // float2 cells of one warp histogram
+  float2* hist_all = reinterpret_cast<float2*>(lsh);
+  float2* my = hist_all + static_cast<int64_t>(warp) * per_warp;
+  unsigned char* stages = lsh + static_cast<size_t>(W) * per_warp * sizeof(float2);
+  unsigned char* my_stage = stages + static_cast<size_t>(warp) * LH_STAGES * LH_ROWS * GROUP;
+  float2* my_gh = reinterpret_cast<float2*>(stages + static_cast<size_t>(W) * LH_STAGES * LH_ROWS * GROUP) +
+                  warp * LH_ROWS;
+  const uint32_t stage_s = static_cast<uint32_t>(__cvta_generic_to_shared(my_stage));
+  const uint32_t hbase = static_cast<uint32_t>(__cvta_generic_to_shared(my + lane));
+  const int maxb1 = max_bins - 1;
+  const float2* peer0[MAX_CS];
+  for (int r = 0; r < cs && r < MAX_CS; ++r) peer0[r] = cl.map_shared_rank(hist_all, r);
+  const int total_items = plan->total_units * G;
+  const int n_small = plan->n_small;
+  for (int item = cid; item < total_items; item += ncl) {
+    const int unit = item / G, grp = item - unit * G;
+    int lo = 0, hi = n_small - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (plan->unit_begin[mid] <= unit) lo = mid; else hi = mid - 1;
+    }
+    const int jj = lo;
+    const int chunk = unit - plan->unit_begin[jj];
+    const int seg_s = plan->seg_start[jj], seg_c = plan->seg_cnt[jj];
+    const int cr = plan->chunk_rows[jj];
+    const int p0 = seg_s + (chunk * cs + rank) * cr;
+    const int p1 = min(seg_s + seg_c, p0 + cr);
+    {
+      float4* z = reinterpret_cast<float4*>(my);
+      for (int i = lane; i < per_warp / 2; i += 32) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    const int nblk = p1 > p0 ? (p1 - p0 + LH_ROWS - 1) / LH_ROWS : 0;
+    const int my_blocks = nblk > warp ? (nblk - warp + W - 1) / W : 0;
+    const bool act = lane < F - grp * GROUP;   // lanes of padding features do no updates
+    const uint8_t* gb = bins + static_cast<int64_t>(grp) * n * GROUP;
+    if (my_blocks > 0) {
+      uint32_t rid[LH_AHEAD + 1];
+      float gr[LH_AHEAD + 1], hr[LH_AHEAD + 1];
+      auto fetch = [&](int j, uint32_t& row, float& gv, float& hv) {
+        const int pos = p0 + (warp + j * W) * LH_ROWS + lane;
+        if (j < my_blocks && pos < p1) {
+          row = order ? __ldg(order + pos) : static_cast<uint32_t>(pos);
+          gv = cbgd::load_gh(gpos, pos);
+          hv = cbgd::load_gh(hpos, pos);
+        } else {
+          row = NONE;   // a row past the end: zero record, zero (g, h)
+          gv = 0.f;
+          hv = 0.f;
+        }
+      };
+      auto copy_bins = [&](int j, uint32_t row) {
+        const uint32_t dst = stage_s + static_cast<uint32_t>(((j % LH_STAGES) * LH_ROWS + lane) * GROUP);
+        if (row != NONE) {
+          const uint8_t* src = gb + static_cast<int64_t>(row) * GROUP;
+          cp_async16(dst, src);
+          cp_async16(dst + 16, src + 16);
+        } else {
+          asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n\tst.shared.v4.u32 [%2], {%1, %1, %1, %1};" ::"r"(dst),
+                       "r"(0u), "r"(dst + 16u)
+                       : "memory");
+        }
+      };
+#pragma unroll
+      for (int q = 0; q < LH_AHEAD; ++q) fetch(q, rid[q], gr[q], hr[q]);
+      copy_bins(0, rid[0]);
+      cp_async_commit();
+      if (1 < my_blocks) copy_bins(1, rid[1]);
+      cp_async_commit();
+      for (int j = 0; j < my_blocks; ++j) {
+        fetch(j + LH_AHEAD, rid[LH_AHEAD], gr[LH_AHEAD], hr[LH_AHEAD]);
+        if (j + 2 < my_blocks) copy_bins(j + 2, rid[2]);
+        cp_async_commit();
+        my_gh[lane] = make_float2(gr[0], hr[0]);
+        cp_async_wait<2>();
+        __syncwarp();
+        if (act) {
+          const unsigned char* sb = my_stage + (j % LH_STAGES) * LH_ROWS * GROUP + lane;
+          const float4* gh4 = reinterpret_cast<const float4*>(my_gh);
+          // shared-memory offsets (bytes) of the 32 rows' cells, loaded up front so that
+          // only the histogram loads remain on the chain
+          uint32_t a[LH_ROWS];
+#pragma unroll
+          for (int i = 0; i < LH_ROWS; ++i)
+            a[i] = hbase + static_cast<uint32_t>(min(static_cast<int>(sb[i * GROUP]), maxb1)) * (GROUP * 8u);
+          float2 v[LH_FWD];
+#pragma unroll
+          for (int i = 0; i < LH_FWD; ++i) v[i] = lds_f2(a[i]);
+          float2 nw[LH_FWD];   // values stored for the previous LH_FWD rows (most recent last)
+#pragma unroll
+          for (int i = 0; i < LH_ROWS; ++i) {
+            float2 nxt = make_float2(0.f, 0.f);
+            if (i + LH_FWD < LH_ROWS) nxt = lds_f2(a[i + LH_FWD]);   // before the stores of rows i .. i+LH_FWD-1
+            float2 cur = v[i % LH_FWD];
+            // the loaded value misses the stores of the previous LH_FWD rows: take the most
+            // recent one to the same cell instead
+#pragma unroll
+            for (int q = LH_FWD; q >= 1; --q)
+              if (i - q >= 0 && a[i] == a[i - q]) cur = nw[(i - q) % LH_FWD];
+            const float4 gq = gh4[i >> 1];
+            cur.x += (i & 1) ? gq.z : gq.x;
+            cur.y += (i & 1) ? gq.w : gq.y;
+            sts_f2(a[i], cur);
+            nw[i % LH_FWD] = cur;
+            v[i % LH_FWD] = nxt;
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < LH_AHEAD; ++q) {
+          rid[q] = rid[q + 1];
+          gr[q] = gr[q + 1];
+          hr[q] = hr[q + 1];
+        }
+      }
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    // the CTA's warps, summed in warp order into warp 0's histogram
+    if (W > 1) {
+      for (int e = threadIdx.x; e < per_warp; e += blockDim.x) {
+        float2 s = hist_all[e];
+        for (int w = 1; w < W; ++w) {
+          const float2 v = hist_all[static_cast<int64_t>(w) * per_warp + e];
+          s.x += v.x;
+          s.y += v.y;
+        }
+        hist_all[e] = s;
+      }
+    }
+    cl.sync();
+    // this CTA's slice of bins, summed over the cluster's CTAs in rank order
+    const int bs = (max_bins + cs - 1) / cs;
+    const int b0 = rank * bs;
+    const int nbs = max(0, min(max_bins, b0 + bs) - b0);
+    float* dst = partials + static_cast<int64_t>(item) * (2 * max_bins * GROUP);
+    for (int i = threadIdx.x; i < nbs * GROUP; i += blockDim.x) {
+      const int e = b0 * GROUP + i;
+      float sx = 0.f, sy = 0.f;
+      for (int r = 0; r < cs; ++r) {
+        const float2 v = peer0[r][e];
+        sx += v.x;
+        sy += v.y;
+      }
+      dst[e] = sx;
+      dst[max_bins * GROUP + e] = sy;
+    }
+    cl.sync();
+  }
+}
+
+// ---------------------------------------- lane-per-feature, one statistic per warp
+// The lane kernel with G and H split over a pair of warps: warp 2p accumulates G and warp
+// 2p + 1 accumulates H of the same rows, each in a private FP32 histogram [max_bins][32]
+// (32 KB at 255 bins instead of 64 KB), so twice as many warps fit on an SM to hide the
+// shared-memory latency that bounds the one-warp-per-scheduler lane kernel. Both warps of a
+// pair stage the same 32-row blocks (the second copy comes from L2); each loads only its
+// own statistic. Store forwarding and the per-unit reduction are as in the lane kernel:
+// the G warps are summed in order into warp 0, the H warps into warp 1.
+__device__ __forceinline__ float lds_f(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts_f(uint32_t addr, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v));
+}
+
+inline size_t lp_warp_bytes(int max_bins) {
+  return static_cast<size_t>(max_bins) * GROUP * sizeof(float) + static_cast<size_t>(LH_STAGES) * LH_ROWS * GROUP +
+         LH_ROWS * sizeof(float);
+}
+inline int lp_warps(int max_bins, int requested_threads) {
+  int w = static_cast<int>((227 * 1024) / lp_warp_bytes(max_bins));
+  if (w > LH_MAX_WARPS) w = LH_MAX_WARPS;
+  if (requested_threads > 0 && requested_threads / 32 < w) w = requested_threads / 32;
+  w &= ~1;
+  return w < 2 ? 2 : w;
+}
+inline size_t lp_smem_bytes(int max_bins, int warps) { return static_cast<size_t>(warps) * lp_warp_bytes(max_bins); }
+
+template <typename GH>
+__global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
+    level_hist_pair_kernel(const uint8_t* __restrict__ bins, int64_t n, int G, int F, const uint32_t* __restrict__ order,
+                           const GH* __restrict__ gpos, const GH* __restrict__ hpos, const Plan* __restrict__ plan,
+                           int max_bins, float* __restrict__ partials) {
+  namespace cgr = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char psh[];
+  constexpr int MAX_CS = 16;
+  constexpr uint32_t NONE = 0xffffffffu;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int cs = static_cast<int>(cl.num_blocks());
+  const int rank = static_cast<int>(cl.block_rank());
+  const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int pair = warp >> 1, stat = warp & 1, P = W >> 1;
+  const GH* sv = stat == 0 ? gpos : hpos;
+  const int per_warp = max_bins * GROUP;   // float cells of one warp histogram
+  float* hist_all = reinterpret_cast<float*>(psh);
+  float* my = hist_all + static_cast<int64_t>(warp) * per_warp;
+  unsigned char* stages = psh + static_cast<size_t>(W) * per_warp * sizeof(float);
+  unsigned char* my_stage = stages + static_cast<size_t>(warp) * LH_STAGES * LH_ROWS * GROUP;
+  float* my_sv = reinterpret_cast<float*>(stages + static_cast<size_t>(W) * LH_STAGES * LH_ROWS * GROUP) +
+                 warp * LH_ROWS;
+  const uint32_t stage_s = static_cast<uint32_t>(__cvta_generic_to_shared(my_stage));
+  const uint32_t hbase = static_cast<uint32_t>(__cvta_generic_to_shared(my + lane));
+  const int maxb1 = max_bins - 1;
+  const float* peer0[MAX_CS];
+  for (int r = 0; r < cs && r < MAX_CS; ++r) peer0[r] = cl.map_shared_rank(hist_all, r);
+  const int total_items = plan->total_units * G;
+  const int n_small = plan->n_small;
+  for (int item = cid; item < total_items; item += ncl) {
+    const int unit = item / G, grp = item - unit * G;
+    int lo = 0, hi = n_small - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (plan->unit_begin[mid] <= unit) lo = mid; else hi = mid - 1;
+    }
+    const int jj = lo;
+    const int chunk = unit - plan->unit_begin[jj];
+    const int seg_s = plan->seg_start[jj], seg_c = plan->seg_cnt[jj];
+    const int cr = plan->chunk_rows[jj];
+    const int p0 = seg_s + (chunk * cs + rank) * cr;
+    const int p1 = min(seg_s + seg_c, p0 + cr);
+    {
+      float4* z = reinterpret_cast<float4*>(my);
+      for (int i = lane; i < per_warp / 4; i += 32) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    const int nblk = p1 > p0 ? (p1 - p0 + LH_ROWS - 1) / LH_ROWS : 0;
+    const int my_blocks = nblk > pair ? (nblk - pair + P - 1) / P : 0;
+    const bool act = lane < F - grp * GROUP;
+    const uint8_t* gb = bins + static_cast<int64_t>(grp) * n * GROUP;
+    if (my_blocks > 0) {
+      uint32_t rid[LH_AHEAD + 1];
+      float vr[LH_AHEAD + 1];
+      auto fetch = [&](int j, uint32_t& row, float& v) {
+        const int pos = p0 + (pair + j * P) * LH_ROWS + lane;
+        if (j < my_blocks && pos < p1) {
+          row = order ? __ldg(order + pos) : static_cast<uint32_t>(pos);
+          v = cbgd::load_gh(sv, pos);
+        } else {
+          row = NONE;   // a row past the end: zero record, zero statistic
+          v = 0.f;
+        }
+      };
+      auto copy_bins = [&](int j, uint32_t row) {
+        const uint32_t dst = stage_s + static_cast<uint32_t>(((j % LH_STAGES) * LH_ROWS + lane) * GROUP);
+        if (row != NONE) {
+          const uint8_t* src = gb + static_cast<int64_t>(row) * GROUP;
+          cp_async16(dst, src);
+          cp_async16(dst + 16, src + 16);
+        } else {
+          asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n\tst.shared.v4.u32 [%2], {%1, %1, %1, %1};" ::"r"(dst),
+                       "r"(0u), "r"(dst + 16u)
+                       : "memory");
+        }
+      };
+#pragma unroll
+      for (int q = 0; q < LH_AHEAD; ++q) fetch(q, rid[q], vr[q]);
+      copy_bins(0, rid[0]);
+      cp_async_commit();
+      if (1 < my_blocks) copy_bins(1, rid[1]);
+      cp_async_commit();
+      for (int j = 0; j < my_blocks; ++j) {
+        fetch(j + LH_AHEAD, rid[LH_AHEAD], vr[LH_AHEAD]);
+        if (j + 2 < my_blocks) copy_bins(j + 2, rid[2]);
+        cp_async_commit();
+        my_sv[lane] = vr[0];
+        cp_async_wait<2>();
+        __syncwarp();
+        if (act) {
+          const unsigned char* sb = my_stage + (j % LH_STAGES) * LH_ROWS * GROUP + lane;
+          const float4* s4 = reinterpret_cast<const float4*>(my_sv);
+          uint32_t a[LH_ROWS];
+#pragma unroll
+          for (int i = 0; i < LH_ROWS; ++i)
+            a[i] = hbase + static_cast<uint32_t>(min(static_cast<int>(sb[i * GROUP]), maxb1)) * (GROUP * 4u);
+          float v[LH_FWD];
+#pragma unroll
+          for (int i = 0; i < LH_FWD; ++i) v[i] = lds_f(a[i]);
+          float nw[LH_FWD];
+#pragma unroll
+          for (int i = 0; i < LH_ROWS; ++i) {
+            float nxt = 0.f;
+            if (i + LH_FWD < LH_ROWS) nxt = lds_f(a[i + LH_FWD]);   // before the stores of rows i .. i+LH_FWD-1
+            float cur = v[i % LH_FWD];
+#pragma unroll
+            for (int q = LH_FWD; q >= 1; --q)
+              if (i - q >= 0 && a[i] == a[i - q]) cur = nw[(i - q) % LH_FWD];
+            const float4 sq = s4[i >> 2];
+            cur += (i & 3) == 0 ? sq.x : (i & 3) == 1 ? sq.y : (i & 3) == 2 ? sq.z : sq.w;
+            sts_f(a[i], cur);
+            nw[i % LH_FWD] = cur;
+            v[i % LH_FWD] = nxt;
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < LH_AHEAD; ++q) {
+          rid[q] = rid[q + 1];
+          vr[q] = vr[q + 1];
+        }
+      }
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    // G warps (even) summed in order into warp 0, H warps (odd) into warp 1
+    if (P > 1) {
+      for (int e = threadIdx.x; e < 2 * per_warp; e += blockDim.x) {
+        const int st = e / per_warp, c = e - st * per_warp;
+        float sum = hist_all[static_cast<int64_t>(st) * per_warp + c];
+        for (int q = 1; q < P; ++q) sum += hist_all[static_cast<int64_t>(2 * q + st) * per_warp + c];
+        hist_all[static_cast<int64_t>(st) * per_warp + c] = sum;
+      }
+    }
+    cl.sync();
+    // this CTA's slice of bins, summed over the cluster's CTAs in rank order
+    const int bs = (max_bins + cs - 1) / cs;
+    const int b0 = rank * bs;
+    const int nbs = max(0, min(max_bins, b0 + bs) - b0);
+    float* dst = partials + static_cast<int64_t>(item) * (2 * max_bins * GROUP);
+    for (int i = threadIdx.x; i < 2 * nbs * GROUP; i += blockDim.x) {
+      const int st = i / (nbs * GROUP), rem = i - st * (nbs * GROUP);
+      const int e = st * per_warp + b0 * GROUP + rem;
+      float sum = 0.f;
+      for (int r = 0; r < cs; ++r) sum += peer0[r][e];
+      dst[e] = sum;
+    }
+    cl.sync();
+  }
+}
+
 // ------------------------------------------------------------ reduce + subtract
 // One thread per (direct leaf jj, feature f, stat, bin): FP64 sum of the item partials,
 // written to the leaf; the sibling gets parent - direct. For the feature the parent was
 // split on, both children follow exactly from the parent (bins <= k stay in child 0, the
 // rest in child 1), so their empty bins are exact zeros rather than rounding residue.
+// Besides the FP64 histogram, a compensated FP32 copy (hi, lo) of every written cell goes
+// to hist_df when it is given, so that split scoring needs no FP64 arithmetic.
+__device__ __forceinline__ void put_cell(double* hist, float2* hist_df, int64_t cell, double v) {
+  hist[cell] = v;
+  if (hist_df) {
+    const float hi = __double2float_rn(v);
+    hist_df[cell] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
+  }
+}
+
 __global__ void reduce_kernel(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F,
                               int max_bins, const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
-                              const cbg_split* __restrict__ splits, int depth) {
+                              const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df) {
   const int jj = blockIdx.y;
   if (jj >= plan->n_small) return;
   const int per_leaf = G * 2 * max_bins * GROUP;
@@ -358,19 +772,19 @@ __global__ void reduce_kernel(const Plan* __restrict__ plan, const float* __rest
     const double pv = hist_prev[pcell];
     const bool small_is_child0 = leaf < (1 << (depth - 1));
     const bool in_child0 = b <= k;
-    hist_cur[cell] = (in_child0 == small_is_child0) ? pv : 0.0;
-    hist_cur[lcell] = (in_child0 == small_is_child0) ? 0.0 : pv;
+    put_cell(hist_cur, hist_df, cell, (in_child0 == small_is_child0) ? pv : 0.0);
+    put_cell(hist_cur, hist_df, lcell, (in_child0 == small_is_child0) ? 0.0 : pv);
     return;
   }
   const int u0 = plan->unit_begin[jj], u1 = plan->unit_begin[jj + 1];
   double s = 0.0;
   for (int u = u0; u < u1; ++u)
     s += static_cast<double>(partials[(static_cast<int64_t>(u) * G + grp) * (2 * max_bins * GROUP) + rem]);
-  hist_cur[cell] = s;
+  put_cell(hist_cur, hist_df, cell, s);
   if (large >= 0) {
     const int64_t pcell = ((static_cast<int64_t>(plan->parent[jj]) * F + f) * max_bins + b) * 2 + st;
     const int64_t lcell = ((static_cast<int64_t>(large) * F + f) * max_bins + b) * 2 + st;
-    hist_cur[lcell] = hist_prev[pcell] - s;
+    put_cell(hist_cur, hist_df, lcell, hist_prev[pcell] - s);
   }
 }
 
@@ -502,13 +916,82 @@ cbg_status wp_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   return CBG_OK;
 }
 
+// Geometry of the lane-per-feature kernels (PAIR: one statistic per warp): one CTA per SM
+// with as many warp histograms as fit, and the cluster size (<= the requested one) that
+// keeps the most CTAs resident.
+template <typename GH, bool PAIR>
+cbg_status lane_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int>, HistGeom> cache;
+  const int warps = PAIR ? lp_warps(L.max_bins, L.threads) : lh_warps(L.max_bins, L.threads);
+  const auto key = std::make_tuple(ctx->device, L.max_bins, warps, L.cluster, static_cast<int>(sizeof(GH)));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *out = it->second;
+      return CBG_OK;
+    }
+  }
+  auto kern = PAIR ? level_hist_pair_kernel<GH> : level_hist_lane_kernel<GH>;
+  const size_t smem = PAIR ? lp_smem_bytes(L.max_bins, warps) : lh_smem_bytes(L.max_bins, warps);
+  CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  HistGeom geom;
+  for (int cs = L.cluster; cs >= 1; cs >>= 1) {
+    if (cs > 8) CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(cs * ctx->num_sms));
+    cfg.blockDim = dim3(static_cast<unsigned>(32 * warps));
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(cs);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      clusters = 0;
+    }
+    if (clusters * cs > geom.clusters * geom.cs) {
+      geom.cs = cs;
+      geom.clusters = clusters;
+    }
+  }
+  if (geom.clusters == 0) return ::cbg::fail(ctx, CBG_EUNSUPPORTED, "no co-resident histogram cluster fits on this device");
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = geom;
+  *out = geom;
+  return CBG_OK;
+}
+
 // The cluster size the plan must chunk for (identical for FP32 and BF16 gradients).
 cbg_status hist_cluster_size(cbg_ctx* ctx, const HistConfig& L, int* cs) {
   HistGeom g;
-  cbg_status st = L.kind == 0 ? wp_geom<float>(ctx, L, &g) : hist_geom<float>(ctx, L, &g);
+  cbg_status st = L.kind == 0   ? wp_geom<float>(ctx, L, &g)
+                  : L.kind == 4 ? lane_geom<float, false>(ctx, L, &g)
+                  : L.kind == 5 ? lane_geom<float, true>(ctx, L, &g)
+                                : hist_geom<float>(ctx, L, &g);
   if (st != CBG_OK) return st;
   *cs = g.cs;
   return CBG_OK;
+}
+
+// Every occupancy query and function attribute that a launch of this configuration
+// needs, made ahead of a graph capture (those calls cannot be captured).
+template <typename GH>
+cbg_status hist_warm(cbg_ctx* ctx, const HistConfig& L) {
+  HistGeom g;
+  cbg_status st = L.kind == 0   ? wp_geom<GH>(ctx, L, &g)
+                  : L.kind == 4 ? lane_geom<GH, false>(ctx, L, &g)
+                  : L.kind == 5 ? lane_geom<GH, true>(ctx, L, &g)
+                                : hist_geom<GH>(ctx, L, &g);
+  if (st != CBG_OK) return st;
+  int cs = 1;
+  return hist_cluster_size(ctx, L, &cs);
 }
 
 template <typename GH, int NB, int MODE>
@@ -563,6 +1046,29 @@ cbg_status launch_hist(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins, c
     cfg.numAttrs = 1;
     CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_wp_kernel<GH>, bins, L.n, L.G, L.F, order, gg, hh, plan,
                                      L.max_bins, partials));
+    return CBG_OK;
+  }
+  if (L.kind == 4 || L.kind == 5) {
+    const bool pair = L.kind == 5;
+    HistGeom geom;
+    st = pair ? lane_geom<GH, true>(ctx, L, &geom) : lane_geom<GH, false>(ctx, L, &geom);
+    if (st != CBG_OK) return st;
+    if (geom.cs != cs) return ::cbg::fail(ctx, CBG_ECUDA, "histogram cluster size changed between plan and launch");
+    const int warps = pair ? lp_warps(L.max_bins, L.threads) : lh_warps(L.max_bins, L.threads);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(geom.cs * geom.clusters));
+    cfg.blockDim = dim3(static_cast<unsigned>(32 * warps));
+    cfg.dynamicSmemBytes = pair ? lp_smem_bytes(L.max_bins, warps) : lh_smem_bytes(L.max_bins, warps);
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(geom.cs);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, pair ? level_hist_pair_kernel<GH> : level_hist_lane_kernel<GH>, bins, L.n,
+                                     L.G, L.F, order, gg, hh, plan, L.max_bins, partials));
     return CBG_OK;
   }
   if (L.kind == 3) {

@@ -109,7 +109,7 @@ extern "C" cbg_status cbg_histogram_noalloc(cbg_ctx* ctx, const uint8_t* bins, i
   if (st != CBG_OK) return st;
   const int per_leaf = hc.G * 2 * max_bins * GROUP;
   reduce_kernel<<<dim3(static_cast<unsigned>(ceil_div(per_leaf, 256)), 1), 256, 0, ctx->stream>>>(
-      plan, partials, hc.G, F, max_bins, nullptr, hist_out, nullptr, 0);
+      plan, partials, hc.G, F, max_bins, nullptr, hist_out, nullptr, 0, nullptr);
   CBG_CHECK_LAUNCH(ctx);
   return CBG_OK;
 }

@@ -50,10 +50,10 @@ struct Layout {
   int64_t n_ptiles;
   size_t hist_elems;                // per hist buffer (doubles)
   size_t part_elems_item;           // floats per partial item
-  size_t term_elems;
   // byte offsets
   size_t o_order_a, o_order_b, o_flags, o_tcnt, o_toff, o_seg_a, o_seg_b, o_plan, o_hist_a, o_hist_b,
-      o_part, o_term, o_best, o_misc, o_count, o_tot_a, o_tot_b, o_gsplit, o_gvals, total;
+      o_part, o_best, o_misc, o_count, o_hdf, o_gsplit, o_gvals, o_gp_a, o_gp_b, o_hp_a, o_hp_b,
+      total;
 };
 
 int pow2_at_least(int v) {
@@ -82,11 +82,13 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
   L->nb_alloc = pow2_at_least(L->max_bins);
   L->D = s->max_depth;
   CBG_REQUIRE(ctx, t.cluster >= 0 && t.cluster <= 16, "cluster must be in [0, 16]");
-  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 3, "kernel must be 0 (default), 1 (shared reductions), 2 "
-              "(warp-private) or 3 (64-bit compare-and-swap)");
-  L->kind = t.kernel == 2 ? 0 : (t.kernel == 3 ? 3 : 1);
-  L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : 2048;
-  L->cluster = t.cluster > 0 ? t.cluster : 8;
+  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 5, "kernel must be 0 (default), 1 (shared reductions), 2 "
+              "(warp-private, 16 features per warp), 3 (64-bit compare-and-swap), 4 (lane per feature) or 5 (lane "
+              "per feature, one statistic per warp)");
+  L->kind = t.kernel == 2 ? 0 : (t.kernel >= 3 ? t.kernel : 1);
+  const bool lane_kind = L->kind == 4 || L->kind == 5;
+  L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : (lane_kind ? 8192 : 2048);
+  L->cluster = t.cluster > 0 ? t.cluster : (lane_kind ? 2 : 8);
   L->threads = t.threads > 0 ? t.threads : 512;
   const int fit = static_cast<int>((227 * 1024) / hist_smem_bytes(L->nb_alloc));
   L->blocks_per_sm = std::max(1, std::min(t.blocks_per_sm > 0 ? t.blocks_per_sm : 3, fit));
@@ -95,7 +97,6 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
   L->n_ptiles = ceil_div(L->n, PT);
   L->hist_elems = static_cast<size_t>(hleaves) * L->F * L->max_bins * 2;
   L->part_elems_item = static_cast<size_t>(2) * L->max_bins * GROUP;
-  L->term_elems = static_cast<size_t>(hleaves) * L->F * (L->max_bins - 1);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     off = (off + 255) / 256 * 256;
@@ -114,14 +115,18 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
   L->o_hist_a = take(L->hist_elems * 8);
   L->o_hist_b = take(L->hist_elems * 8);
   L->o_part = take(static_cast<size_t>(L->max_items) * L->part_elems_item * 4);
-  L->o_term = take(L->term_elems * 4);
-  L->o_tot_a = take((static_cast<size_t>(2) << L->D) * 8);
-  L->o_tot_b = take((static_cast<size_t>(2) << L->D) * 8);
+  L->o_hdf = take(L->hist_elems * sizeof(float2));   // (hi, lo) FP32 copy of the current level's histogram
   L->o_best = take(static_cast<size_t>(L->F) * sizeof(BestF) + 64);
   L->o_misc = take(256);
   L->o_count = take(256);
   L->o_gsplit = take(sizeof(cbg_split) * MAX_DEPTH + 256);   // per-tree outputs while replaying a graph
   L->o_gvals = take(sizeof(double) * (static_cast<size_t>(1) << L->D));
+  // (g, h) in the row order of each level (position order), for the kernel that reads
+  // them by position; 4 bytes per row covers both FP32 and BF16
+  L->o_gp_a = take(L->n * 4);
+  L->o_gp_b = take(L->n * 4);
+  L->o_hp_a = take(L->n * 4);
+  L->o_hp_b = take(L->n * 4);
   L->total = take(0) + 256;
   return CBG_OK;
 }
@@ -238,109 +243,114 @@ __device__ __forceinline__ DF df_shfl(DF v, int src) {
   return DF{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
 }
 
-// One warp per (leaf l, feature f). Lane i owns bins [8i, 8i+8): compensated prefix sums
-// of the FP64 histogram give G_L(k), H_L(k); the leaf total is the last prefix, the right
-// side the rest. term[l][f][k] = G_L^2/(H_L+l2) + G_R^2/(H_R+l2) in FP32.
-constexpr int TERM_BINS_PER_LANE = 8;   // 32 lanes x 8 = 256 bins
-
-__global__ void leaf_terms_kernel(const double* __restrict__ hist, int level_leaves, int F, int max_bins,
-                                  const int32_t* __restrict__ n_borders, double l2, float* __restrict__ term) {
-  const int64_t wid = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= static_cast<int64_t>(level_leaves) * F) return;
-  const int l = static_cast<int>(wid / F), f = static_cast<int>(wid - static_cast<int64_t>(l) * F);
-  const int K = max_bins - 1;
-  const int nb = min(n_borders[f], K);
-  if (nb <= 0) return;
-  const double* hl = hist + (static_cast<int64_t>(l) * F + f) * max_bins * 2;
-  DF g[TERM_BINS_PER_LANE], h[TERM_BINS_PER_LANE];
-  DF sg{0.f, 0.f}, sh{0.f, 0.f};
-#pragma unroll
-  for (int i = 0; i < TERM_BINS_PER_LANE; ++i) {
-    const int b = lane * TERM_BINS_PER_LANE + i;
-    double2 v = b < max_bins ? reinterpret_cast<const double2*>(hl)[b] : make_double2(0.0, 0.0);
-    sg = df_add(sg, df_from_double(v.x));
-    sh = df_add(sh, df_from_double(v.y));
-    g[i] = sg;   // inclusive prefix within the lane
-    h[i] = sh;
-  }
-  // inclusive scan of lane totals
-  DF ig = sg, ih = sh;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const DF ug = df_shfl_up(ig, o), uh = df_shfl_up(ih, o);
-    if (lane >= o) {
-      ig = df_add(ug, ig);
-      ih = df_add(uh, ih);
-    }
-  }
-  const DF tg = df_shfl(ig, 31), th = df_shfl(ih, 31);
-  DF eg = df_shfl_up(ig, 1), eh = df_shfl_up(ih, 1);
-  if (lane == 0) eg = eh = DF{0.f, 0.f};
-  const float l2f = static_cast<float>(l2);
-  float* out = term + (static_cast<int64_t>(l) * F + f) * K;
-#pragma unroll
-  for (int i = 0; i < TERM_BINS_PER_LANE; ++i) {
-    const int k = lane * TERM_BINS_PER_LANE + i;
-    if (k < nb) {
-      const DF GL = df_add(eg, g[i]), HL = df_add(eh, h[i]);
-      const DF GR = df_sub(tg, GL), HR = df_sub(th, HL);
-      out[k] = score_term_f(GL.hi + GL.lo, HL.hi + HL.lo, l2f) + score_term_f(GR.hi + GR.lo, HR.hi + HR.lo, l2f);
-    }
-  }
-}
-
 __device__ __forceinline__ bool better(double s, int k, double bs, int bk) {
   return s > bs || (s == bs && k < bk);
 }
 
-// Block per feature: score(f,k) = sum over leaves of term (compensated FP32); argmax over
-// k. The last block to finish picks the best feature (ties to the smallest f, then k),
-// writes the split and the child totals of every leaf.
-__global__ void argmax_kernel(const float* __restrict__ term, int level_leaves, int F, int max_bins,
-                              const int32_t* __restrict__ n_borders, BestF* __restrict__ best, Misc* misc,
-                              int force_f, int force_k, int depth, cbg_split* __restrict__ splits) {
-  __shared__ double s_sc[256];
-  __shared__ int s_k[256];
+// Split scoring of one level in one kernel, a block per feature (Sections 3-4: one split
+// per level, scored over every leaf of the level). It reads the compensated FP32 copy
+// (hi, lo) of the FP64 histogram that the reduction writes, so it runs on the FP32 pipe
+// alone (GB300 executes FP64 at 1/64 of the FP32 rate).
+//  - Warp w takes leaves w, w + SC_WARPS, ... For each it forms compensated prefix sums
+//    over bins (lane i owns bins [8i, 8i + 8), then a warp scan), so G_L(k), H_L(k) and
+//    the leaf totals come out at about 2^-44 relative, and adds the FP32 term
+//    G_L^2/(H_L+l2) + G_R^2/(H_R+l2) of every border to its own compensated accumulators.
+//  - The warps' accumulators are added in warp order (compensated); the block keeps its
+//    best border.
+//  - The last block to finish picks the best feature (ties to the smallest f, then k) and
+//    writes the split.
+constexpr int SC_WARPS = 8;
+constexpr int SC_BINS_PER_LANE = 8;   // 32 lanes x 8 = 256 bins
+
+__global__ void __launch_bounds__(SC_WARPS * 32)
+    score_level_kernel(const float2* __restrict__ hist_df, int level_leaves, int F, int max_bins,
+                       const int32_t* __restrict__ n_borders, double l2, BestF* __restrict__ best, Misc* misc,
+                       int force_f, int force_k, int depth, cbg_split* __restrict__ splits) {
+  constexpr int NT = SC_WARPS * 32;
+  __shared__ DF s_acc[SC_WARPS][256];
+  __shared__ double r_s[NT];
+  __shared__ int r_f[NT], r_k[NT];
   __shared__ bool is_last;
   const int f = blockIdx.x, K = max_bins - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = min(n_borders[f], K);
+  const float l2f = static_cast<float>(l2);
+  DF acc[SC_BINS_PER_LANE];
+#pragma unroll
+  for (int i = 0; i < SC_BINS_PER_LANE; ++i) acc[i] = DF{0.f, 0.f};
+  if (nb > 0) {
+    for (int l = warp; l < level_leaves; l += SC_WARPS) {
+      const float4* hl = reinterpret_cast<const float4*>(hist_df + (static_cast<int64_t>(l) * F + f) * max_bins * 2);
+      DF g[SC_BINS_PER_LANE], h[SC_BINS_PER_LANE];
+      DF sg{0.f, 0.f}, sh{0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < SC_BINS_PER_LANE; ++i) {
+        const int b = lane * SC_BINS_PER_LANE + i;
+        const float4 v = b < max_bins ? hl[b] : make_float4(0.f, 0.f, 0.f, 0.f);   // (G hi, G lo, H hi, H lo)
+        sg = df_add(sg, DF{v.x, v.y});
+        sh = df_add(sh, DF{v.z, v.w});
+        g[i] = sg;   // inclusive prefix within the lane
+        h[i] = sh;
+      }
+      DF ig = sg, ih = sh;   // inclusive scan of the lane totals
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const DF ug = df_shfl_up(ig, o), uh = df_shfl_up(ih, o);
+        if (lane >= o) {
+          ig = df_add(ug, ig);
+          ih = df_add(uh, ih);
+        }
+      }
+      const DF tg = df_shfl(ig, 31), th = df_shfl(ih, 31);
+      DF eg = df_shfl_up(ig, 1), eh = df_shfl_up(ih, 1);
+      if (lane == 0) eg = eh = DF{0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < SC_BINS_PER_LANE; ++i) {
+        const int k = lane * SC_BINS_PER_LANE + i;
+        if (k < nb) {
+          const DF GL = df_add(eg, g[i]), HL = df_add(eh, h[i]);
+          const DF GR = df_sub(tg, GL), HR = df_sub(th, HL);
+          const float t = score_term_f(GL.hi + GL.lo, HL.hi + HL.lo, l2f) +
+                          score_term_f(GR.hi + GR.lo, HR.hi + HR.lo, l2f);
+          acc[i] = df_add(acc[i], DF{t, 0.f});
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < SC_BINS_PER_LANE; ++i) s_acc[warp][lane * SC_BINS_PER_LANE + i] = acc[i];
+  __syncthreads();
   double bs = -INFINITY;
   int bk = -1;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-    float sum = 0.0f, comp = 0.0f;
-    for (int l = 0; l < level_leaves; ++l) {
-      const float y = term[(static_cast<int64_t>(l) * F + f) * K + k] - comp;
-      const float tsum = sum + y;
-      comp = (tsum - sum) - y;
-      sum = tsum;
-    }
-    const double s = static_cast<double>(sum) - static_cast<double>(comp);
-    if (f == force_f && k == force_k) misc->forced_score = s;
-    if (bk < 0 || better(s, k, bs, bk)) {
-      bs = s;
+  for (int k = threadIdx.x; k < nb; k += NT) {
+    DF t = s_acc[0][k];
+    for (int w = 1; w < SC_WARPS; ++w) t = df_add(t, s_acc[w][k]);
+    const double sc = static_cast<double>(t.hi) + static_cast<double>(t.lo);
+    if (f == force_f && k == force_k) misc->forced_score = sc;
+    if (bk < 0 || better(sc, k, bs, bk)) {
+      bs = sc;
       bk = k;
     }
   }
   __threadfence();   // the forced-score store must be visible before this block is counted
-  s_sc[threadIdx.x] = bs;
-  s_k[threadIdx.x] = bk;
+  r_s[threadIdx.x] = bs;
+  r_k[threadIdx.x] = bk;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+  for (int o = NT / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
-      int ok = s_k[threadIdx.x + o];
-      if (ok >= 0 && (s_k[threadIdx.x] < 0 || better(s_sc[threadIdx.x + o], ok, s_sc[threadIdx.x], s_k[threadIdx.x]))) {
-        s_sc[threadIdx.x] = s_sc[threadIdx.x + o];
-        s_k[threadIdx.x] = ok;
+      const int ok = r_k[threadIdx.x + o];
+      if (ok >= 0 && (r_k[threadIdx.x] < 0 || better(r_s[threadIdx.x + o], ok, r_s[threadIdx.x], r_k[threadIdx.x]))) {
+        r_s[threadIdx.x] = r_s[threadIdx.x + o];
+        r_k[threadIdx.x] = ok;
       }
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    best[f].score = s_sc[0];
-    best[f].k = s_k[0];
+    best[f].score = r_s[0];
+    best[f].k = r_k[0];
     __threadfence();
-    unsigned ticket = atomicAdd(&misc->done, 1u);
+    const unsigned ticket = atomicAdd(&misc->done, 1u);
     is_last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
@@ -349,26 +359,24 @@ __global__ void argmax_kernel(const float* __restrict__ term, int level_leaves, 
   // last block: global argmax over features
   double gbs = -INFINITY;
   int gbf = -1, gbk = -1;
-  for (int ff = threadIdx.x; ff < F; ff += blockDim.x) {
-    double s = __ldcg(&best[ff].score);
-    int k = __ldcg(&best[ff].k);
-    if (k >= 0 && (gbf < 0 || s > gbs || (s == gbs && ff < gbf))) {
-      gbs = s;
+  for (int ff = threadIdx.x; ff < F; ff += NT) {
+    const double sc = __ldcg(&best[ff].score);
+    const int k = __ldcg(&best[ff].k);
+    if (k >= 0 && (gbf < 0 || sc > gbs || (sc == gbs && ff < gbf))) {
+      gbs = sc;
       gbf = ff;
       gbk = k;
     }
   }
-  __shared__ double r_s[256];
-  __shared__ int r_f[256], r_k[256];
   r_s[threadIdx.x] = gbs;
   r_f[threadIdx.x] = gbf;
   r_k[threadIdx.x] = gbk;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+  for (int o = NT / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
-      int of = r_f[threadIdx.x + o];
-      double os = r_s[threadIdx.x + o];
-      int mf = r_f[threadIdx.x];
+      const int of = r_f[threadIdx.x + o];
+      const double os = r_s[threadIdx.x + o];
+      const int mf = r_f[threadIdx.x];
       if (of >= 0 && (mf < 0 || os > r_s[threadIdx.x] || (os == r_s[threadIdx.x] && of < mf))) {
         r_s[threadIdx.x] = os;
         r_f[threadIdx.x] = of;
@@ -392,15 +400,11 @@ __global__ void argmax_kernel(const float* __restrict__ term, int level_leaves, 
   }
 }
 
-// Child totals of the chosen split, FP64: one warp per leaf of the level; leaf l keeps bins
-// <= k (child l), the rest go to child l + 2^d.
-__global__ void child_totals_kernel(const double* __restrict__ hist, int level_leaves, int F, int max_bins,
-                                    const cbg_split* __restrict__ splits, int depth,
-                                    double* __restrict__ child_totals, double* __restrict__ tot_next) {
-  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// FP64 child totals of the level's split for leaf l, one warp: bins <= k stay in leaf l,
+// the rest go to l + 2^d (every row stays in l when no split exists).
+__device__ void child_totals_warp(const double* __restrict__ hist, int l, int level_leaves, int F, int max_bins,
+                                  int sf, int sk, double* __restrict__ child_totals) {
   const int lane = threadIdx.x & 31;
-  if (l >= level_leaves) return;
-  const int sf = splits[depth].feature, sk = splits[depth].border;
   const int cf = sf >= 0 ? sf : 0;
   const double2* hl = reinterpret_cast<const double2*>(hist + (static_cast<int64_t>(l) * F + cf) * max_bins * 2);
   double g0 = 0.0, h0 = 0.0, g1 = 0.0, h1 = 0.0;
@@ -426,10 +430,6 @@ __global__ void child_totals_kernel(const double* __restrict__ hist, int level_l
     child_totals[2 * l + 1] = h0;
     child_totals[2 * (l + level_leaves)] = g1;
     child_totals[2 * (l + level_leaves) + 1] = h1;
-    tot_next[2 * l] = g0;
-    tot_next[2 * l + 1] = h0;
-    tot_next[2 * (l + level_leaves)] = g1;
-    tot_next[2 * (l + level_leaves) + 1] = h1;
   }
 }
 
@@ -529,8 +529,30 @@ __device__ void plan_next_level(uint32_t* __restrict__ tile_cnt, int64_t n_ptile
   plan->level_leaves = 2 * L;
 }
 
-// A: per position (8 consecutive positions per thread), the split bit of its row; leaf +=
-// 2^d * bit. Unless this is the last level: ones per tile and per leaf (run-length counted
+// The leaf segments of a level in memory order, staged in shared memory: seg_pos[i] is
+// the first position of the i-th segment and seg_leaf[i] its leaf. Positions are grouped
+// by leaf, so the leaf of a position is found here instead of being read per row.
+__device__ void load_seg_table(const Segs* __restrict__ seg, int L, int* seg_pos, int* seg_leaf) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    const int l = seg->order[i];
+    seg_leaf[i] = l;
+    seg_pos[i] = seg->start[l];
+  }
+}
+
+// The segment holding position pos: the last i with seg_pos[i] <= pos. An empty segment
+// starts where the next one does and comes before it, so it is never the last such i.
+__device__ __forceinline__ int seg_find(const int* seg_pos, int L, int64_t pos) {
+  int lo = 0, hi = L - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg_pos[mid] <= pos) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// A: the FP64 child totals of the level's split (one warp per leaf); per position (8
+// consecutive positions per thread), the split bit of its row; leaf += 2^d * bit. Unless this is the last level: ones per tile and per leaf (run-length counted
 // in shared memory, since positions are grouped by leaf), and the last block to finish
 // plans the next level.
 __global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_t* __restrict__ bins_t, int64_t n,
@@ -538,17 +560,24 @@ __global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_
                                   uint16_t* __restrict__ leaf, uint8_t* __restrict__ flags,
                                   uint32_t* __restrict__ tile_cnt, Segs* seg, int write_flags, int64_t n_ptiles,
                                   Segs* __restrict__ nxt, Plan* __restrict__ plan, int rows_per_item, int cs,
-                                  unsigned long long* __restrict__ rows_hist, Misc* misc) {
+                                  unsigned long long* __restrict__ rows_hist, Misc* misc,
+                                  const double* __restrict__ hist, int F, int max_bins,
+                                  double* __restrict__ child_totals) {
   __shared__ uint32_t wsum[PT_THREADS / 32];
   __shared__ uint32_t sh_ones[1 << MAX_DEPTH];
+  __shared__ int sh_pos[1 << (MAX_DEPTH - 1)], sh_leaf[1 << (MAX_DEPTH - 1)];
   __shared__ bool is_last;
   const int L = 1 << depth;
-  if (write_flags) {
+  if (write_flags)
     for (int i = threadIdx.x; i < L; i += blockDim.x) sh_ones[i] = 0;
-    __syncthreads();
-  }
+  load_seg_table(seg, L, sh_pos, sh_leaf);
+  __syncthreads();
   const int f = splits[depth].feature, k = splits[depth].border;
+  // the FP64 child totals of the split, one warp per leaf of the level
+  for (int l = blockIdx.x * (PT_THREADS / 32) + (threadIdx.x >> 5); l < L; l += gridDim.x * (PT_THREADS / 32))
+    child_totals_warp(hist, l, L, F, max_bins, f, k, child_totals);
   const int64_t base = static_cast<int64_t>(blockIdx.x) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
+  int si = seg_find(sh_pos, L, base);
   uint32_t cnt = 0, run = 0;
   int cur = -1;
 #pragma unroll
@@ -557,8 +586,9 @@ __global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_
     if (pos < n) {
       const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
       const int bit = split_bit(bins, bins_t, n, row, f, k);
-      const int lf = leaf[row] & (L - 1);
-      if (bit) leaf[row] = static_cast<uint16_t>(lf + L);
+      while (si + 1 < L && sh_pos[si + 1] <= pos) ++si;
+      const int lf = sh_leaf[si];
+      if (bit) leaf[row] = static_cast<uint16_t>(lf + L);   // rows of leaf lf already hold lf
       if (write_flags) {
         flags[pos] = static_cast<uint8_t>(bit);
         if (lf != cur) {
@@ -597,10 +627,15 @@ __global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_
 // C: stable partition of every segment: the row at position i moves to
 // start + (zeros before it) or start + zeros + (ones before it).
 __global__ void part_scatter_kernel(const uint32_t* __restrict__ order, const uint8_t* __restrict__ flags, int64_t n,
-                                    const uint32_t* __restrict__ tile_off, const uint16_t* __restrict__ leaf,
-                                    const Segs* __restrict__ cur, int depth, uint32_t* __restrict__ order_out) {
+                                    const uint32_t* __restrict__ tile_off, const Segs* __restrict__ cur, int depth,
+                                    uint32_t* __restrict__ order_out,
+                                    const void* __restrict__ g_in, const void* __restrict__ h_in,
+                                    void* __restrict__ g_out, void* __restrict__ h_out, int gh_bytes) {
   __shared__ uint32_t sh[PT_THREADS / 32];
+  __shared__ int sh_pos[1 << (MAX_DEPTH - 1)], sh_leaf[1 << (MAX_DEPTH - 1)];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int L = 1 << depth;
+  load_seg_table(cur, L, sh_pos, sh_leaf);
   const int64_t base = static_cast<int64_t>(blockIdx.x) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
   uint8_t fl[PT / PT_THREADS];
   uint32_t s = 0;
@@ -626,13 +661,14 @@ __global__ void part_scatter_kernel(const uint32_t* __restrict__ order, const ui
   }
   __syncthreads();
   uint32_t ones_before = tile_off[blockIdx.x] + sh[warp] + x - s;
-  const int mask = (1 << depth) - 1;
+  int si = seg_find(sh_pos, L, base);
 #pragma unroll
   for (int i = 0; i < PT / PT_THREADS; ++i) {
     const int64_t pos = base + i;
     if (pos < n) {
       const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
-      const int l = leaf[row] & mask;
+      while (si + 1 < L && sh_pos[si + 1] <= pos) ++si;
+      const int l = sh_leaf[si];
       const int start = cur->start[l];
       const uint32_t ob = ones_before - cur->ones_before[l];       // ones of leaf l before pos
       const int zeros_total = cur->cnt[l] - static_cast<int>(cur->ones[l]);
@@ -641,7 +677,16 @@ __global__ void part_scatter_kernel(const uint32_t* __restrict__ order, const ui
         dst = start + zeros_total + static_cast<int>(ob);
       else
         dst = start + static_cast<int>(pos - start) - static_cast<int>(ob);
-      if (dst >= 0 && dst < n) order_out[dst] = row;
+      if (dst >= 0 && dst < n) {
+        order_out[dst] = row;
+        if (gh_bytes == 4) {
+          static_cast<uint32_t*>(g_out)[dst] = static_cast<const uint32_t*>(g_in)[pos];
+          static_cast<uint32_t*>(h_out)[dst] = static_cast<const uint32_t*>(h_in)[pos];
+        } else if (gh_bytes == 2) {
+          static_cast<uint16_t*>(g_out)[dst] = static_cast<const uint16_t*>(g_in)[pos];
+          static_cast<uint16_t*>(h_out)[dst] = static_cast<const uint16_t*>(h_in)[pos];
+        }
+      }
     }
     ones_before += fl[i];
   }
@@ -796,6 +841,8 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
   const int d = a->depth;
   CBG_REQUIRE(ctx, d >= 0 && d < L.D, "depth %d outside [0, max_depth)", d);
   CBG_REQUIRE(ctx, a->bins && a->n_borders && a->g && a->h && a->leaf && a->splits && a->child_totals, "NULL argument");
+  CBG_REQUIRE(ctx, (L.kind != 4 && L.kind != 5) || (reinterpret_cast<uintptr_t>(a->bins) & 15) == 0,
+              "bins must be 16-byte aligned for the lane-per-feature histogram kernel");
   CBG_REQUIRE(ctx, a->gh_dtype == CBG_F32 || a->gh_dtype == CBG_BF16, "bad gh_dtype");
   CBG_REQUIRE(ctx, a->l2 >= 0.0 && std::isfinite(a->l2), "l2 must be finite and >= 0");
   CBG_REQUIRE(ctx, a->force_feature < L.F, "force_feature out of range");
@@ -811,8 +858,7 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
   double* hist_cur = at<double>(S, d % 2 == 0 ? L.o_hist_a : L.o_hist_b);
   const double* hist_prev = at<double>(S, d % 2 == 0 ? L.o_hist_b : L.o_hist_a);
   float* partials = at<float>(S, L.o_part);
-  float* term = at<float>(S, L.o_term);
-  double* tot_nxt = at<double>(S, d % 2 == 0 ? L.o_tot_b : L.o_tot_a);
+  float2* hist_df = at<float2>(S, L.o_hdf);
   BestF* best = at<BestF>(S, L.o_best);
   Misc* misc = at<Misc>(S, L.o_misc);
   uint8_t* flags = at<uint8_t>(S, L.o_flags);
@@ -824,8 +870,19 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
   CBG_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &capturing));
   if (capturing == cudaStreamCaptureStatusNone) st = prof_begin(ctx, &ev0, &ev1);
   if (st != CBG_OK) return st;
-  st = a->gh_dtype == CBG_F32 ? launch_hist<float>(ctx, hist_config(L), a->bins, order_cur, a->g, a->h, plan, partials)
-                              : launch_hist<__nv_bfloat16>(ctx, hist_config(L), a->bins, order_cur, a->g, a->h, plan, partials);
+  // the lane-per-feature kernels read (g, h) by position: the caller's arrays at the root
+  // (positions are rows), then the copies the previous level's partition moved along (for
+  // the shared-reduction kernel the copy costs the partition more than it saves)
+  const bool by_pos = L.kind == 4 || L.kind == 5;
+  const void* g_pos = d == 0 ? a->g : at<char>(S, d % 2 == 1 ? L.o_gp_a : L.o_gp_b);
+  const void* h_pos = d == 0 ? a->h : at<char>(S, d % 2 == 1 ? L.o_hp_a : L.o_hp_b);
+  void* g_pos_nxt = at<char>(S, (d + 1) % 2 == 1 ? L.o_gp_a : L.o_gp_b);
+  void* h_pos_nxt = at<char>(S, (d + 1) % 2 == 1 ? L.o_hp_a : L.o_hp_b);
+  const void* g_hist = by_pos ? g_pos : a->g;
+  const void* h_hist = by_pos ? h_pos : a->h;
+  st = a->gh_dtype == CBG_F32 ? launch_hist<float>(ctx, hist_config(L), a->bins, order_cur, g_hist, h_hist, plan, partials)
+                              : launch_hist<__nv_bfloat16>(ctx, hist_config(L), a->bins, order_cur, g_hist, h_hist, plan,
+                                                           partials);
   if (st != CBG_OK) return st;
   st = prof_end(ctx, ev1);
   if (st != CBG_OK) return st;
@@ -834,24 +891,15 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
     const int per_leaf = L.G * 2 * L.max_bins * GROUP;
     dim3 grid(static_cast<unsigned>(ceil_div(per_leaf, 256)), static_cast<unsigned>(d == 0 ? 1 : (1 << (d - 1))));
     reduce_kernel<<<grid, 256, 0, ctx->stream>>>(plan, partials, L.G, L.F, L.max_bins, hist_prev, hist_cur,
-                                                 a->splits, d);
+                                                 a->splits, d, hist_df);
     CBG_CHECK_LAUNCH(ctx);
   }
   // 3. split scores and argmax
   const int level_leaves = 1 << d;
-  {
-    const int64_t threads = static_cast<int64_t>(level_leaves) * L.F;
-    leaf_terms_kernel<<<static_cast<unsigned>(ceil_div(threads * 32, 256)), 256, 0, ctx->stream>>>(
-        hist_cur, level_leaves, L.F, L.max_bins, a->n_borders, a->l2, term);
-    CBG_CHECK_LAUNCH(ctx);
-    argmax_kernel<<<L.F, 256, 0, ctx->stream>>>(term, level_leaves, L.F, L.max_bins, a->n_borders, best, misc,
-                                                a->force_feature, a->force_border, d, a->splits);
-    CBG_CHECK_LAUNCH(ctx);
-    child_totals_kernel<<<static_cast<unsigned>(ceil_div(static_cast<int64_t>(level_leaves) * 32, 256)), 256, 0,
-                          ctx->stream>>>(hist_cur, level_leaves, L.F, L.max_bins, a->splits, d, a->child_totals,
-                                         tot_nxt);
-    CBG_CHECK_LAUNCH(ctx);
-  }
+  score_level_kernel<<<L.F, SC_WARPS * 32, 0, ctx->stream>>>(hist_df, level_leaves, L.F, L.max_bins, a->n_borders,
+                                                           a->l2, best, misc, a->force_feature, a->force_border, d,
+                                                           a->splits);
+  CBG_CHECK_LAUNCH(ctx);
   if (a->hist_out)
     CBG_CUDA(ctx, cudaMemcpyAsync(a->hist_out, hist_cur,
                                   static_cast<size_t>(level_leaves) * L.F * L.max_bins * 2 * sizeof(double),
@@ -865,11 +913,13 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
   }
   part_flags_kernel<<<static_cast<unsigned>(L.n_ptiles), PT_THREADS, 0, ctx->stream>>>(
       a->bins, a->bins_t, L.n, order_cur, a->splits, d, a->leaf, flags, tcnt, seg_cur, last ? 0 : 1, L.n_ptiles,
-      seg_nxt, plan, L.rows_per_item, cs, at<unsigned long long>(S, L.o_count), misc);
+      seg_nxt, plan, L.rows_per_item, cs, at<unsigned long long>(S, L.o_count), misc, hist_cur, L.F, L.max_bins,
+      a->child_totals);
   CBG_CHECK_LAUNCH(ctx);
   if (!last) {
     part_scatter_kernel<<<static_cast<unsigned>(L.n_ptiles), PT_THREADS, 0, ctx->stream>>>(
-        order_cur, flags, L.n, tcnt, a->leaf, seg_cur, d, order_nxt);
+        order_cur, flags, L.n, tcnt, seg_cur, d, order_nxt, g_pos, h_pos, g_pos_nxt, h_pos_nxt,
+        by_pos ? (a->gh_dtype == CBG_F32 ? 4 : 2) : 0);
     CBG_CHECK_LAUNCH(ctx);
   }
   return CBG_OK;
@@ -1001,11 +1051,7 @@ cbg_status cbg_boost(cbg_ctx* ctx, const cbg_boost_args* a) {
   if (st != CBG_OK) return st;
   st = check_state(ctx, L, a->state, a->state_bytes);
   if (st != CBG_OK) return st;
-  HistGeom geom;
-  st = a->gh_dtype == CBG_F32 ? hist_geom<float>(ctx, hist_config(L), &geom) : hist_geom<__nv_bfloat16>(ctx, hist_config(L), &geom);
-  if (st != CBG_OK) return st;
-  int cs = 1;
-  st = hist_cluster_size(ctx, hist_config(L), &cs);
+  st = a->gh_dtype == CBG_F32 ? hist_warm<float>(ctx, hist_config(L)) : hist_warm<__nv_bfloat16>(ctx, hist_config(L));
   if (st != CBG_OK) return st;
   cbg_split* sp_tmp = at<cbg_split>(a->state, L.o_gsplit);
   double* v_tmp = at<double>(a->state, L.o_gvals);
@@ -1092,17 +1138,7 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
     st = check_state(ctx, L, p.state, p.state_bytes);
     if (st != CBG_OK) return st;
     // launch-geometry queries happen here, before the capture
-    HistGeom geom;
-    st = gh_dtype == CBG_F32 ? hist_geom<float>(ctx, hist_config(L), &geom)
-                             : hist_geom<__nv_bfloat16>(ctx, hist_config(L), &geom);
-    if (st != CBG_OK) return st;
-    if (hist_config(L).kind == 0) {
-      st = gh_dtype == CBG_F32 ? wp_geom<float>(ctx, hist_config(L), &geom)
-                               : wp_geom<__nv_bfloat16>(ctx, hist_config(L), &geom);
-      if (st != CBG_OK) return st;
-    }
-    int cs = 1;
-    st = hist_cluster_size(ctx, hist_config(L), &cs);
+    st = gh_dtype == CBG_F32 ? hist_warm<float>(ctx, hist_config(L)) : hist_warm<__nv_bfloat16>(ctx, hist_config(L));
     if (st != CBG_OK) return st;
     st = cbg_gradients(ctx, p.loss, p.y, p.pred, p.shape.n, gh_dtype, p.g, p.h);
     if (st != CBG_OK) return st;
@@ -1170,3 +1206,129 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+
+// The tilings the autotuner times: the shared-reduction kernel with clusters of 4 or 8
+// and 2048 or 4096 rows per CTA of a unit; the lane-per-feature kernel with clusters of 2
+// and 8192 or 16384 rows; its one-statistic-per-warp form with clusters of 2 or 4 and
+// 8192 or 16384 rows; the 16-feature warp-private kernel once.
+std::vector<cbg_tiles> autotune_candidates() {
+  std::vector<cbg_tiles> c;
+  auto add = [&](int kernel, int cluster, int rows) {
+    cbg_tiles t{};
+    t.kernel = kernel;
+    t.cluster = cluster;
+    t.rows_per_item = rows;
+    c.push_back(t);
+  };
+  for (int cl : {4, 8})
+    for (int r : {2048, 4096}) add(1, cl, r);
+  for (int r : {8192, 16384}) add(4, 2, r);
+  for (int cl : {2, 4})
+    for (int r : {8192, 16384}) add(5, cl, r);
+  add(2, 2, 8192);
+  return c;
+}
+
+cbg_status tune_tree(cbg_ctx* ctx, const cbg_tree_shape* s, const cbg_autotune_args* a) {
+  cbg_status st = cbg_tree_begin(ctx, s, a->state, a->state_bytes, a->leaf);
+  if (st != CBG_OK) return st;
+  for (int d = 0; d < a->depth; ++d) {
+    cbg_level_args la{};
+    la.shape = s;
+    la.state = a->state;
+    la.state_bytes = a->state_bytes;
+    la.bins = a->bins;
+    la.bins_t = a->bins_t;
+    la.n_borders = a->n_borders;
+    la.g = a->g;
+    la.h = a->h;
+    la.gh_dtype = a->gh_dtype;
+    la.depth = d;
+    la.l2 = a->l2;
+    la.force_feature = -1;
+    la.force_border = -1;
+    la.leaf = a->leaf;
+    la.splits = a->splits;
+    la.child_totals = a->child_totals;
+    la.last_level = d == a->depth - 1;
+    st = cbg_build_level(ctx, &la);
+    if (st != CBG_OK) return st;
+  }
+  return CBG_OK;
+}
+
+}  // namespace
+
+cbg_status cbg_autotune_state_bytes(const cbg_tree_shape* shape, size_t* bytes) {
+  if (!shape || !bytes) return CBG_EINVAL;
+  size_t mx = 0;
+  for (const cbg_tiles& t : autotune_candidates()) {
+    cbg_tree_shape s = *shape;
+    s.tiles = t;
+    Layout L;
+    cbg_status st = make_layout(nullptr, &s, &L);
+    if (st != CBG_OK) return st;
+    mx = std::max(mx, L.total);
+  }
+  *bytes = mx;
+  return CBG_OK;
+}
+
+cbg_status cbg_autotune_tiles(cbg_ctx* ctx, const cbg_autotune_args* a, cbg_tiles* best, double* best_ms) {
+  if (!ctx) return CBG_EINVAL;
+  CBG_REQUIRE(ctx, a != nullptr && a->shape != nullptr && best != nullptr && best_ms != nullptr, "NULL argument");
+  CBG_REQUIRE(ctx, a->depth >= 1 && a->depth <= a->shape->max_depth, "depth outside [1, max_depth]");
+  CBG_REQUIRE(ctx, a->reps >= 1, "reps must be >= 1");
+  DeviceGuard guard(ctx->device);
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  CBG_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &capturing));
+  CBG_REQUIRE(ctx, capturing == cudaStreamCaptureStatusNone, "the autotuner cannot run while the stream is captured");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CBG_CUDA(ctx, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ctx, CBG_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(ce));
+  }
+  double best_t = INFINITY;
+  cbg_tiles best_c{};
+  cbg_status result = CBG_OK;
+  for (const cbg_tiles& cand : autotune_candidates()) {
+    cbg_tree_shape s = *a->shape;
+    s.tiles = cand;
+    Layout L;
+    if (make_layout(ctx, &s, &L) != CBG_OK || L.total > a->state_bytes) continue;
+    double total = 0.0;
+    bool ok = true;
+    for (int r = 0; r <= a->reps && ok; ++r) {
+      if ((ce = cudaEventRecord(e0, ctx->stream)) != cudaSuccess) break;
+      ok = tune_tree(ctx, &s, a) == CBG_OK;
+      if (!ok) break;
+      if ((ce = cudaEventRecord(e1, ctx->stream)) != cudaSuccess) break;
+      if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+      if (r > 0) total += ms;
+    }
+    if (ce != cudaSuccess) {
+      result = fail(ctx, CBG_ECUDA, "autotuner timing: %s", cudaGetErrorString(ce));
+      break;
+    }
+    if (!ok) continue;   // a candidate this device or these inputs cannot run
+    const double t = total / a->reps;
+    if (t < best_t) {
+      best_t = t;
+      best_c = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != CBG_OK) return result;
+  if (!(best_t < INFINITY)) return fail(ctx, CBG_EINVAL, "no autotuner candidate could run on these inputs");
+  *best = best_c;
+  *best_ms = best_t;
+  return CBG_OK;
+}

@@ -142,11 +142,49 @@ def rowmajor_from_grouped(flat: np.ndarray, n: int, F_pad: int) -> np.ndarray:
     return np.ascontiguousarray(flat.reshape(F_pad // 32, n, 32).transpose(1, 0, 2)).reshape(n, F_pad)
 
 
+def autotune(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, l2: float = 3.0, gh_dtype: str = "f32",
+             reps: int = 2):
+    """Fastest histogram tiling for this problem (cbg_autotune_tiles), timed on trees built
+    from its gradients at prediction 0. Returns (tiles dict, ms per tree)."""
+    import torch
+    dev = prep.bins.device
+    shape = cbg.make_shape(prep.n, prep.F, prep.F_pad, prep.max_bins, depth)
+    state = torch.empty(cbg.cbg_autotune_state_bytes(shape), dtype=torch.uint8, device=dev)
+    tdt = torch.float32 if gh_dtype == "f32" else torch.bfloat16
+    g = torch.empty(prep.n, dtype=tdt, device=dev)
+    h = torch.empty(prep.n, dtype=tdt, device=dev)
+    cbg.cbg_gradients(ctx, loss, y, torch.zeros(prep.n, dtype=torch.float32, device=dev), prep.n, gh_dtype, g, h)
+    leaf = torch.empty(prep.n, dtype=torch.int16, device=dev)
+    splits = torch.empty((depth, 2), dtype=torch.float64, device=dev)
+    child = torch.empty((1 << depth, 2), dtype=torch.float64, device=dev)
+    return cbg.cbg_autotune_tiles(ctx, shape, state, prep.bins, prep.n_borders, g, h, gh_dtype, depth, l2, leaf,
+                                  splits, child, bins_t=prep.bins_t, reps=reps)
+
+
+def autotune_batch(ctx: cbg.Context, preps, ys, losses, depth: int, l2: float = 3.0, gh_dtype: str = "f32"):
+    """Tiles for every problem of a batch: one autotuner run per distinct bin count, on
+    the problem with the most rows among those that share it."""
+    by_bins: dict[int, int] = {}
+    for i, p in enumerate(preps):
+        j = by_bins.get(p.max_bins)
+        if j is None or p.n > preps[j].n:
+            by_bins[p.max_bins] = i
+    chosen = {mb: autotune(ctx, preps[i], ys[i], losses[i], depth, l2, gh_dtype)[0] for mb, i in by_bins.items()}
+    return [chosen[p.max_bins] for p in preps]
+
+
 def fit_batched(ctx: cbg.Context, preps, ys, losses, depth: int, trees: int, lr: float, l2: float,
-                gh_dtype: str = "f32", tiles: dict | None = None, branches: int = 0):
+                gh_dtype: str = "f32", tiles=None, branches: int = 0):
     """Boost many independent problems together (cbg_boost_batched): one captured graph per
-    round of trees, with the problems on parallel branches. Returns one Model per problem."""
-    bufs = [alloc_fit(p, depth, trees, gh_dtype, tiles) for p in preps]
+    round of trees, with the problems on parallel branches. tiles: None (library
+    defaults), one dict for every problem, a list with one dict per problem, or "auto"
+    (autotune_batch). Returns one Model per problem and the buffers."""
+    if isinstance(tiles, str):
+        if tiles != "auto":
+            raise ValueError("tiles must be None, a dict, a list of dicts or 'auto'")
+        tiles = autotune_batch(ctx, preps, ys, losses, depth, l2, gh_dtype)
+    per = tiles if isinstance(tiles, list) else [tiles] * len(preps)
+    bufs = [alloc_fit(p, depth, trees, gh_dtype, t) for p, t in zip(preps, per)]
     probs = []
     for p, b, y, loss in zip(preps, bufs, ys, losses):
         pr = cbg.Problem()

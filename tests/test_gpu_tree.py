@@ -312,13 +312,50 @@ def test_batched_matches_problem_by_problem(ctx):
         assert compared >= depth, i
 
 
+def test_autotuned_tiles_train_like_the_oracle(ctx):
+    """cbg_autotune_tiles returns one of its candidate tilings with a positive time, and
+    trees trained with the tiles it picks -- for one problem and, through
+    fit_batched(tiles="auto"), for a batch -- match the oracle up to its first near-tie."""
+    w = synth.logloss_1m(n=60000, trees=12)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    y = to_dev(w.y)
+    tiles, ms = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2)
+    assert tiles["kernel"] in (1, 2, 4, 5) and tiles["cluster"] >= 1 and tiles["rows_per_item"] >= 2048
+    assert ms > 0
+    model = train.fit(ctx, prep, y, w.loss, w.depth, w.trees, w.lr, w.l2, tiles=tiles, use_graph=True)
+    cbg.cbg_sync(ctx)
+    ref_prep = oracle.preprocess(w, prep.F_pad)
+    res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, w.depth, w.trees, w.lr, w.l2)
+    compared, _ = _compare_fit(res, model.host_splits(), to_host(model.pred), w.trees, w.depth)
+    assert compared >= w.depth
+    ws = synth.batched_256(n_problems=4, n_max=20000, trees=4)
+    preps, ys = [], []
+    for wi in ws:
+        import torch
+        cat = to_dev(wi.cat) if wi.n_cat else torch.zeros((0, wi.n), dtype=torch.int32, device="cuda")
+        preps.append(train.preprocess(ctx, to_dev(wi.x), cat, to_dev(wi.y), wi.label_kind, wi.max_borders, a=wi.a,
+                                      seed=wi.seed))
+        ys.append(to_dev(wi.y))
+    depth, trees, lr, l2 = 6, 4, 0.1, 3.0
+    models, _ = train.fit_batched(ctx, preps, ys, [wi.loss for wi in ws], depth, trees, lr, l2, tiles="auto",
+                                  branches=2)
+    cbg.cbg_sync(ctx)
+    for i, (wi, p) in enumerate(zip(ws, preps)):
+        rp = oracle.preprocess(wi, p.F_pad)
+        res = oracle.fit(rp["bins"], wi.n_features, rp["n_borders"], wi.y, wi.loss, depth, trees, lr, l2)
+        compared, _ = _compare_fit(res, models[i].host_splits(), to_host(models[i].pred), trees, depth)
+        assert compared >= 1, i
+
+
 @pytest.mark.parametrize("case", [LEVEL_CASES[0], LEVEL_CASES[3], LEVEL_CASES[5]])
 @pytest.mark.parametrize("cluster", [1, 4])
-@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
 def test_histogram_kernel_variants_match_oracle(ctx, case, cluster, kernel):
-    """The other histogram kernels -- warp-private without atomics (tiles.kernel = 2) and
-    64-bit compare-and-swap on interleaved (G, H) (tiles.kernel = 3) -- with and without
-    thread-block clusters, on forced levels against the oracle."""
+    """Every histogram kernel -- shared-memory reductions (tiles.kernel = 1), warp-private
+    with 16 features per warp (2), 64-bit compare-and-swap on interleaved (G, H) (3), lane
+    per feature with store forwarding (4) and the same with one statistic per warp (5) --
+    with and without thread-block clusters, on forced levels against the oracle."""
     n, F, F_pad, max_bins, depth, intg, dtype, bt = case
     bins, nb, g, h, forced = synth.random_level_case(n + F + 7, n, F, F_pad, max_bins, depth, integer_grads=intg)
     if dtype == "bf16":
