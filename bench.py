@@ -58,6 +58,24 @@ def parse_args():
 
 
 # ------------------------------------------------------------------ helpers
+def job_time_ms(rank_ms: float, ws: int, device=None) -> float:
+    """The job's timed-region duration: the maximum over ranks of each rank's duration
+    (every rank trains its own replica, so the slowest one ends the job)."""
+    if ws <= 1:
+        return rank_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([rank_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, job_ms: float) -> float:
+    """Units processed by all ranks per second of job time (weak scaling: per-rank work
+    is fixed as the number of ranks grows)."""
+    return units_per_rank * ws / (job_ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -193,11 +211,20 @@ def batched_comparison(ctx, n_problems, trees, dev):
     def batched():
         return train.fit_batched(ctx, preps, ys, [w.loss for w in ws], depth, trees, lr, l2)[0]
 
+    # histogram tiles from the autotuner, once per bin count (setup, outside the timing)
+    t0 = time.perf_counter()
+    auto_tiles = train.autotune_batch(ctx, preps, ys, [w.loss for w in ws], depth, l2)
+    tune_s = time.perf_counter() - t0
+
+    def batched_auto():
+        return train.fit_batched(ctx, preps, ys, [w.loss for w in ws], depth, trees, lr, l2, tiles=auto_tiles)[0]
+
     plain()
-    batched()                       # warm-up of both forms
+    batched()                       # warm-up of every form
+    batched_auto()
     torch.cuda.synchronize()
     out = {}
-    for name, fn in (("plain", plain), ("batched", batched)):
+    for name, fn in (("plain", plain), ("batched", batched), ("batched_auto", batched_auto)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         res = fn()
@@ -207,12 +234,19 @@ def batched_comparison(ctx, n_problems, trees, dev):
         preds = [b.pred for b in bufs] if name == "plain" else [m.pred for m in res]
         losses = [training_loss(w.loss, y, pr) for w, y, pr in zip(ws, ys, preds)]
         out[name] = {"trees_per_s": n_problems * trees / (ms / 1e3), "ms": ms, "losses": losses}
-    rel = max(abs(a - b) / max(abs(a), 1e-30) for a, b in zip(out["plain"]["losses"], out["batched"]["losses"]))
+    def rel(name):
+        return max(abs(a - b) / max(abs(a), 1e-30) for a, b in zip(out["plain"]["losses"], out[name]["losses"]))
+    distinct = sorted({(t["kernel"], t["cluster"], t["rows_per_item"]) for t in auto_tiles})
     return {"workload": f"batched_256 first {n_problems} problems (n log-uniform 1k..200k, 10-200 floats + "
                         f"0-8 categoricals, half RMSE half Logloss), depth 6, {trees} trees each, 128 borders",
             "plain_trees_per_s": out["plain"]["trees_per_s"], "batched_trees_per_s": out["batched"]["trees_per_s"],
             "speedup": out["batched"]["trees_per_s"] / out["plain"]["trees_per_s"],
-            "max_rel_final_loss_diff": rel}
+            "max_rel_final_loss_diff": rel("batched"),
+            "batched_autotuned_trees_per_s": out["batched_auto"]["trees_per_s"],
+            "speedup_autotuned": out["batched_auto"]["trees_per_s"] / out["plain"]["trees_per_s"],
+            "max_rel_final_loss_diff_autotuned": rel("batched_auto"),
+            "autotuned_tiles": [{"kernel": k, "cluster": c, "rows_per_item": r} for k, c, r in distinct],
+            "autotune_setup_s": tune_s}
 
 
 # ------------------------------------------------------------------ arms
@@ -322,13 +356,9 @@ def run_ours(args):
         rows_hist = cbg.cbg_tree_rows_histogrammed(ctx, bufs.shape, bufs.state, reset=True)
         hist_timing = ("CUDA events around every histogram launch of one extra step with host launches "
                        "(the timed steps replay a captured graph)")
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_time_ms(sum(step_ms), ws, dev)
+    value = whole_job_rate(T * args.steps, ws, total_ms)
     trees_total = T * args.steps * ws
-    value = trees_total / (total_ms / 1e3)
     n, F, mb = w.n, prep0.F, prep0.max_bins
     rfb = n * F * mb * D * T * args.steps * ws / (total_ms / 1e3)
 

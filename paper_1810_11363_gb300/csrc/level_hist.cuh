@@ -733,8 +733,8 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
 }
 
 // ------------------------------------------------------------ reduce + subtract
-// One thread per (direct leaf jj, feature f, stat, bin): FP64 sum of the item partials,
-// written to the leaf; the sibling gets parent - direct. For the feature the parent was
+// Every cell of a directly computed leaf gets the FP64 sum of its unit partials; the
+// sibling gets parent - direct. For the feature the parent was
 // split on, both children follow exactly from the parent (bins <= k stay in child 0, the
 // rest in child 1), so their empty bins are exact zeros rather than rounding residue.
 // Besides the FP64 histogram, a compensated FP32 copy (hi, lo) of every written cell goes
@@ -747,45 +747,76 @@ __device__ __forceinline__ void put_cell(double* hist, float2* hist_df, int64_t 
   }
 }
 
-__global__ void reduce_kernel(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F,
-                              int max_bins, const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
-                              const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df) {
+// A block takes a tile of 32 features (one group) x RD_BINS bins x 2 statistics of one
+// directly computed leaf: threads sum the unit partials of a cell in FP64 in unit order
+// (reads coalesced over the group's features), the tile is transposed through shared
+// memory, and the cells go out in the histogram's [leaf][f][b][stat] order (writes
+// coalesced over bins and statistics).
+constexpr int RD_BINS = 8;
+constexpr int RD_THREADS = 256;   // 2 x RD_BINS x 32 = 512 cells, two per thread
+
+__global__ void __launch_bounds__(RD_THREADS)
+    reduce_kernel(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
+                  const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
+                  const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df) {
+  constexpr int CELLS = 2 * RD_BINS * GROUP;
+  __shared__ double tile[GROUP][RD_BINS][2];
   const int jj = blockIdx.y;
   if (jj >= plan->n_small) return;
-  const int per_leaf = G * 2 * max_bins * GROUP;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= per_leaf) return;
-  const int grp = e / (2 * max_bins * GROUP);
-  const int rem = e - grp * (2 * max_bins * GROUP);
-  const int st = rem / (max_bins * GROUP);
-  const int rem2 = rem - st * (max_bins * GROUP);
-  const int b = rem2 / GROUP, fl = rem2 - b * GROUP;
-  const int f = grp * GROUP + fl;
-  if (f >= F) return;
+  const int nbt = (max_bins + RD_BINS - 1) / RD_BINS;
+  const int grp = blockIdx.x / nbt, b0 = (blockIdx.x - grp * nbt) * RD_BINS;
+  if (grp >= G) return;
+  const int u0 = plan->unit_begin[jj], u1 = plan->unit_begin[jj + 1];
+  const int64_t item_elems = static_cast<int64_t>(2) * max_bins * GROUP;
+  for (int c = threadIdx.x; c < CELLS; c += RD_THREADS) {
+    const int fl = c % GROUP, rest = c / GROUP;
+    const int st = rest / RD_BINS, bl = rest - st * RD_BINS;
+    const int b = b0 + bl;
+    double s = 0.0;
+    if (b < max_bins) {
+      const float* src = partials + (static_cast<int64_t>(u0) * G + grp) * item_elems +
+                         static_cast<int64_t>(st) * max_bins * GROUP + b * GROUP + fl;
+      for (int u = u0; u < u1; ++u, src += G * item_elems) s += static_cast<double>(*src);
+    }
+    tile[fl][bl][st] = s;
+  }
+  __syncthreads();
   const int leaf = plan->small_leaf[jj];
   const int large = plan->large_leaf[jj];
-  const int64_t cell = ((static_cast<int64_t>(leaf) * F + f) * max_bins + b) * 2 + st;
-  if (large >= 0 && depth > 0 && splits[depth - 1].feature == f) {
-    const int k = splits[depth - 1].border;
-    const int64_t pcell = ((static_cast<int64_t>(plan->parent[jj]) * F + f) * max_bins + b) * 2 + st;
-    const int64_t lcell = ((static_cast<int64_t>(large) * F + f) * max_bins + b) * 2 + st;
-    const double pv = hist_prev[pcell];
-    const bool small_is_child0 = leaf < (1 << (depth - 1));
-    const bool in_child0 = b <= k;
-    put_cell(hist_cur, hist_df, cell, (in_child0 == small_is_child0) ? pv : 0.0);
-    put_cell(hist_cur, hist_df, lcell, (in_child0 == small_is_child0) ? 0.0 : pv);
-    return;
+  const int par = plan->parent[jj];
+  const bool exact = large >= 0 && depth > 0 && splits[depth - 1].feature >= grp * GROUP &&
+                     splits[depth - 1].feature < (grp + 1) * GROUP;
+  for (int c = threadIdx.x; c < CELLS; c += RD_THREADS) {
+    const int fl = c / (2 * RD_BINS), rem = c - fl * (2 * RD_BINS);
+    const int bl = rem >> 1, st = rem & 1;
+    const int f = grp * GROUP + fl, b = b0 + bl;
+    if (f >= F || b >= max_bins) continue;
+    const int64_t cell = ((static_cast<int64_t>(leaf) * F + f) * max_bins + b) * 2 + st;
+    if (exact && splits[depth - 1].feature == f) {
+      // the children of the parent's split feature follow exactly from the parent
+      const int k = splits[depth - 1].border;
+      const int64_t pcell = ((static_cast<int64_t>(par) * F + f) * max_bins + b) * 2 + st;
+      const int64_t lcell = ((static_cast<int64_t>(large) * F + f) * max_bins + b) * 2 + st;
+      const double pv = hist_prev[pcell];
+      const bool small_is_child0 = leaf < (1 << (depth - 1));
+      const bool in_child0 = b <= k;
+      put_cell(hist_cur, hist_df, cell, (in_child0 == small_is_child0) ? pv : 0.0);
+      put_cell(hist_cur, hist_df, lcell, (in_child0 == small_is_child0) ? 0.0 : pv);
+      continue;
+    }
+    const double s = tile[fl][bl][st];
+    put_cell(hist_cur, hist_df, cell, s);
+    if (large >= 0) {
+      const int64_t pcell = ((static_cast<int64_t>(par) * F + f) * max_bins + b) * 2 + st;
+      const int64_t lcell = ((static_cast<int64_t>(large) * F + f) * max_bins + b) * 2 + st;
+      put_cell(hist_cur, hist_df, lcell, hist_prev[pcell] - s);
+    }
   }
-  const int u0 = plan->unit_begin[jj], u1 = plan->unit_begin[jj + 1];
-  double s = 0.0;
-  for (int u = u0; u < u1; ++u)
-    s += static_cast<double>(partials[(static_cast<int64_t>(u) * G + grp) * (2 * max_bins * GROUP) + rem]);
-  put_cell(hist_cur, hist_df, cell, s);
-  if (large >= 0) {
-    const int64_t pcell = ((static_cast<int64_t>(plan->parent[jj]) * F + f) * max_bins + b) * 2 + st;
-    const int64_t lcell = ((static_cast<int64_t>(large) * F + f) * max_bins + b) * 2 + st;
-    put_cell(hist_cur, hist_df, lcell, hist_prev[pcell] - s);
-  }
+}
+
+// Grid of reduce_kernel for one level: (bin tiles x groups, directly computed leaves).
+inline dim3 reduce_grid(int G, int max_bins, int n_small) {
+  return dim3(static_cast<unsigned>(G * ((max_bins + RD_BINS - 1) / RD_BINS)), static_cast<unsigned>(n_small));
 }
 
 // Launch geometry of the histogram kernel for one (bins allocation, threads, cluster

@@ -107,9 +107,8 @@ extern "C" cbg_status cbg_histogram_noalloc(cbg_ctx* ctx, const uint8_t* bins, i
   st = gh_dtype == CBG_F32 ? launch_hist<float>(ctx, hc, bins, nullptr, g, h, plan, partials)
                            : launch_hist<__nv_bfloat16>(ctx, hc, bins, nullptr, g, h, plan, partials);
   if (st != CBG_OK) return st;
-  const int per_leaf = hc.G * 2 * max_bins * GROUP;
-  reduce_kernel<<<dim3(static_cast<unsigned>(ceil_div(per_leaf, 256)), 1), 256, 0, ctx->stream>>>(
-      plan, partials, hc.G, F, max_bins, nullptr, hist_out, nullptr, 0, nullptr);
+  reduce_kernel<<<reduce_grid(hc.G, max_bins, 1), RD_THREADS, 0, ctx->stream>>>(plan, partials, hc.G, F, max_bins,
+                                                                               nullptr, hist_out, nullptr, 0, nullptr);
   CBG_CHECK_LAUNCH(ctx);
   return CBG_OK;
 }

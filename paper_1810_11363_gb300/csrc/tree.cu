@@ -230,11 +230,6 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
 
 __device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
 
-__device__ __forceinline__ DF df_from_double(double x) {
-  const float hi = __double2float_rn(x);
-  return DF{hi, __double2float_rn(x - static_cast<double>(hi))};
-}
-
 __device__ __forceinline__ DF df_shfl_up(DF v, int o) {
   return DF{__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
 }
@@ -479,54 +474,123 @@ __device__ void plan_next_level(uint32_t* __restrict__ tile_cnt, int64_t n_ptile
     __syncthreads();
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  // per-parent data, staged in shared memory by all threads: parents in memory order
+  // (i) for the ones-before scan, and by leaf id (p) for the child pairs
+  constexpr int PER_T = (1 << (MAX_DEPTH - 1)) / PT_THREADS;   // parents per thread
+  __shared__ uint32_t s_ones_by_leaf[1 << (MAX_DEPTH - 1)];
+  __shared__ uint32_t s_wsum[PT_THREADS / 32];
   const int L = 1 << depth;
-  uint32_t run = 0;
-  for (int i = 0; i < L; ++i) {
-    const int l = cur->order[i];
-    cur->ones_before[l] = run;
-    run += __ldcg(&cur->ones[l]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) s_ones_by_leaf[i] = __ldcg(&cur->ones[i]);
+  __syncthreads();
+  // block exclusive scan over parents i in memory order (PER_T consecutive per thread)
+  auto block_scan = [&](uint32_t (&v)[PER_T], uint32_t& total) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int q = 0; q < PER_T; ++q) t += v[q];
+    uint32_t x = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    total = 0;
+    for (int w = 0; w < PT_THREADS / 32; ++w) {
+      if (w < warp) before += s_wsum[w];
+      total += s_wsum[w];
+    }
+    __syncthreads();
+    uint32_t run = before + x - t;
+#pragma unroll
+    for (int q = 0; q < PER_T; ++q) {
+      const uint32_t vq = v[q];
+      v[q] = run;
+      run += vq;
+    }
+  };
+  {
+    uint32_t v[PER_T];
+    int leaf_of[PER_T];
+#pragma unroll
+    for (int q = 0; q < PER_T; ++q) {
+      const int i = threadIdx.x * PER_T + q;
+      leaf_of[q] = i < L ? cur->order[i] : -1;
+      v[q] = i < L ? s_ones_by_leaf[leaf_of[q]] : 0u;
+    }
+    uint32_t total;
+    block_scan(v, total);
+#pragma unroll
+    for (int q = 0; q < PER_T; ++q) {
+      const int i = threadIdx.x * PER_T + q;
+      if (i >= L) continue;
+      const int l = leaf_of[q];
+      cur->ones_before[l] = v[q];
+      const int st = cur->start[l], c = cur->cnt[l];
+      const int c1 = static_cast<int>(s_ones_by_leaf[l]);
+      const int c0 = c - c1;
+      nxt->start[l] = st;
+      nxt->cnt[l] = c0;
+      nxt->start[l + L] = st + c0;
+      nxt->cnt[l + L] = c1;
+      nxt->order[2 * i] = l;
+      nxt->order[2 * i + 1] = l + L;
+      nxt->ones[l] = 0;
+      nxt->ones[l + L] = 0;
+    }
   }
-  int units = 0;
-  for (int i = 0; i < L; ++i) {
-    const int l = cur->order[i];
-    const int s = cur->start[l], c = cur->cnt[l];
-    const int c1 = static_cast<int>(__ldcg(&cur->ones[l]));
-    const int c0 = c - c1;
-    nxt->start[l] = s;
-    nxt->cnt[l] = c0;
-    nxt->start[l + L] = s + c0;
-    nxt->cnt[l + L] = c1;
-    nxt->order[2 * i] = l;
-    nxt->order[2 * i + 1] = l + L;
-    nxt->ones[l] = 0;
-    nxt->ones[l + L] = 0;
-  }
-  // pair p = children p and p + L of parent p
-  unsigned long long rows = 0;
-  for (int p = 0; p < L; ++p) {
-    const int a = p, b = p + L;
-    const int small = nxt->cnt[a] <= nxt->cnt[b] ? a : b;
-    const int large = small == a ? b : a;
-    const int m = nxt->cnt[small];
+  // pair p = children p and p + L of parent p; the smaller one is histogrammed directly
+  {
     const int per_unit = rows_per_item * cs;
-    int chunks = (m + per_unit - 1) / per_unit;
-    if (chunks < 1) chunks = 1;
-    plan->small_leaf[p] = small;
-    plan->large_leaf[p] = large;
-    plan->parent[p] = p;
-    plan->unit_begin[p] = units;
-    plan->chunk_rows[p] = m > 0 ? (m + chunks * cs - 1) / (chunks * cs) : 1;
-    plan->seg_start[p] = nxt->start[small];
-    plan->seg_cnt[p] = m;
-    units += chunks;
-    rows += static_cast<unsigned long long>(m);
+    uint32_t v[PER_T];
+    int m_of[PER_T];
+    unsigned long long rows = 0;
+#pragma unroll
+    for (int q = 0; q < PER_T; ++q) {
+      const int p = threadIdx.x * PER_T + q;
+      v[q] = 0;
+      m_of[q] = 0;
+      if (p < L) {
+        const int c = cur->cnt[p];
+        const int c1 = static_cast<int>(s_ones_by_leaf[p]);
+        const int m = min(c - c1, c1);
+        int chunks = (m + per_unit - 1) / per_unit;
+        if (chunks < 1) chunks = 1;
+        v[q] = static_cast<uint32_t>(chunks);
+        m_of[q] = m;
+        rows += static_cast<unsigned long long>(m);
+      }
+    }
+    uint32_t units;
+    block_scan(v, units);
+#pragma unroll
+    for (int q = 0; q < PER_T; ++q) {
+      const int p = threadIdx.x * PER_T + q;
+      if (p >= L) continue;
+      const int c = cur->cnt[p];
+      const int c1 = static_cast<int>(s_ones_by_leaf[p]);
+      const int c0 = c - c1;
+      const bool small_is_a = c0 <= c1;   // ties go to child p
+      const int small = small_is_a ? p : p + L;
+      const int m = m_of[q];
+      const int chunks = (m + per_unit - 1) / per_unit < 1 ? 1 : (m + per_unit - 1) / per_unit;
+      plan->small_leaf[p] = small;
+      plan->large_leaf[p] = small_is_a ? p + L : p;
+      plan->parent[p] = p;
+      plan->unit_begin[p] = static_cast<int>(v[q]);
+      plan->chunk_rows[p] = m > 0 ? (m + chunks * cs - 1) / (chunks * cs) : 1;
+      plan->seg_start[p] = small_is_a ? cur->start[p] : cur->start[p] + c0;
+      plan->seg_cnt[p] = m;
+    }
+    if (rows) atomicAdd(rows_hist, rows);
+    if (threadIdx.x == 0) {
+      plan->unit_begin[L] = static_cast<int>(units);
+      plan->n_small = L;
+      plan->total_units = static_cast<int>(units);
+      plan->level_leaves = 2 * L;
+    }
   }
-  *rows_hist += rows;
-  plan->unit_begin[L] = units;
-  plan->n_small = L;
-  plan->total_units = units;
-  plan->level_leaves = 2 * L;
 }
 
 // The leaf segments of a level in memory order, staged in shared memory: seg_pos[i] is
@@ -888,10 +952,8 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
   if (st != CBG_OK) return st;
   // 2. FP64 reduction of the partials + sibling subtraction
   {
-    const int per_leaf = L.G * 2 * L.max_bins * GROUP;
-    dim3 grid(static_cast<unsigned>(ceil_div(per_leaf, 256)), static_cast<unsigned>(d == 0 ? 1 : (1 << (d - 1))));
-    reduce_kernel<<<grid, 256, 0, ctx->stream>>>(plan, partials, L.G, L.F, L.max_bins, hist_prev, hist_cur,
-                                                 a->splits, d, hist_df);
+    reduce_kernel<<<reduce_grid(L.G, L.max_bins, d == 0 ? 1 : (1 << (d - 1))), RD_THREADS, 0, ctx->stream>>>(
+        plan, partials, L.G, L.F, L.max_bins, hist_prev, hist_cur, a->splits, d, hist_df);
     CBG_CHECK_LAUNCH(ctx);
   }
   // 3. split scores and argmax
