@@ -141,9 +141,18 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+HIST_KERNEL_START = ("template <typename GH, int NB, int MODE>\n__global__ void __launch_bounds__(512, 3) "
+                     "level_hist_kernel(")
+
+
 def hist_source_hash():
-    with open(HIST_SOURCE, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """sha256 (first 16 hex digits) of the default histogram kernel's own source text, from
+    its template line to its closing brace."""
+    with open(HIST_SOURCE) as fh:
+        src = fh.read()
+    start = src.index(HIST_KERNEL_START)
+    end = src.index("\n}\n", start) + 3
+    return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
 
 
 def recorded_traffic_per_row():

@@ -752,8 +752,8 @@ __device__ __forceinline__ void put_cell(double* hist, float2* hist_df, int64_t 
 // (reads coalesced over the group's features), the tile is transposed through shared
 // memory, and the cells go out in the histogram's [leaf][f][b][stat] order (writes
 // coalesced over bins and statistics).
-constexpr int RD_BINS = 8;
-constexpr int RD_THREADS = 256;   // 2 x RD_BINS x 32 = 512 cells, two per thread
+constexpr int RD_BINS = 4;
+constexpr int RD_THREADS = 256;   // 2 x RD_BINS x 32 = 256 cells, one per thread
 
 __global__ void __launch_bounds__(RD_THREADS)
     reduce_kernel(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,

@@ -254,7 +254,7 @@ __device__ __forceinline__ bool better(double s, int k, double bs, int bk) {
 //    best border.
 //  - The last block to finish picks the best feature (ties to the smallest f, then k) and
 //    writes the split.
-constexpr int SC_WARPS = 8;
+constexpr int SC_WARPS = 16;
 constexpr int SC_BINS_PER_LANE = 8;   // 32 lanes x 8 = 256 bins
 
 __global__ void __launch_bounds__(SC_WARPS * 32)
