@@ -77,6 +77,8 @@ def lib():
                 "or_loss": (f64, [i32, f32p, f64p, i64]),
                 "or_fit": (None, [u8p, i64, i32, i32, i32p, i32, f32p, i32, i32, i32, i32, f64, f64,
                                   f64p, i32p, i32p, f64p, f64p, f64p, f64p]),
+                "or_ts_full": (None, [u32p, f32p, i64, f64, f64, u32p, i64, f32p]),
+                "or_predict": (None, [u8p, i64, i32, i32p, i32p, f64p, i32, i32, f64, f64p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -266,6 +268,28 @@ def fit(bins, F: int, n_borders, y, loss_name: str, depth: int, trees: int, lr: 
                  _p(ss, _f64), _p(s2, _f64), _p(lv, _f64), _p(losses, _f64))
     return {"pred": pred, "split_f": sf, "split_k": sk, "score": ss, "second": s2,
             "leaf_values": lv, "losses": losses, "max_bins": max_bins}
+
+
+def ts_full(cat, y, prior_value: float, a: float, cat_new):
+    """Full-data TS of new rows (float32 [m]): every training row counts."""
+    cat, y, cat_new = _c(cat, np.uint32), _c(y, np.float32), _c(cat_new, np.uint32)
+    ts = np.empty(cat_new.shape[0], np.float32)
+    lib().or_ts_full(_p(cat, _u32), _p(y, _f32), cat.shape[0], prior_value, a, _p(cat_new, _u32),
+                     cat_new.shape[0], _p(ts, _f32))
+    return ts
+
+
+def predict(bins, split_f, split_k, leaf_values, lr: float):
+    """Model value of every row of bins [n][F_pad] (FP64): sum over trees of lr x the leaf
+    value its bins select."""
+    bins = _c(bins, np.uint8)
+    sf, sk = _c(split_f, np.int32), _c(split_k, np.int32)
+    lv = _c(leaf_values, np.float64)
+    T, D = sf.shape
+    pred = np.empty(bins.shape[0], np.float64)
+    lib().or_predict(_p(bins, _u8), bins.shape[0], bins.shape[1], _p(sf, _i32), _p(sk, _i32), _p(lv, _f64), T, D,
+                     lr, _p(pred, _f64))
+    return pred
 
 
 def preprocess(workload, F_pad: int):

@@ -25,6 +25,10 @@
 //                    tree) + Section 4 "Fast scorer" (one split per level)
 //   leaf index       Section 4 "Fast scorer": leaf = sum_i 2^i B(x, f(t,i))
 //   leaf values      Section 3: gradient / Newton step leaf values
+//   full-data TS     Section 2 (Eq. 1 with every training row "before" a new row):
+//                    the statistic of a row that is not in the training permutation
+//   prediction       Section 4 "Fast scorer": a row's model value is the sum over
+//                    trees of the value of the leaf its binary features select
 //
 // Parity pins for every function live in tests/test_oracle_*.py.
 
@@ -387,6 +391,49 @@ void or_fit(const uint8_t* bins, int64_t n, int F_pad, int F, const int* n_borde
     for (int l = 0; l < L; ++l) leaf_values[static_cast<int64_t>(t) * L + l] = v[l];
     or_apply_leaf_values(leaf.data(), n, v.data(), lr, pred);
     losses[t] = or_loss(loss, y, pred, n);
+  }
+}
+
+// ------------------------------------------------------------- full-data TS
+// For rows outside the training data (inference), every training row counts as
+// "before": per category, S = sum of the labels and N = the number of training rows
+// with that category (in row order); a new row with category c gets
+// (S_c + a*P) / (N_c + a), and an unseen category gets (0 + a*P) / (0 + a).
+void or_ts_full(const uint32_t* cat, const float* y, int64_t n, double prior, double a,
+                const uint32_t* cat_new, int64_t m, float* ts) {
+  std::unordered_map<uint32_t, std::pair<double, double>> stats;
+  for (int64_t r = 0; r < n; ++r) {
+    auto& st = stats[cat[r]];
+    st.first += static_cast<double>(y[r]);
+    st.second += 1.0;
+  }
+  for (int64_t i = 0; i < m; ++i) {
+    auto it = stats.find(cat_new[i]);
+    const double S = it == stats.end() ? 0.0 : it->second.first;
+    const double N = it == stats.end() ? 0.0 : it->second.second;
+    ts[i] = static_cast<float>((S + a * prior) / (N + a));
+  }
+}
+
+// --------------------------------------------------------------- prediction
+// Model value of every row: sum over trees t (in order) of lr * v_t[leaf_t(row)],
+// where leaf_t(row) = sum_d 2^d [bin(row, f_td) > k_td] (a level with f_td < 0 sends
+// every row to its 0 side). bins is row-major [n][F_pad]; split_f, split_k are
+// [T][D] and leaf_values [T][2^D] (before the learning rate).
+void or_predict(const uint8_t* bins, int64_t n, int F_pad, const int* split_f, const int* split_k,
+                const double* leaf_values, int trees, int depth, double lr, double* pred) {
+  const int64_t L = int64_t(1) << depth;
+  for (int64_t r = 0; r < n; ++r) {
+    double s = 0.0;
+    for (int t = 0; t < trees; ++t) {
+      int64_t leaf = 0;
+      for (int d = 0; d < depth; ++d) {
+        const int f = split_f[t * depth + d];
+        if (f >= 0 && bins[r * F_pad + f] > split_k[t * depth + d]) leaf |= int64_t(1) << d;
+      }
+      s += lr * leaf_values[t * L + leaf];
+    }
+    pred[r] = s;
   }
 }
 
