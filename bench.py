@@ -54,6 +54,8 @@ def parse_args():
                    help="problems of the batched_256 workload for the batched-vs-plain comparison (0 = skip)")
     p.add_argument("--batched-trees", type=int, default=20)
     p.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-storage comparison step")
+    p.add_argument("--scorer-trees", type=int, default=8000,
+                   help="trees of the model-prediction measurement (0 = skip)")
     return p.parse_args()
 
 
@@ -258,6 +260,44 @@ def batched_comparison(ctx, n_problems, trees, dev):
             "autotune_setup_s": tune_s}
 
 
+def scorer_bench(ctx, dev, trees, rows=100_000, F=2000, depth=6, reps=5):
+    """Model prediction (cbg_predict) on the shape of the paper's scorer comparison: 10^5
+    Epsilon-shaped rows (2000 features, 129 bins) through `trees` depth-6 trees with
+    random splits and leaf values. The 200 MB bin matrix is larger than L2."""
+    import torch
+    from paper_1810_11363_gb300 import cbg, train
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    bins_t = torch.randint(0, 129, (F, rows), dtype=torch.uint8, device=dev, generator=g)
+    rec = torch.zeros((trees, depth, 2), dtype=torch.float64, device=dev)
+    fk = rec.view(torch.int32).view(trees, depth, 4)
+    fk[:, :, 0] = torch.randint(0, F, (trees, depth), dtype=torch.int32, device=dev, generator=g)
+    fk[:, :, 1] = torch.randint(0, 128, (trees, depth), dtype=torch.int32, device=dev, generator=g)
+    values = torch.randn((trees, 1 << depth), dtype=torch.float64, device=dev, generator=g)
+    model = train.Model(rec, values, None, depth, 0.1)
+    pred = torch.zeros(rows, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        pred.zero_()
+        train.predict(ctx, model, bins_t, F, pred=pred)
+    ms = []
+    for _ in range(reps):
+        pred.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        train.predict(ctx, model, bins_t, F, pred=pred)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    cbg.cbg_sync(ctx)
+    t = statistics.median(ms)
+    return {"workload": f"{rows} rows x {F} features (129 bins) through {trees} depth-{depth} trees, random "
+                        "splits and leaf values", "ms": t, "rows_x_trees_per_s": rows * trees / (t / 1e3),
+            "timing": f"CUDA events, median of {reps} calls after 2 untimed",
+            "paper_table3_context": "CatBoost CPU scorer on Epsilon, 8000 trees: 2.4 s (1 thread), 231 ms "
+                                    "(32 threads), Intel Xeon E5-2660"}
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args):
     ws, rank, _ = dist_env()
@@ -436,11 +476,15 @@ def run_ours(args):
     batched = None
     if args.batched_problems > 0 and rank == 0:
         batched = batched_comparison(ctx, args.batched_problems, args.batched_trees, dev)
+    scorer = None
+    if args.scorer_trees > 0 and rank == 0:
+        scorer = scorer_bench(ctx, dev, args.scorer_trees)
 
-    launches_per_step = None
-    # kernels of ours per step: preprocessing launches + per tree (levels x kernels + apply)
-    per_level = 7
-    launches_per_step = T * ((D - 1) * per_level + 5 + 1)
+    # kernels of ours per step: the preprocessing launches of logloss_1m (359, counted in
+    # its ncu launch list), the first gradients, and per tree: tree_begin, 5 kernels per
+    # level (histogram, reduction, scoring, partition flags, scatter; no scatter at the
+    # last level), apply, and the record kernel of a graph replay
+    launches_per_step = 359 + 1 + T * (1 + 5 * D - 1 + 1 + (1 if use_graph else 0))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -461,7 +505,7 @@ def run_ours(args):
                            "gh_storage": args.gh, "graph_replay": use_graph, "hist_tiles": tiles},
                 "row_feature_bins_per_s": rfb, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "forms": forms, "batched_vs_plain": batched,
+                "forms": forms, "batched_vs_plain": batched, "scorer": scorer,
                 "breakdown": {"step_ms": step_ms}}
         print(json.dumps(line), flush=True)
     if ws > 1:

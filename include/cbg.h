@@ -355,6 +355,58 @@ cbg_status cbg_profile_read(cbg_ctx* ctx, int reset, double* hist_ms, int64_t* h
 cbg_status cbg_tree_rows_histogrammed(cbg_ctx* ctx, const cbg_tree_shape* shape, void* state, int reset,
                                       int64_t* rows);
 
+/* ------------------------------------------------------------ inference -- */
+
+/* Full-data target-statistic table of one categorical column, for rows that are
+ * not in the training permutation (Section 2, Eq. 1 with every training row
+ * counted as seen before the new row). The table lists the distinct category
+ * ids ascending, each with the label sum S and the count N over all n training
+ * rows.
+ * cat: device uint32 [n]; y: device float [n].
+ * ids, cnts: device uint32 [n]; sums: device double [n]. The first *n_unique
+ * entries are written.
+ * n_unique: device int32 [1].
+ * Binary-label sums are exact integers; real-label sums are FP64 segmented sums
+ * (another order than the row order). Uses the context workspace. */
+cbg_status cbg_ts_table(cbg_ctx* ctx, const uint32_t* cat, const float* y, int64_t n, int label_kind,
+                        uint32_t* ids, double* sums, uint32_t* cnts, int32_t* n_unique);
+
+/* Target statistic of m new rows from a cbg_ts_table table: a row with
+ * category c gets (S_c + a*P) / (N_c + a), evaluated in FP64 without fused
+ * multiply-add and rounded to float; a category absent from the table gets
+ * (0 + a*P)/(0 + a).
+ * ids/sums/cnts/n_unique: device, as written by cbg_ts_table.
+ * cat_new: device uint32 [m]; ts: device float [m].
+ * prior P and a > 0: host doubles. */
+cbg_status cbg_ts_apply(cbg_ctx* ctx, const uint32_t* ids, const double* sums, const uint32_t* cnts,
+                        const int32_t* n_unique, const uint32_t* cat_new, int64_t m, double prior, double a,
+                        float* ts);
+
+/* Model prediction (Section 4 "Fast scorer"). For every row r, trees t = 0..T-1 in
+ * order:
+ *   leaf = sum_d 2^d [bin(r, f_td) > k_td]
+ *   pred[r] += float(lr * leaf_values[t][leaf])
+ * The sum is in FP32 in tree order, the same arithmetic as cbg_apply_tree, so
+ * the training rows get back their training predictions bit for bit. A level
+ * with feature -1 sends every row to its 0 side.
+ * bins_t: device uint8 [F][n] (column-major, as cbg_quantize writes it);
+ * splits: device cbg_split [T][depth]; leaf_values: device double [T][2^depth]
+ * (before the learning rate); pred: device float [n], in/out (zero it for a
+ * fresh prediction). depth 1..10. Uses the context workspace for the per-tree
+ * increments float(lr * v). */
+typedef struct cbg_predict_args {
+  const uint8_t* bins_t;
+  int64_t n;
+  int32_t F;
+  const cbg_split* splits;
+  const double* leaf_values;
+  int32_t trees;
+  int32_t depth;
+  double lr;
+  float* pred;
+} cbg_predict_args;
+cbg_status cbg_predict(cbg_ctx* ctx, const cbg_predict_args* args);
+
 /* ------------------------------------------------------------ autotuner -- */
 
 /* Histogram-tile autotuner. The paper has no counterpart: it picks the tiling

@@ -51,6 +51,11 @@ class AutotuneArgs(C.Structure):
                 ("child_totals", c_vp), ("reps", c_i32)]
 
 
+class PredictArgs(C.Structure):
+    _fields_ = [("bins_t", c_vp), ("n", c_i64), ("F", c_i32), ("splits", c_vp), ("leaf_values", c_vp),
+                ("trees", c_i32), ("depth", c_i32), ("lr", c_f64), ("pred", c_vp)]
+
+
 class LevelArgs(C.Structure):
     _fields_ = [("shape", C.POINTER(TreeShape)), ("state", c_vp), ("state_bytes", C.c_size_t),
                 ("bins", c_vp), ("bins_t", c_vp), ("n_borders", c_vp), ("g", c_vp), ("h", c_vp),
@@ -106,6 +111,9 @@ SIGNATURES = {
     "cbg_profile_enable": (c_i32, [c_vp, C.c_int]),
     "cbg_profile_read": (c_i32, [c_vp, C.c_int, C.POINTER(c_f64), C.POINTER(c_i64)]),
     "cbg_tree_rows_histogrammed": (c_i32, [c_vp, C.POINTER(TreeShape), c_vp, C.c_int, C.POINTER(c_i64)]),
+    "cbg_ts_table": (c_i32, [c_vp, c_vp, c_vp, c_i64, C.c_int, c_vp, c_vp, c_vp, c_vp]),
+    "cbg_ts_apply": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_f64, c_f64, c_vp]),
+    "cbg_predict": (c_i32, [c_vp, C.POINTER(PredictArgs)]),
     "cbg_autotune_state_bytes": (c_i32, [C.POINTER(TreeShape), C.POINTER(C.c_size_t)]),
     "cbg_autotune_tiles": (c_i32, [c_vp, C.POINTER(AutotuneArgs), C.POINTER(Tiles), C.POINTER(c_f64)]),
 }
@@ -283,6 +291,22 @@ def cbg_tree_rows_histogrammed(ctx: Context, shape: TreeShape, state, reset: boo
     ctx.check(ctx.lib.cbg_tree_rows_histogrammed(ctx.h, C.byref(shape), _p(state), int(reset), C.byref(rows)),
               "cbg_tree_rows_histogrammed")
     return int(rows.value)
+
+
+def cbg_ts_table(ctx: Context, cat, y, n: int, label_kind: str, ids, sums, cnts, n_unique):
+    ctx.check(ctx.lib.cbg_ts_table(ctx.h, _p(cat), _p(y), n, LABEL[label_kind], _p(ids), _p(sums), _p(cnts),
+                                   _p(n_unique)), "cbg_ts_table")
+
+
+def cbg_ts_apply(ctx: Context, ids, sums, cnts, n_unique, cat_new, m: int, prior: float, a: float, ts):
+    ctx.check(ctx.lib.cbg_ts_apply(ctx.h, _p(ids), _p(sums), _p(cnts), _p(n_unique), _p(cat_new), m, prior, a,
+                                   _p(ts)), "cbg_ts_apply")
+
+
+def cbg_predict(ctx: Context, bins_t, n: int, F: int, splits, leaf_values, trees: int, depth: int, lr: float,
+                pred):
+    a = PredictArgs(_p(bins_t), n, F, _p(splits), _p(leaf_values), trees, depth, lr, _p(pred))
+    ctx.check(ctx.lib.cbg_predict(ctx.h, C.byref(a)), "cbg_predict")
 
 
 def cbg_autotune_state_bytes(shape: TreeShape) -> int:

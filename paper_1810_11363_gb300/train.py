@@ -3,6 +3,9 @@
 preprocess(): permutation sigma, prior, ordered target statistics (Section 2, Eq. 1),
 quantile borders and uint8 quantisation of float and TS columns (Section 4).
 fit(): classic boosting of oblivious trees through cbg_boost (Sections 3-4).
+ts_tables() / preprocess_new() / predict(): the inference path: full-data statistics of
+new rows, quantisation with the training borders, and the model value (Section 4,
+"Fast scorer").
 All arithmetic runs in libcbg's kernels; this module only allocates and marshals.
 """
 from __future__ import annotations
@@ -206,3 +209,68 @@ def fit_batched(ctx: cbg.Context, preps, ys, losses, depth: int, trees: int, lr:
         probs.append(pr)
     cbg.cbg_boost_batched(ctx, probs, gh_dtype, depth, trees, lr, l2, branches)
     return [Model(b.splits[:trees], b.leaf_values[:trees], b.pred, depth, lr) for b in bufs], bufs
+
+
+# ------------------------------------------------------------------ inference
+@dataclass
+class TSTable:
+    ids: object       # uint32 (as int32 tensor) [n]: distinct category ids ascending
+    sums: object      # float64 [n]: label sums
+    cnts: object      # uint32 (as int32 tensor) [n]: counts
+    n_unique: object  # int32 [1] on the device
+
+
+def ts_tables(ctx: cbg.Context, cat, y, label_kind: str):
+    """One full-data statistic table per categorical column of cat [C][n] (cbg_ts_table)."""
+    import torch
+    dev = y.device
+    n = int(y.numel())
+    out = []
+    for c in range(int(cat.shape[0])):
+        t = TSTable(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.float64, device=dev),
+                    torch.empty(n, dtype=torch.int32, device=dev), torch.empty(1, dtype=torch.int32, device=dev))
+        cbg.cbg_ts_table(ctx, cat[c], y, n, label_kind, t.ids, t.sums, t.cnts, t.n_unique)
+        out.append(t)
+    return out
+
+
+def ts_apply(ctx: cbg.Context, tables, cat_new, prior: float, a: float = 1.0):
+    """Statistics of new rows cat_new [C][m] from the training tables: float32 [C][m]."""
+    import torch
+    m = int(cat_new.shape[1]) if cat_new.dim() == 2 else 0
+    ts = torch.empty((len(tables), m), dtype=torch.float32, device=cat_new.device)
+    for c, t in enumerate(tables):
+        cbg.cbg_ts_apply(ctx, t.ids, t.sums, t.cnts, t.n_unique, cat_new[c], m, prior, a, ts[c])
+    return ts
+
+
+def preprocess_new(ctx: cbg.Context, prep: Prepared, tables, x_new, cat_new, a: float = 1.0):
+    """Column-major bins [F][m] of new rows with the training borders: floats as given,
+    categoricals through their full-data statistics (ts_apply)."""
+    import torch
+    m = int(x_new.shape[1]) if x_new.shape[0] else int(cat_new.shape[1])
+    dev = x_new.device
+    F = prep.F
+    max_borders = int(prep.borders.shape[1])
+    bins = torch.zeros(prep.F_pad * m, dtype=torch.uint8, device=dev)
+    bins_t = torch.empty((F, m), dtype=torch.uint8, device=dev)
+    Ff = prep.F_float
+    if Ff:
+        cbg.cbg_quantize(ctx, x_new, m, Ff, prep.borders[:Ff], prep.n_borders[:Ff], max_borders, bins, prep.F_pad, 0,
+                         bins_t)
+    if F > Ff:
+        ts = ts_apply(ctx, tables, cat_new, prep.prior, a)
+        cbg.cbg_quantize(ctx, ts, m, F - Ff, prep.borders[Ff:], prep.n_borders[Ff:], max_borders, bins, prep.F_pad,
+                         Ff, bins_t)
+    return bins_t
+
+
+def predict(ctx: cbg.Context, model: Model, bins_t, F: int, trees: int | None = None, pred=None):
+    """Model value of every row of bins_t [F][m] (cbg_predict), float32 [m]."""
+    import torch
+    m = int(bins_t.shape[1])
+    T = int(model.splits.shape[0]) if trees is None else trees
+    if pred is None:
+        pred = torch.zeros(m, dtype=torch.float32, device=bins_t.device)
+    cbg.cbg_predict(ctx, bins_t, m, F, model.splits, model.leaf_values, T, model.depth, model.lr, pred)
+    return pred
