@@ -56,6 +56,8 @@ def parse_args():
     p.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-storage comparison step")
     p.add_argument("--scorer-trees", type=int, default=8000,
                    help="trees of the model-prediction measurement (0 = skip)")
+    p.add_argument("--paper-setting-trees", type=int, default=200,
+                   help="trees of the 4e5 x 2000, 15-border, depth-6 measurement (0 = skip)")
     return p.parse_args()
 
 
@@ -298,6 +300,44 @@ def scorer_bench(ctx, dev, trees, rows=100_000, F=2000, depth=6, reps=5):
                                     "(32 threads), Intel Xeon E5-2660"}
 
 
+def paper_setting_bench(ctx, dev, trees, n=400_000, F=2000, borders=15, depth=6):
+    """Tree construction on the setting of the paper's own GPU timing (Section 5): an
+    Epsilon-shaped dense problem (4e5 x 2000 N(0,1), y ~ Bernoulli(sigmoid(w.x)), w ~
+    N(0, 1/2000)), 15 borders, depth 6, classic boosting, no subsampling; histogram
+    tiles from the autotuner. Mean construction time per tree with graph replay."""
+    import math
+
+    import torch
+    from paper_1810_11363_gb300 import cbg, train
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    x = torch.randn((F, n), generator=g, device=dev)
+    wv = torch.randn(F, generator=g, device=dev) / math.sqrt(F)
+    y = (torch.rand(n, generator=g, device=dev) < torch.sigmoid(wv @ x)).float()
+    cat = torch.zeros((0, n), dtype=torch.int32, device=dev)
+    prep = train.preprocess(ctx, x, cat, y, "binary", borders, seed=0)
+    del x
+    tiles, _ = train.autotune(ctx, prep, y, "logloss", depth)
+    bufs = train.alloc_fit(prep, depth, trees, tiles=tiles)
+    stream = torch.cuda.current_stream(dev)
+    train.fit(ctx, prep, y, "logloss", depth, min(trees, 5), 0.1, 3.0, bufs=bufs, use_graph=True)   # warm-up
+    bufs.pred.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    train.fit(ctx, prep, y, "logloss", depth, trees, 0.1, 3.0, bufs=bufs, use_graph=True)
+    e1.record(stream)
+    e1.synchronize()
+    cbg.cbg_sync(ctx)
+    ms = e0.elapsed_time(e1)
+    return {"workload": f"Epsilon-shaped {n} x {F} dense N(0,1), logistic labels, {borders} borders "
+                        f"({prep.max_bins} bins), depth {depth}, {trees} trees, lr 0.1, L2 3",
+            "ms_per_tree": ms / trees, "trees_per_s": trees / (ms / 1e3),
+            "hist_tiles": {"kernel": tiles["kernel"], "cluster": tiles["cluster"],
+                           "rows_per_item": tiles["rows_per_item"]},
+            "paper_context": "CatBoost GPU, Epsilon, 15 bins, depth 6, classic scheme: 17.9 ms/tree on "
+                             "an NVIDIA P100 (not the same data or hardware)"}
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args):
     ws, rank, _ = dist_env()
@@ -479,6 +519,9 @@ def run_ours(args):
     scorer = None
     if args.scorer_trees > 0 and rank == 0:
         scorer = scorer_bench(ctx, dev, args.scorer_trees)
+    paper_setting = None
+    if args.paper_setting_trees > 0 and rank == 0:
+        paper_setting = paper_setting_bench(ctx, dev, args.paper_setting_trees)
 
     # kernels of ours per step: the preprocessing launches of logloss_1m (359, counted in
     # its ncu launch list), the first gradients, and per tree: tree_begin, 5 kernels per
@@ -505,7 +548,7 @@ def run_ours(args):
                            "gh_storage": args.gh, "graph_replay": use_graph, "hist_tiles": tiles},
                 "row_feature_bins_per_s": rfb, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "forms": forms, "batched_vs_plain": batched, "scorer": scorer,
+                "forms": forms, "batched_vs_plain": batched, "scorer": scorer, "paper_setting": paper_setting,
                 "breakdown": {"step_ms": step_ms}}
         print(json.dumps(line), flush=True)
     if ws > 1:

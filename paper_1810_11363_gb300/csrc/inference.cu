@@ -91,20 +91,27 @@ __global__ void ts_apply_kernel(const uint32_t* __restrict__ ids, const double* 
 }
 
 // float(lr * v) for every leaf of every tree, and the splits packed as (feature, border).
+// A level without a split (feature -1, or one outside [0, F)) becomes (0, 255): no bin is
+// above 255, so every row takes its 0 side without a test in the hot loop.
 __global__ void predict_prep_kernel(const cbg_split* __restrict__ splits, const double* __restrict__ values,
-                                    int64_t n_values, int64_t n_splits, double lr, float* __restrict__ inc,
+                                    int64_t n_values, int64_t n_splits, int F, double lr, float* __restrict__ inc,
                                     int2* __restrict__ fk) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_values;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     inc[i] = static_cast<float>(lr * values[i]);
-    if (i < n_splits) fk[i] = make_int2(splits[i].feature, splits[i].border);
+    if (i < n_splits) {
+      const int f = splits[i].feature;
+      fk[i] = (f >= 0 && f < F) ? make_int2(f, splits[i].border) : make_int2(0, 255);
+    }
   }
 }
 
 // One thread per row, every tree in order. The splits and increments of a chunk of trees
 // are staged in shared memory by the whole block; the rows of a block read each split's
 // bin column as consecutive bytes (column-major bins). All blocks sweep the trees in the
-// same order, so the feature columns the current chunk needs stay in L2.
+// same order, so the feature columns the current chunk needs stay in L2. One row per
+// thread leaves few warps per SM (10^5 rows: 20), so the tree loop is unrolled by 4 to
+// keep 4 x depth independent bin loads of a thread in flight.
 constexpr int PRED_THREADS = 256;
 constexpr int PRED_SMEM_FLOATS = 8192;   // increments of one chunk: trees x 2^depth
 
@@ -119,6 +126,7 @@ __global__ void __launch_bounds__(PRED_THREADS) predict_kernel(const uint8_t* __
   __shared__ int2 s_fk[TC * D];
   const int64_t r = blockIdx.x * static_cast<int64_t>(PRED_THREADS) + threadIdx.x;
   const bool live = r < n;
+  const uint8_t* col = bins_t + (live ? r : 0);
   float acc = live ? pred[r] : 0.f;
   for (int t0 = 0; t0 < trees; t0 += TC) {
     const int tc = min(TC, trees - t0);
@@ -127,13 +135,13 @@ __global__ void __launch_bounds__(PRED_THREADS) predict_kernel(const uint8_t* __
     for (int i = threadIdx.x; i < tc * D; i += PRED_THREADS) s_fk[i] = fk[static_cast<int64_t>(t0) * D + i];
     __syncthreads();
     if (!live) continue;
-#pragma unroll 2
+#pragma unroll 4
     for (int t = 0; t < tc; ++t) {
       int leaf = 0;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const int2 s = s_fk[t * D + d];
-        if (s.x >= 0 && s.x < F && bins_t[static_cast<int64_t>(s.x) * n + r] > s.y) leaf |= 1 << d;
+        if (__ldg(col + static_cast<int64_t>(s.x) * n) > s.y) leaf |= 1 << d;
       }
       acc += s_inc[t * L + leaf];
     }
@@ -229,7 +237,7 @@ cbg_status cbg_predict(cbg_ctx* ctx, const cbg_predict_args* a) {
   float* inc = cv.take<float>(n_values);
   int2* fk = cv.take<int2>(n_splits);
   predict_prep_kernel<<<grid_for(n_values), BLOCK, 0, ctx->stream>>>(a->splits, a->leaf_values, n_values, n_splits,
-                                                                     a->lr, inc, fk);
+                                                                     a->F, a->lr, inc, fk);
   CBG_CHECK_LAUNCH(ctx);
   switch (a->depth) {
     case 1: return launch_predict<1>(ctx, a, fk, inc);
