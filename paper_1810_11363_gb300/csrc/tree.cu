@@ -18,6 +18,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 using namespace cbg;
@@ -246,7 +247,8 @@ __device__ __forceinline__ bool better(double s, int k, double bs, int bk) {
 // per level, scored over every leaf of the level). It reads the compensated FP32 copy
 // (hi, lo) of the FP64 histogram that the reduction writes, so it runs on the FP32 pipe
 // alone (GB300 executes FP64 at 1/64 of the FP32 rate).
-//  - Warp w takes leaves w, w + SC_WARPS, ... For each it forms compensated prefix sums
+//  - A block has min(16, 2^d) warps; warp w takes leaves w, w + warps, ... For each it
+//    forms compensated prefix sums
 //    over bins (lane i owns bins [8i, 8i + 8), then a warp scan), so G_L(k), H_L(k) and
 //    the leaf totals come out at about 2^-44 relative, and adds the FP32 term
 //    G_L^2/(H_L+l2) + G_R^2/(H_R+l2) of every border to its own compensated accumulators.
@@ -254,9 +256,10 @@ __device__ __forceinline__ bool better(double s, int k, double bs, int bk) {
 //    best border.
 //  - The last block to finish picks the best feature (ties to the smallest f, then k) and
 //    writes the split.
-constexpr int SC_WARPS = 16;
+constexpr int SC_MAX_WARPS = 16;
 constexpr int SC_BINS_PER_LANE = 8;   // 32 lanes x 8 = 256 bins
 
+template <int SC_WARPS>
 __global__ void __launch_bounds__(SC_WARPS * 32)
     score_level_kernel(const float2* __restrict__ hist_df, int level_leaves, int F, int max_bins,
                        const int32_t* __restrict__ n_borders, double l2, BestF* __restrict__ best, Misc* misc,
@@ -958,10 +961,20 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
   }
   // 3. split scores and argmax
   const int level_leaves = 1 << d;
-  score_level_kernel<<<L.F, SC_WARPS * 32, 0, ctx->stream>>>(hist_df, level_leaves, L.F, L.max_bins, a->n_borders,
+  {
+    auto launch = [&](auto warps) {
+      constexpr int W = decltype(warps)::value;
+      score_level_kernel<W><<<L.F, W * 32, 0, ctx->stream>>>(hist_df, level_leaves, L.F, L.max_bins, a->n_borders,
                                                            a->l2, best, misc, a->force_feature, a->force_border, d,
                                                            a->splits);
-  CBG_CHECK_LAUNCH(ctx);
+    };
+    if (level_leaves >= SC_MAX_WARPS) launch(std::integral_constant<int, SC_MAX_WARPS>{});
+    else if (level_leaves >= 8) launch(std::integral_constant<int, 8>{});
+    else if (level_leaves >= 4) launch(std::integral_constant<int, 4>{});
+    else if (level_leaves >= 2) launch(std::integral_constant<int, 2>{});
+    else launch(std::integral_constant<int, 1>{});
+    CBG_CHECK_LAUNCH(ctx);
+  }
   if (a->hist_out)
     CBG_CUDA(ctx, cudaMemcpyAsync(a->hist_out, hist_cur,
                                   static_cast<size_t>(level_leaves) * L.F * L.max_bins * 2 * sizeof(double),
