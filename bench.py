@@ -145,18 +145,21 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+HIST_ITEM_START = "template <typename GH, int NB, int MODE>\n__device__ __forceinline__ void hist_item("
 HIST_KERNEL_START = ("template <typename GH, int NB, int MODE>\n__global__ void __launch_bounds__(512, 3) "
                      "level_hist_kernel(")
 
 
 def hist_source_hash():
-    """sha256 (first 16 hex digits) of the default histogram kernel's own source text, from
-    its template line to its closing brace."""
+    """sha256 (first 16 hex digits) of the default histogram kernel's source text: its
+    per-item routine and the kernel, each from its template line to its closing brace."""
     with open(HIST_SOURCE) as fh:
         src = fh.read()
-    start = src.index(HIST_KERNEL_START)
-    end = src.index("\n}\n", start) + 3
-    return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
+    parts = []
+    for marker in (HIST_ITEM_START, HIST_KERNEL_START):
+        start = src.index(marker)
+        parts.append(src[start:src.index("\n}\n", start) + 3])
+    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
 
 
 def recorded_traffic_per_row():

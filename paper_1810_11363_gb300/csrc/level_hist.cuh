@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "cbg_internal.cuh"
 
@@ -94,98 +95,190 @@ __device__ __forceinline__ void cas_add2(float2* p, float gx, float hy) {
   }
 }
 
+// One problem's inputs to a histogram launch (the batched form passes a table of them).
+struct HistProblem {
+  const uint8_t* bins;
+  int64_t n;
+  int G, F;
+  const uint32_t* order;    // row order of the level (NULL: identity)
+  const void* g;            // gradients / hessians (by row), GH
+  const void* h;
+  const Plan* plan;
+  int max_bins;
+  float* partials;
+};
+
+// One work item (unit x group) of one problem, for this CTA of the cluster: accumulate
+// the item's rows into the CTA's shared histogram, then sum this CTA's slice of bins over
+// the cluster (distributed shared memory) into the item's FP32 partial.
+template <typename GH, int NB, int MODE>
+__device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs, int rank, float* hsh,
+                                          const float* const* peer, uint32_t sbase) {
+  namespace cgr = cooperative_groups;
+  constexpr int PLANE = NB * GROUP;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int j = lane >> 1, c = lane & 1;
+  uint32_t off[16];   // lane (j, c) updates feature 16c + (l + j) % 16 at iteration l
+#pragma unroll
+  for (int l = 0; l < 16; ++l) off[l] = sbase + 4u * static_cast<uint32_t>(c * 16 + ((l + j) & 15));
+  const Plan* plan = P.plan;
+  const int G = P.G;
+  const int unit = item / G, grp = item - unit * G;
+  // leaf of this unit: last jj with unit_begin[jj] <= unit
+  int lo = 0, hi = plan->n_small - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (plan->unit_begin[mid] <= unit) lo = mid; else hi = mid - 1;
+  }
+  const int jj = lo;
+  const int chunk = unit - plan->unit_begin[jj];
+  const int seg_s = plan->seg_start[jj], seg_c = plan->seg_cnt[jj];
+  const int cr = plan->chunk_rows[jj];
+  const int p0 = seg_s + (chunk * cs + rank) * cr;
+  const int p1 = min(seg_s + seg_c, p0 + cr);
+  // zero the rows the problem's bins use (rows at or above max_bins are never read)
+  if (MODE == 0) {   // two planes [NB][32]
+    const int rows4 = P.max_bins * GROUP / 4;   // float4 per plane
+    for (int i = threadIdx.x; i < 2 * rows4; i += blockDim.x) {
+      const int st = i / rows4;
+      reinterpret_cast<float4*>(hsh + st * PLANE)[i - st * rows4] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  } else {           // interleaved [NB][32] float2
+    for (int i = threadIdx.x; i < P.max_bins * GROUP / 2; i += blockDim.x)
+      reinterpret_cast<float4*>(hsh)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  const bool active = grp * GROUP + c * 16 < P.F;
+  const uint8_t* gbase = P.bins + static_cast<int64_t>(grp) * P.n * GROUP + c * 16;
+  const GH* g = static_cast<const GH*>(P.g);
+  const GH* h = static_cast<const GH*>(P.h);
+  const uint32_t* order = P.order;
+  if (active) {
+    for (int pos = p0 + warp * 16 + j; pos < p1; pos += nw * 16) {
+      const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(gbase + static_cast<int64_t>(row) * GROUP));
+      const float gv = cbgd::load_gh(g, row), hv = cbgd::load_gh(h, row);
+      // rotate the 16 bytes so that byte l of R is byte (l + j) % 16 of v
+      uint32_t w0 = v.x, w1 = v.y, w2 = v.z, w3 = v.w;
+      const int q = (j >> 2) & 3, r = j & 3;
+      if (q & 2) {
+        uint32_t t = w0; w0 = w2; w2 = t;
+        t = w1; w1 = w3; w3 = t;
+      }
+      if (q & 1) {
+        uint32_t t = w0; w0 = w1; w1 = w2; w2 = w3; w3 = t;
+      }
+      uint32_t R[4];
+      R[0] = __funnelshift_r(w0, w1, 8 * r);
+      R[1] = __funnelshift_r(w1, w2, 8 * r);
+      R[2] = __funnelshift_r(w2, w3, 8 * r);
+      R[3] = __funnelshift_r(w3, w0, 8 * r);
+#pragma unroll
+      for (int l = 0; l < 16; ++l) {
+        const uint32_t b = (R[l >> 2] >> (8 * (l & 3))) & (NB - 1);
+        if (MODE == 0) {
+          const uint32_t a = off[l] + b * (GROUP * 4);
+          red_add(a, gv);
+          red_add(a + PLANE * 4, hv);
+        } else {
+          // off[l] - sbase is 4 x (feature within the group)
+          const uint32_t f = (off[l] - sbase) >> 2;
+          cas_add2(reinterpret_cast<float2*>(hsh) + b * GROUP + f, gv, hv);
+        }
+      }
+    }
+  }
+  cgr::this_cluster().sync();
+  // this CTA's slice of bins, summed over the cluster's CTAs in rank order
+  const int max_bins = P.max_bins;
+  const int bs = (max_bins + cs - 1) / cs;
+  const int b0 = rank * bs;
+  const int nbs = max(0, min(max_bins, b0 + bs) - b0);
+  float* dst = P.partials + static_cast<int64_t>(item) * (2 * max_bins * GROUP);
+  for (int i = threadIdx.x; i < 2 * nbs * GROUP; i += blockDim.x) {
+    const int st = i / (nbs * GROUP), rem = i - st * (nbs * GROUP);
+    const int e = MODE == 0 ? st * PLANE + b0 * GROUP + rem : (b0 * GROUP + rem) * 2 + st;
+    float v = 0.f;
+    for (int r = 0; r < cs; ++r) v += peer[r][e];
+    dst[st * (max_bins * GROUP) + b0 * GROUP + rem] = v;
+  }
+  cgr::this_cluster().sync();
+}
+
+// Cluster geometry shared by the single-problem and batched kernels: rank, cluster index,
+// and the peers' shared histograms.
+struct HistCta {
+  int cs, rank, cid, ncl;
+  const float* peer[16];
+  uint32_t sbase;
+  __device__ explicit HistCta(float* hsh) {
+    namespace cgr = cooperative_groups;
+    cgr::cluster_group cl = cgr::this_cluster();
+    cs = static_cast<int>(cl.num_blocks());
+    rank = static_cast<int>(cl.block_rank());
+    cid = blockIdx.x / cs;
+    ncl = gridDim.x / cs;
+    for (int r = 0; r < cs && r < 16; ++r) peer[r] = cl.map_shared_rank(hsh, r);
+    sbase = static_cast<uint32_t>(__cvta_generic_to_shared(hsh));
+  }
+};
+
 template <typename GH, int NB, int MODE>
 __global__ void __launch_bounds__(512, 3) level_hist_kernel(const uint8_t* __restrict__ bins, int64_t n, int G, int F,
                                                          const uint32_t* __restrict__ order,
                                                          const GH* __restrict__ g, const GH* __restrict__ h,
                                                          const Plan* __restrict__ plan, int max_bins,
                                                          float* __restrict__ partials) {
-  namespace cgr = cooperative_groups;
   extern __shared__ __align__(16) float hsh[];   // [2][NB][32]
-  constexpr int PLANE = NB * GROUP;
-  constexpr int MAX_CS = 16;
-  cgr::cluster_group cl = cgr::this_cluster();
-  const int cs = static_cast<int>(cl.num_blocks());
-  const int rank = static_cast<int>(cl.block_rank());
-  const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
-  const float* peer[MAX_CS];
-  for (int r = 0; r < cs && r < MAX_CS; ++r) peer[r] = cl.map_shared_rank(hsh, r);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int j = lane >> 1, c = lane & 1;
-  const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(hsh));
-  uint32_t off[16];
-#pragma unroll
-  for (int l = 0; l < 16; ++l) off[l] = sbase + 4u * static_cast<uint32_t>(c * 16 + ((l + j) & 15));
+  HistCta k(hsh);
+  const HistProblem P{bins, n, G, F, order, g, h, plan, max_bins, partials};
   const int total_items = plan->total_units * G;
-  const int n_small = plan->n_small;
-  for (int item = cid; item < total_items; item += ncl) {
-    const int unit = item / G, grp = item - unit * G;
-    // leaf of this unit: last jj with unit_begin[jj] <= unit
-    int lo = 0, hi = n_small - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (plan->unit_begin[mid] <= unit) lo = mid; else hi = mid - 1;
-    }
-    const int jj = lo;
-    const int chunk = unit - plan->unit_begin[jj];
-    const int seg_s = plan->seg_start[jj], seg_c = plan->seg_cnt[jj];
-    const int cr = plan->chunk_rows[jj];
-    const int p0 = seg_s + (chunk * cs + rank) * cr;
-    const int p1 = min(seg_s + seg_c, p0 + cr);
-    for (int i = threadIdx.x; i < 2 * PLANE / 4; i += blockDim.x)
-      reinterpret_cast<float4*>(hsh)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int item = k.cid; item < total_items; item += k.ncl)
+    hist_item<GH, NB, MODE>(P, item, k.cs, k.rank, hsh, k.peer, k.sbase);
+}
+
+// The batched form: one launch for a level of many problems. The work items of all
+// problems are numbered one after the other; every CTA first computes, from the problems'
+// plans, the first item of each problem, then walks the items like the single-problem
+// kernel, looking up an item's problem by binary search.
+constexpr int HIST_MAX_BATCH = 2048;
+
+template <typename GH, int NB>
+__global__ void __launch_bounds__(512, 3) level_hist_batched_kernel(const HistProblem* __restrict__ probs, int n_probs) {
+  extern __shared__ __align__(16) float hsh[];   // [2][NB][32]
+  __shared__ int s_first[HIST_MAX_BATCH + 1];
+  __shared__ int s_carry;
+  HistCta k(hsh);
+  // s_first[p] = items of problems 0..p-1 (block-wide scan in chunks of blockDim)
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n_probs; base += blockDim.x) {
+    const int p = base + threadIdx.x;
+    const int cnt = p < n_probs ? probs[p].plan->total_units * probs[p].G : 0;
+    s_first[p < n_probs ? p + 1 : HIST_MAX_BATCH] = cnt;   // counts, scanned below
     __syncthreads();
-    const bool active = grp * GROUP + c * 16 < F;
-    const uint8_t* gbase = bins + static_cast<int64_t>(grp) * n * GROUP + c * 16;
-    if (active) {
-      for (int pos = p0 + warp * 16 + j; pos < p1; pos += nw * 16) {
-        const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(gbase + static_cast<int64_t>(row) * GROUP));
-        const float gv = cbgd::load_gh(g, row), hv = cbgd::load_gh(h, row);
-        // rotate the 16 bytes so that byte l of R is byte (l + j) % 16 of v
-        uint32_t w0 = v.x, w1 = v.y, w2 = v.z, w3 = v.w;
-        const int q = (j >> 2) & 3, r = j & 3;
-        if (q & 2) {
-          uint32_t t = w0; w0 = w2; w2 = t;
-          t = w1; w1 = w3; w3 = t;
-        }
-        if (q & 1) {
-          uint32_t t = w0; w0 = w1; w1 = w2; w2 = w3; w3 = t;
-        }
-        uint32_t R[4];
-        R[0] = __funnelshift_r(w0, w1, 8 * r);
-        R[1] = __funnelshift_r(w1, w2, 8 * r);
-        R[2] = __funnelshift_r(w2, w3, 8 * r);
-        R[3] = __funnelshift_r(w3, w0, 8 * r);
-#pragma unroll
-        for (int l = 0; l < 16; ++l) {
-          const uint32_t b = (R[l >> 2] >> (8 * (l & 3))) & (NB - 1);
-          if (MODE == 0) {
-            const uint32_t a = off[l] + b * (GROUP * 4);
-            red_add(a, gv);
-            red_add(a + PLANE * 4, hv);
-          } else {
-            // off[l] - sbase is 4 x (feature within the group)
-            const uint32_t f = (off[l] - sbase) >> 2;
-            cas_add2(reinterpret_cast<float2*>(hsh) + b * GROUP + f, gv, hv);
-          }
-        }
+    if (threadIdx.x == 0) {
+      int run = s_carry;
+      const int end = min(n_probs, base + static_cast<int>(blockDim.x));
+      for (int q = base; q < end; ++q) {
+        run += s_first[q + 1];
+        s_first[q + 1] = run;
       }
+      s_carry = run;
     }
-    cl.sync();
-    // this CTA's slice of bins, summed over the cluster's CTAs in rank order
-    const int bs = (max_bins + cs - 1) / cs;
-    const int b0 = rank * bs;
-    const int nbs = max(0, min(max_bins, b0 + bs) - b0);
-    float* dst = partials + static_cast<int64_t>(item) * (2 * max_bins * GROUP);
-    for (int i = threadIdx.x; i < 2 * nbs * GROUP; i += blockDim.x) {
-      const int st = i / (nbs * GROUP), rem = i - st * (nbs * GROUP);
-      const int e = MODE == 0 ? st * PLANE + b0 * GROUP + rem : (b0 * GROUP + rem) * 2 + st;
-      float v = 0.f;
-      for (int r = 0; r < cs; ++r) v += peer[r][e];
-      dst[st * (max_bins * GROUP) + b0 * GROUP + rem] = v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) s_first[0] = 0;
+  __syncthreads();
+  const int total_items = s_first[n_probs];
+  for (int item = k.cid; item < total_items; item += k.ncl) {
+    int lo = 0, hi = n_probs - 1;   // last p with s_first[p] <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_first[mid] <= item) lo = mid; else hi = mid - 1;
     }
-    cl.sync();
+    const HistProblem P = probs[lo];
+    hist_item<GH, NB, 0>(P, item - s_first[lo], k.cs, k.rank, hsh, k.peer, k.sbase);
   }
 }
 
@@ -1047,6 +1140,97 @@ cbg_status launch_hist_nb(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins
   CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_kernel<GH, NB, MODE>, bins, L.n, L.G, L.F, order, g, h, plan,
                                    L.max_bins, partials));
   return CBG_OK;
+}
+
+// The batched kernel with the cluster size the problems' plans were made for: the number
+// of co-resident clusters (cached per geometry); 0 if none fits.
+template <typename GH, int NB>
+cbg_status batched_clusters(cbg_ctx* ctx, int threads, int cs, int* clusters) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, int> cache;
+  const auto key = std::make_tuple(ctx->device, threads, cs, static_cast<int>(sizeof(GH)));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *clusters = it->second;
+      return CBG_OK;
+    }
+  }
+  auto kern = level_hist_batched_kernel<GH, NB>;
+  CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(hist_smem_bytes(NB))));
+  if (cs > 8) CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(cs * ctx->num_sms));
+  cfg.blockDim = dim3(static_cast<unsigned>(threads));
+  cfg.dynamicSmemBytes = hist_smem_bytes(NB);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(cs);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = n;
+  *clusters = n;
+  return CBG_OK;
+}
+
+template <typename GH, int NB>
+cbg_status launch_hist_batched_nb(cbg_ctx* ctx, const HistProblem* table, int n_probs, int threads, int cs) {
+  int clusters = 0;
+  cbg_status st = batched_clusters<GH, NB>(ctx, threads, cs, &clusters);
+  if (st != CBG_OK) return st;
+  if (clusters <= 0) return ::cbg::fail(ctx, CBG_EUNSUPPORTED, "no co-resident batched histogram cluster of %d fits", cs);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(cs * clusters));
+  cfg.blockDim = dim3(static_cast<unsigned>(threads));
+  cfg.dynamicSmemBytes = hist_smem_bytes(NB);
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(cs);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_batched_kernel<GH, NB>, table, n_probs));
+  return CBG_OK;
+}
+
+// One histogram launch for a level of many problems (shared-reduction kernel): table is a
+// device array of n_probs entries, nb_alloc the largest bin allocation among them.
+template <typename GH>
+cbg_status launch_hist_batched(cbg_ctx* ctx, int nb_alloc, const HistProblem* table, int n_probs, int threads,
+                               int cs, bool query_only = false) {
+  auto run = [&](auto nbc) -> cbg_status {
+    constexpr int NB = decltype(nbc)::value;
+    if (query_only) {
+      int clusters = 0;
+      cbg_status st = batched_clusters<GH, NB>(ctx, threads, cs, &clusters);
+      if (st != CBG_OK) return st;
+      return clusters > 0 ? CBG_OK : CBG_EUNSUPPORTED;
+    }
+    return launch_hist_batched_nb<GH, NB>(ctx, table, n_probs, threads, cs);
+  };
+  switch (nb_alloc) {
+    case 2: return run(std::integral_constant<int, 2>{});
+    case 4: return run(std::integral_constant<int, 4>{});
+    case 8: return run(std::integral_constant<int, 8>{});
+    case 16: return run(std::integral_constant<int, 16>{});
+    case 32: return run(std::integral_constant<int, 32>{});
+    case 64: return run(std::integral_constant<int, 64>{});
+    case 128: return run(std::integral_constant<int, 128>{});
+    case 256: return run(std::integral_constant<int, 256>{});
+    default: return ::cbg::fail(ctx, CBG_EINVAL, "unsupported bin allocation %d", nb_alloc);
+  }
 }
 
 template <typename GH>

@@ -897,7 +897,17 @@ cbg_status cbg_tree_begin(cbg_ctx* ctx, const cbg_tree_shape* shape, void* state
   return CBG_OK;
 }
 
-cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
+namespace {
+cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist);
+}
+
+cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) { return build_level_impl(ctx, a, true); }
+
+namespace {
+
+// One level; do_hist = false when the histogram of this level was computed by a batched
+// launch over many problems (cbg_boost_batched).
+cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist) {
   if (!ctx) return CBG_EINVAL;
   CBG_REQUIRE(ctx, a != nullptr, "args is NULL");
   Layout L;
@@ -935,7 +945,7 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
   CBG_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &capturing));
-  if (capturing == cudaStreamCaptureStatusNone) st = prof_begin(ctx, &ev0, &ev1);
+  if (do_hist && capturing == cudaStreamCaptureStatusNone) st = prof_begin(ctx, &ev0, &ev1);
   if (st != CBG_OK) return st;
   // the lane-per-feature kernels read (g, h) by position: the caller's arrays at the root
   // (positions are rows), then the copies the previous level's partition moved along (for
@@ -947,12 +957,14 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
   void* h_pos_nxt = at<char>(S, (d + 1) % 2 == 1 ? L.o_hp_a : L.o_hp_b);
   const void* g_hist = by_pos ? g_pos : a->g;
   const void* h_hist = by_pos ? h_pos : a->h;
-  st = a->gh_dtype == CBG_F32 ? launch_hist<float>(ctx, hist_config(L), a->bins, order_cur, g_hist, h_hist, plan, partials)
-                              : launch_hist<__nv_bfloat16>(ctx, hist_config(L), a->bins, order_cur, g_hist, h_hist, plan,
-                                                           partials);
-  if (st != CBG_OK) return st;
-  st = prof_end(ctx, ev1);
-  if (st != CBG_OK) return st;
+  if (do_hist) {
+    st = a->gh_dtype == CBG_F32
+             ? launch_hist<float>(ctx, hist_config(L), a->bins, order_cur, g_hist, h_hist, plan, partials)
+             : launch_hist<__nv_bfloat16>(ctx, hist_config(L), a->bins, order_cur, g_hist, h_hist, plan, partials);
+    if (st != CBG_OK) return st;
+    st = prof_end(ctx, ev1);
+    if (st != CBG_OK) return st;
+  }
   // 2. FP64 reduction of the partials + sibling subtraction
   {
     reduce_kernel<<<reduce_grid(L.G, L.max_bins, d == 0 ? 1 : (1 << (d - 1))), RD_THREADS, 0, ctx->stream>>>(
@@ -999,6 +1011,8 @@ cbg_status cbg_build_level(cbg_ctx* ctx, const cbg_level_args* a) {
   }
   return CBG_OK;
 }
+
+}  // namespace
 
 cbg_status cbg_tree_rows_histogrammed(cbg_ctx* ctx, const cbg_tree_shape* shape, void* state, int reset,
                                       int64_t* rows) {
@@ -1221,6 +1235,55 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
     CBG_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned), ctx->stream));
   }
   if (trees == 0) return CBG_OK;
+  // One histogram launch per level for all problems when they all use the shared-reduction
+  // kernel with the same tiling (the plans are chunked for one cluster size); the other
+  // kernels of a level run per problem on the graph branches.
+  bool batch_hist = n_problems <= HIST_MAX_BATCH;
+  Layout L0;
+  {
+    cbg_status st = make_layout(ctx, &problems[0].shape, &L0);
+    if (st != CBG_OK) return st;
+  }
+  int nb_alloc = 2, cs_plan = 1;
+  for (int i = 0; i < n_problems && batch_hist; ++i) {
+    Layout L;
+    cbg_status st = make_layout(ctx, &problems[i].shape, &L);
+    if (st != CBG_OK) return st;
+    batch_hist = L.kind == 1 && L.cluster == L0.cluster && L.rows_per_item == L0.rows_per_item &&
+                 L.threads == L0.threads;
+    nb_alloc = std::max(nb_alloc, L.nb_alloc);
+  }
+  std::vector<HistProblem*> tables;   // device tables, one per level
+  if (batch_hist) {
+    cbg_status st = hist_cluster_size(ctx, hist_config(L0), &cs_plan);
+    if (st != CBG_OK) return st;
+    st = gh_dtype == CBG_F32 ? launch_hist_batched<float>(ctx, nb_alloc, nullptr, n_problems, L0.threads, cs_plan, true)
+                             : launch_hist_batched<__nv_bfloat16>(ctx, nb_alloc, nullptr, n_problems, L0.threads,
+                                                                  cs_plan, true);
+    batch_hist = st == CBG_OK;
+  }
+  if (batch_hist) {
+    const size_t per_level = static_cast<size_t>(n_problems) * sizeof(HistProblem);
+    cbg_status st = ws_reserve(ctx, depth * (per_level + 256) + 256);
+    if (st != CBG_OK) return st;
+    Carve cv(ctx->ws);
+    std::vector<HistProblem> host(n_problems);
+    for (int d = 0; d < depth; ++d) {
+      for (int i = 0; i < n_problems; ++i) {
+        const cbg_problem& p = problems[i];
+        Layout L;
+        make_layout(ctx, &p.shape, &L);
+        void* S = p.state;
+        host[i] = HistProblem{p.bins, L.n, L.G, L.F,
+                              d == 0 ? nullptr : at<uint32_t>(S, d % 2 == 1 ? L.o_order_a : L.o_order_b),
+                              p.g, p.h, at<Plan>(S, L.o_plan), L.max_bins, at<float>(S, L.o_part)};
+      }
+      HistProblem* dev = cv.take<HistProblem>(n_problems);
+      CBG_CUDA(ctx, cudaMemcpyAsync(dev, host.data(), per_level, cudaMemcpyHostToDevice, ctx->stream));
+      tables.push_back(dev);
+    }
+    CBG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the host staging vector is reused
+  }
   if (!ctx->capture_stream) CBG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
   while (static_cast<int>(ctx->branch_streams.size()) < nb) {
     cudaStream_t st;
@@ -1240,25 +1303,110 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
   cudaError_t ce = cudaEventRecord(ctx->branch_events[nb], origin);
   for (int b = 0; b < nb && ce == cudaSuccess; ++b) ce = cudaStreamWaitEvent(ctx->branch_streams[b], ctx->branch_events[nb], 0);
   if (ce != cudaSuccess) st = fail(ctx, CBG_ECUDA, "forking the batched round failed: %s", cudaGetErrorString(ce));
-  for (int i = 0; i < n_problems && st == CBG_OK; ++i) {
+  // join every branch into the origin stream, and fork the origin again
+  auto join = [&]() {
+    for (int b = 0; b < nb && st == CBG_OK; ++b) {
+      ce = cudaEventRecord(ctx->branch_events[b], ctx->branch_streams[b]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(origin, ctx->branch_events[b], 0);
+      if (ce != cudaSuccess) st = fail(ctx, CBG_ECUDA, "joining the batched round failed: %s", cudaGetErrorString(ce));
+    }
+  };
+  auto fork = [&]() {
+    if (st != CBG_OK) return;
+    ce = cudaEventRecord(ctx->branch_events[nb], origin);
+    for (int b = 0; b < nb && ce == cudaSuccess; ++b)
+      ce = cudaStreamWaitEvent(ctx->branch_streams[b], ctx->branch_events[nb], 0);
+    if (ce != cudaSuccess) st = fail(ctx, CBG_ECUDA, "forking the batched round failed: %s", cudaGetErrorString(ce));
+  };
+  auto record = [&](int i) {
     Layout L;
     st = make_layout(ctx, &problems[i].shape, &L);
-    if (st != CBG_OK) break;
-    ctx->stream = ctx->branch_streams[i % nb];
+    if (st != CBG_OK) return;
     cbg_split* sp_tmp = at<cbg_split>(problems[i].state, L.o_gsplit);
     double* v_tmp = at<double>(problems[i].state, L.o_gvals);
     unsigned* counter = reinterpret_cast<unsigned*>(at<char>(problems[i].state, L.o_gsplit) + sizeof(cbg_split) * MAX_DEPTH);
-    st = boost_one_tree(ctx, &args[i], sp_tmp, v_tmp);
-    if (st != CBG_OK) break;
     record_tree_kernel<<<1, 256, 0, ctx->stream>>>(sp_tmp, v_tmp, depth, problems[i].splits, problems[i].leaf_values,
                                                    counter, trees);
     if (cudaGetLastError() != cudaSuccess) st = fail(ctx, CBG_ECUDA, "record kernel launch failed during capture");
+  };
+  if (!batch_hist) {
+    for (int i = 0; i < n_problems && st == CBG_OK; ++i) {
+      Layout L;
+      st = make_layout(ctx, &problems[i].shape, &L);
+      if (st != CBG_OK) break;
+      ctx->stream = ctx->branch_streams[i % nb];
+      st = boost_one_tree(ctx, &args[i], at<cbg_split>(problems[i].state, L.o_gsplit),
+                          at<double>(problems[i].state, L.o_gvals));
+      if (st == CBG_OK) record(i);
+    }
+  } else {
+    for (int i = 0; i < n_problems && st == CBG_OK; ++i) {
+      ctx->stream = ctx->branch_streams[i % nb];
+      st = cbg_tree_begin(ctx, args[i].shape, args[i].state, args[i].state_bytes, args[i].leaf);
+    }
+    for (int d = 0; d < depth && st == CBG_OK; ++d) {
+      join();
+      ctx->stream = origin;
+      if (st == CBG_OK)
+        st = gh_dtype == CBG_F32
+                 ? launch_hist_batched<float>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan)
+                 : launch_hist_batched<__nv_bfloat16>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan);
+      fork();
+      for (int i = 0; i < n_problems && st == CBG_OK; ++i) {
+        const cbg_problem& p = problems[i];
+        Layout L;
+        st = make_layout(ctx, &p.shape, &L);
+        if (st != CBG_OK) break;
+        ctx->stream = ctx->branch_streams[i % nb];
+        cbg_level_args la{};
+        la.shape = &p.shape;
+        la.state = p.state;
+        la.state_bytes = p.state_bytes;
+        la.bins = p.bins;
+        la.bins_t = p.bins_t;
+        la.n_borders = p.n_borders;
+        la.g = p.g;
+        la.h = p.h;
+        la.gh_dtype = gh_dtype;
+        la.depth = d;
+        la.l2 = l2;
+        la.force_feature = -1;
+        la.force_border = -1;
+        la.leaf = p.leaf;
+        la.splits = at<cbg_split>(p.state, L.o_gsplit);
+        la.child_totals = p.child_totals;
+        la.last_level = d == depth - 1;
+        st = build_level_impl(ctx, &la, false);
+      }
+    }
+    for (int i = 0; i < n_problems && st == CBG_OK; ++i) {
+      const cbg_problem& p = problems[i];
+      Layout L;
+      st = make_layout(ctx, &p.shape, &L);
+      if (st != CBG_OK) break;
+      ctx->stream = ctx->branch_streams[i % nb];
+      cbg_apply_args aa{};
+      aa.bins = p.bins;
+      aa.n = p.shape.n;
+      aa.F_pad = p.shape.F_pad;
+      aa.splits = at<cbg_split>(p.state, L.o_gsplit);
+      aa.depth = depth;
+      aa.leaf_totals = p.child_totals;
+      aa.l2 = l2;
+      aa.lr = lr;
+      aa.leaf_in = p.leaf;
+      aa.pred = p.pred;
+      aa.leaf_values_out = at<double>(p.state, L.o_gvals);
+      aa.y = p.y;
+      aa.loss = p.loss;
+      aa.gh_dtype = gh_dtype;
+      aa.g = p.g;
+      aa.h = p.h;
+      st = cbg_apply_tree(ctx, &aa);
+      if (st == CBG_OK) record(i);
+    }
   }
-  for (int b = 0; b < nb && st == CBG_OK; ++b) {
-    ce = cudaEventRecord(ctx->branch_events[b], ctx->branch_streams[b]);
-    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(origin, ctx->branch_events[b], 0);
-    if (ce != cudaSuccess) st = fail(ctx, CBG_ECUDA, "joining the batched round failed: %s", cudaGetErrorString(ce));
-  }
+  join();
   ctx->stream = origin;
   ce = cudaStreamEndCapture(origin, &graph);
   ctx->stream = user_stream;
@@ -1285,8 +1433,8 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
 // ------------------------------------------------------------------ autotuner
 namespace {
 
-// The tilings the autotuner times: the shared-reduction kernel with clusters of 4 or 8
-// and 2048 or 4096 rows per CTA of a unit; the lane-per-feature kernel with clusters of 2
+// The tilings the autotuner times: the shared-reduction kernel with clusters of 1, 2, 4
+// or 8 and 2048 or 4096 rows per CTA of a unit; the lane-per-feature kernel with clusters of 2
 // and 8192 or 16384 rows; its one-statistic-per-warp form with clusters of 2 or 4 and
 // 8192 or 16384 rows; the 16-feature warp-private kernel once.
 std::vector<cbg_tiles> autotune_candidates() {
@@ -1298,7 +1446,7 @@ std::vector<cbg_tiles> autotune_candidates() {
     t.rows_per_item = rows;
     c.push_back(t);
   };
-  for (int cl : {4, 8})
+  for (int cl : {1, 2, 4, 8})
     for (int r : {2048, 4096}) add(1, cl, r);
   for (int r : {8192, 16384}) add(4, 2, r);
   for (int cl : {2, 4})

@@ -164,16 +164,36 @@ def autotune(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, l2: flo
                                   splits, child, bins_t=prep.bins_t, reps=reps)
 
 
-def autotune_batch(ctx: cbg.Context, preps, ys, losses, depth: int, l2: float = 3.0, gh_dtype: str = "f32"):
-    """Tiles for every problem of a batch: one autotuner run per distinct bin count, on
-    the problem with the most rows among those that share it."""
-    by_bins: dict[int, int] = {}
-    for i, p in enumerate(preps):
-        j = by_bins.get(p.max_bins)
-        if j is None or p.n > preps[j].n:
-            by_bins[p.max_bins] = i
-    chosen = {mb: autotune(ctx, preps[i], ys[i], losses[i], depth, l2, gh_dtype)[0] for mb, i in by_bins.items()}
-    return [chosen[p.max_bins] for p in preps]
+# Tilings timed on a whole batch: the shared-reduction kernel (whose histograms of a level
+# then run as one launch for every problem) with clusters of 1, 2 and 8, and the
+# lane-per-feature kernels per problem.
+BATCH_CANDIDATES = ([{"kernel": 1, "cluster": c, "rows_per_item": 2048} for c in (1, 2, 8)] +
+                    [{"kernel": 4, "cluster": 2, "rows_per_item": r} for r in (8192, 16384)] +
+                    [{"kernel": 5, "cluster": 2, "rows_per_item": 8192}])
+
+
+def autotune_batch(ctx: cbg.Context, preps, ys, losses, depth: int, l2: float = 3.0, gh_dtype: str = "f32",
+                   rounds: int = 3, candidates=None):
+    """Tiles for a batch, timed on the batch itself: every candidate tiling, applied to every
+    problem, trains one round of trees and then 1 + rounds rounds (fit_batched); the time of
+    the extra rounds, without the graph capture both calls pay, picks the winner. Returns
+    one tiles dict per problem (all the same)."""
+    import torch
+    stream = torch.cuda.current_stream(preps[0].bins.device)
+    best, best_ms = None, float("inf")
+    for t in candidates or BATCH_CANDIDATES:
+        ms = []
+        for k in (1, 1 + rounds):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fit_batched(ctx, preps, ys, losses, depth, k, 0.1, l2, gh_dtype, tiles=dict(t))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        per_round = (ms[1] - ms[0]) / rounds
+        if per_round < best_ms:
+            best, best_ms = t, per_round
+    return [dict(best) for _ in preps]
 
 
 def fit_batched(ctx: cbg.Context, preps, ys, losses, depth: int, trees: int, lr: float, l2: float,
@@ -181,7 +201,7 @@ def fit_batched(ctx: cbg.Context, preps, ys, losses, depth: int, trees: int, lr:
     """Boost many independent problems together (cbg_boost_batched): one captured graph per
     round of trees, with the problems on parallel branches. tiles: None (library
     defaults), one dict for every problem, a list with one dict per problem, or "auto"
-    (autotune_batch). Returns one Model per problem and the buffers."""
+    (autotune_batch on this batch). Returns one Model per problem and the buffers."""
     if isinstance(tiles, str):
         if tiles != "auto":
             raise ValueError("tiles must be None, a dict, a list of dicts or 'auto'")
