@@ -848,16 +848,15 @@ __device__ __forceinline__ void put_cell(double* hist, float2* hist_df, int64_t 
 constexpr int RD_BINS = 4;
 constexpr int RD_THREADS = 256;   // 2 x RD_BINS x 32 = 256 cells, one per thread
 
-__global__ void __launch_bounds__(RD_THREADS)
-    reduce_kernel(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
+__device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
                   const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
-                  const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df) {
+                  const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df, int bx, int by) {
   constexpr int CELLS = 2 * RD_BINS * GROUP;
   __shared__ double tile[GROUP][RD_BINS][2];
-  const int jj = blockIdx.y;
+  const int jj = by;
   if (jj >= plan->n_small) return;
   const int nbt = (max_bins + RD_BINS - 1) / RD_BINS;
-  const int grp = blockIdx.x / nbt, b0 = (blockIdx.x - grp * nbt) * RD_BINS;
+  const int grp = bx / nbt, b0 = (bx - grp * nbt) * RD_BINS;
   if (grp >= G) return;
   const int u0 = plan->unit_begin[jj], u1 = plan->unit_begin[jj + 1];
   const int64_t item_elems = static_cast<int64_t>(2) * max_bins * GROUP;
@@ -905,6 +904,13 @@ __global__ void __launch_bounds__(RD_THREADS)
       put_cell(hist_cur, hist_df, lcell, hist_prev[pcell] - s);
     }
   }
+}
+
+__global__ void __launch_bounds__(RD_THREADS)
+    reduce_kernel(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
+                  const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
+                  const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df) {
+  reduce_body(plan, partials, G, F, max_bins, hist_prev, hist_cur, splits, depth, hist_df, blockIdx.x, blockIdx.y);
 }
 
 // Grid of reduce_kernel for one level: (bin tiles x groups, directly computed leaves).

@@ -182,9 +182,9 @@ unsigned grid_stride_blocks(int64_t n, int block) {
 }
 
 // ------------------------------------------------------------------ tree begin
-__global__ void tree_begin_kernel(Plan* plan, Segs* seg, int n, int rows_per_item, int cs,
-                                  unsigned long long* rows_hist) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// The root's plan and segment (one thread): every row in leaf 0, chunked into units.
+__device__ void tree_begin_body(Plan* plan, Segs* seg, int n, int rows_per_item, int cs,
+                                unsigned long long* rows_hist) {
   *rows_hist += static_cast<unsigned long long>(n);
   const int per_unit = rows_per_item * cs;
   int chunks = (n + per_unit - 1) / per_unit;
@@ -203,6 +203,11 @@ __global__ void tree_begin_kernel(Plan* plan, Segs* seg, int n, int rows_per_ite
   seg->start[0] = 0;
   seg->cnt[0] = n;
   seg->order[0] = 0;
+}
+
+__global__ void tree_begin_kernel(Plan* plan, Segs* seg, int n, int rows_per_item, int cs,
+                                  unsigned long long* rows_hist) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) tree_begin_body(plan, seg, n, rows_per_item, cs, rows_hist);
 }
 
 // ----------------------------------------------------------------- scoring
@@ -260,16 +265,15 @@ constexpr int SC_MAX_WARPS = 16;
 constexpr int SC_BINS_PER_LANE = 8;   // 32 lanes x 8 = 256 bins
 
 template <int SC_WARPS>
-__global__ void __launch_bounds__(SC_WARPS * 32)
-    score_level_kernel(const float2* __restrict__ hist_df, int level_leaves, int F, int max_bins,
+__device__ __forceinline__ void score_level_body(const float2* __restrict__ hist_df, int level_leaves, int F, int max_bins,
                        const int32_t* __restrict__ n_borders, double l2, BestF* __restrict__ best, Misc* misc,
-                       int force_f, int force_k, int depth, cbg_split* __restrict__ splits) {
+                       int force_f, int force_k, int depth, cbg_split* __restrict__ splits, int bid, int nblk) {
   constexpr int NT = SC_WARPS * 32;
   __shared__ DF s_acc[SC_WARPS][256];
   __shared__ double r_s[NT];
   __shared__ int r_f[NT], r_k[NT];
   __shared__ bool is_last;
-  const int f = blockIdx.x, K = max_bins - 1;
+  const int f = bid, K = max_bins - 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = min(n_borders[f], K);
   const float l2f = static_cast<float>(l2);
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
     best[f].k = r_k[0];
     __threadfence();
     const unsigned ticket = atomicAdd(&misc->done, 1u);
-    is_last = (ticket == gridDim.x - 1);
+    is_last = (ticket == nblk - 1);
   }
   __syncthreads();
   if (!is_last) return;
@@ -396,6 +400,14 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
     splits[depth].score = cf >= 0 ? cs : -INFINITY;
     misc->done = 0;
   }
+}
+
+template <int SC_WARPS>
+__global__ void __launch_bounds__(SC_WARPS * 32)
+    score_level_kernel(const float2* __restrict__ hist_df, int level_leaves, int F, int max_bins,
+                       const int32_t* __restrict__ n_borders, double l2, BestF* __restrict__ best, Misc* misc,
+                       int force_f, int force_k, int depth, cbg_split* __restrict__ splits) {
+  score_level_body<SC_WARPS>(hist_df, level_leaves, F, max_bins, n_borders, l2, best, misc, force_f, force_k, depth, splits, blockIdx.x, gridDim.x);
 }
 
 // FP64 child totals of the level's split for leaf l, one warp: bins <= k stay in leaf l,
@@ -622,14 +634,14 @@ __device__ __forceinline__ int seg_find(const int* seg_pos, int L, int64_t pos) 
 // consecutive positions per thread), the split bit of its row; leaf += 2^d * bit. Unless this is the last level: ones per tile and per leaf (run-length counted
 // in shared memory, since positions are grouped by leaf), and the last block to finish
 // plans the next level.
-__global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_t* __restrict__ bins_t, int64_t n,
+__device__ __forceinline__ void part_flags_body(const uint8_t* __restrict__ bins, const uint8_t* __restrict__ bins_t, int64_t n,
                                   const uint32_t* __restrict__ order, const cbg_split* __restrict__ splits, int depth,
                                   uint16_t* __restrict__ leaf, uint8_t* __restrict__ flags,
                                   uint32_t* __restrict__ tile_cnt, Segs* seg, int write_flags, int64_t n_ptiles,
                                   Segs* __restrict__ nxt, Plan* __restrict__ plan, int rows_per_item, int cs,
                                   unsigned long long* __restrict__ rows_hist, Misc* misc,
                                   const double* __restrict__ hist, int F, int max_bins,
-                                  double* __restrict__ child_totals) {
+                                  double* __restrict__ child_totals, int bid, int nblk) {
   __shared__ uint32_t wsum[PT_THREADS / 32];
   __shared__ uint32_t sh_ones[1 << MAX_DEPTH];
   __shared__ int sh_pos[1 << (MAX_DEPTH - 1)], sh_leaf[1 << (MAX_DEPTH - 1)];
@@ -641,9 +653,9 @@ __global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_
   __syncthreads();
   const int f = splits[depth].feature, k = splits[depth].border;
   // the FP64 child totals of the split, one warp per leaf of the level
-  for (int l = blockIdx.x * (PT_THREADS / 32) + (threadIdx.x >> 5); l < L; l += gridDim.x * (PT_THREADS / 32))
+  for (int l = bid * (PT_THREADS / 32) + (threadIdx.x >> 5); l < L; l += nblk * (PT_THREADS / 32))
     child_totals_warp(hist, l, L, F, max_bins, f, k, child_totals);
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
+  const int64_t base = static_cast<int64_t>(bid) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
   int si = seg_find(sh_pos, L, base);
   uint32_t cnt = 0, run = 0;
   int cur = -1;
@@ -677,13 +689,13 @@ __global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_
   if (threadIdx.x == 0) {
     uint32_t s = 0;
     for (int w = 0; w < PT_THREADS / 32; ++w) s += wsum[w];
-    tile_cnt[blockIdx.x] = s;
+    tile_cnt[bid] = s;
   }
   for (int i = threadIdx.x; i < L; i += blockDim.x)
     if (sh_ones[i]) atomicAdd(&seg->ones[i], sh_ones[i]);
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(&misc->done_part, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) is_last = atomicAdd(&misc->done_part, 1u) == nblk - 1;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
@@ -691,19 +703,30 @@ __global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_
   if (threadIdx.x == 0) misc->done_part = 0;
 }
 
+__global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_t* __restrict__ bins_t, int64_t n,
+                                  const uint32_t* __restrict__ order, const cbg_split* __restrict__ splits, int depth,
+                                  uint16_t* __restrict__ leaf, uint8_t* __restrict__ flags,
+                                  uint32_t* __restrict__ tile_cnt, Segs* seg, int write_flags, int64_t n_ptiles,
+                                  Segs* __restrict__ nxt, Plan* __restrict__ plan, int rows_per_item, int cs,
+                                  unsigned long long* __restrict__ rows_hist, Misc* misc,
+                                  const double* __restrict__ hist, int F, int max_bins,
+                                  double* __restrict__ child_totals) {
+  part_flags_body(bins, bins_t, n, order, splits, depth, leaf, flags, tile_cnt, seg, write_flags, n_ptiles, nxt, plan, rows_per_item, cs, rows_hist, misc, hist, F, max_bins, child_totals, blockIdx.x, gridDim.x);
+}
+
 // C: stable partition of every segment: the row at position i moves to
 // start + (zeros before it) or start + zeros + (ones before it).
-__global__ void part_scatter_kernel(const uint32_t* __restrict__ order, const uint8_t* __restrict__ flags, int64_t n,
+__device__ __forceinline__ void part_scatter_body(const uint32_t* __restrict__ order, const uint8_t* __restrict__ flags, int64_t n,
                                     const uint32_t* __restrict__ tile_off, const Segs* __restrict__ cur, int depth,
                                     uint32_t* __restrict__ order_out,
                                     const void* __restrict__ g_in, const void* __restrict__ h_in,
-                                    void* __restrict__ g_out, void* __restrict__ h_out, int gh_bytes) {
+                                    void* __restrict__ g_out, void* __restrict__ h_out, int gh_bytes, int bid, int nblk) {
   __shared__ uint32_t sh[PT_THREADS / 32];
   __shared__ int sh_pos[1 << (MAX_DEPTH - 1)], sh_leaf[1 << (MAX_DEPTH - 1)];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int L = 1 << depth;
   load_seg_table(cur, L, sh_pos, sh_leaf);
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
+  const int64_t base = static_cast<int64_t>(bid) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
   uint8_t fl[PT / PT_THREADS];
   uint32_t s = 0;
 #pragma unroll
@@ -727,7 +750,7 @@ __global__ void part_scatter_kernel(const uint32_t* __restrict__ order, const ui
     }
   }
   __syncthreads();
-  uint32_t ones_before = tile_off[blockIdx.x] + sh[warp] + x - s;
+  uint32_t ones_before = tile_off[bid] + sh[warp] + x - s;
   int si = seg_find(sh_pos, L, base);
 #pragma unroll
   for (int i = 0; i < PT / PT_THREADS; ++i) {
@@ -759,13 +782,21 @@ __global__ void part_scatter_kernel(const uint32_t* __restrict__ order, const ui
   }
 }
 
+__global__ void part_scatter_kernel(const uint32_t* __restrict__ order, const uint8_t* __restrict__ flags, int64_t n,
+                                    const uint32_t* __restrict__ tile_off, const Segs* __restrict__ cur, int depth,
+                                    uint32_t* __restrict__ order_out,
+                                    const void* __restrict__ g_in, const void* __restrict__ h_in,
+                                    void* __restrict__ g_out, void* __restrict__ h_out, int gh_bytes) {
+  part_scatter_body(order, flags, n, tile_off, cur, depth, order_out, g_in, h_in, g_out, h_out, gh_bytes, blockIdx.x, gridDim.x);
+}
+
 // ------------------------------------------------------------------- apply
 template <typename GH>
-__global__ void apply_kernel(const uint8_t* __restrict__ bins, int64_t n, int groups, const cbg_split* __restrict__ splits,
+__device__ __forceinline__ void apply_body(const uint8_t* __restrict__ bins, int64_t n, int groups, const cbg_split* __restrict__ splits,
                              int depth, const double* __restrict__ leaf_totals, const double* __restrict__ values_in,
                              double l2, double lr, const uint16_t* __restrict__ leaf_in, uint16_t* __restrict__ leaf_out,
                              float* __restrict__ pred, double* __restrict__ values_out, const float* __restrict__ y,
-                             int loss, GH* __restrict__ g, GH* __restrict__ h) {
+                             int loss, GH* __restrict__ g, GH* __restrict__ h, int bid, int nblk) {
   __shared__ float lrv[1 << MAX_DEPTH];
   __shared__ int sf[MAX_DEPTH], sk[MAX_DEPTH];
   const int L = 1 << depth;
@@ -778,15 +809,15 @@ __global__ void apply_kernel(const uint8_t* __restrict__ bins, int64_t n, int gr
       v = values_in[l];
     }
     lrv[l] = static_cast<float>(lr * v);
-    if (values_out && blockIdx.x == 0) values_out[l] = v;
+    if (values_out && bid == 0) values_out[l] = v;
   }
   if (threadIdx.x < depth) {
     sf[threadIdx.x] = splits[threadIdx.x].feature;
     sk[threadIdx.x] = splits[threadIdx.x].border;
   }
   __syncthreads();
-  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
-       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  for (int64_t r = bid * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
+       r += static_cast<int64_t>(nblk) * blockDim.x) {
     int l;
     if (leaf_in) {
       l = leaf_in[r] & (L - 1);
@@ -818,13 +849,22 @@ __global__ void apply_kernel(const uint8_t* __restrict__ bins, int64_t n, int gr
   }
 }
 
+template <typename GH>
+__global__ void apply_kernel(const uint8_t* __restrict__ bins, int64_t n, int groups, const cbg_split* __restrict__ splits,
+                             int depth, const double* __restrict__ leaf_totals, const double* __restrict__ values_in,
+                             double l2, double lr, const uint16_t* __restrict__ leaf_in, uint16_t* __restrict__ leaf_out,
+                             float* __restrict__ pred, double* __restrict__ values_out, const float* __restrict__ y,
+                             int loss, GH* __restrict__ g, GH* __restrict__ h) {
+  apply_body<GH>(bins, n, groups, splits, depth, leaf_totals, values_in, l2, lr, leaf_in, leaf_out, pred, values_out, y, loss, g, h, blockIdx.x, gridDim.x);
+}
+
 // ------------------------------------------------------------- host helpers
 // Copies one tree's splits and leaf values from the graph's fixed scratch to tree slot t of
 // the model (t read from, then advanced in, a device counter), so one captured tree can be
 // replayed for every tree of the run.
-__global__ void record_tree_kernel(const cbg_split* __restrict__ sp_tmp, const double* __restrict__ v_tmp, int depth,
-                                   cbg_split* __restrict__ splits, double* __restrict__ values,
-                                   unsigned* __restrict__ counter, int trees) {
+__device__ __forceinline__ void record_tree_body(const cbg_split* __restrict__ sp_tmp, const double* __restrict__ v_tmp,
+                                                 int depth, cbg_split* __restrict__ splits, double* __restrict__ values,
+                                                 unsigned* __restrict__ counter, int trees) {
   __shared__ unsigned t;
   if (threadIdx.x == 0) t = *counter;
   __syncthreads();
@@ -835,6 +875,122 @@ __global__ void record_tree_kernel(const cbg_split* __restrict__ sp_tmp, const d
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = t + 1;
+}
+
+__global__ void record_tree_kernel(const cbg_split* __restrict__ sp_tmp, const double* __restrict__ v_tmp, int depth,
+                                   cbg_split* __restrict__ splits, double* __restrict__ values,
+                                   unsigned* __restrict__ counter, int trees) {
+  record_tree_body(sp_tmp, v_tmp, depth, splits, values, counter, trees);
+}
+
+// ---------------------------------------------------------------- batched form
+// Everything the level kernels need for one problem of a batched round, with the buffers
+// of one level (the ping-pong buffers alternate between levels). A block map gives every
+// block of a batched launch its problem and its block index within that problem.
+struct LevelProblem {
+  const uint8_t* bins;
+  const uint8_t* bins_t;
+  int64_t n;
+  int F, G, max_bins, rows_per_item, cs;
+  int64_t n_ptiles;
+  int apply_blocks;
+  const int32_t* n_borders;
+  const float* y;
+  int loss;
+  float* pred;
+  void* g;
+  void* h;
+  uint16_t* leaf;
+  cbg_split* sp;              // the tree's splits (graph scratch)
+  double* vals;               // the tree's leaf values (graph scratch)
+  double* child_totals;
+  cbg_split* splits_out;      // model slots [T][D]
+  double* values_out;         // model slots [T][2^D]
+  unsigned* counter;
+  Plan* plan;
+  float* partials;
+  float2* hist_df;
+  BestF* best;
+  Misc* misc;
+  uint8_t* flags;
+  uint32_t* tcnt;
+  unsigned long long* rows_hist;
+  Segs* seg_root;
+  Segs* seg_cur;
+  Segs* seg_nxt;
+  const uint32_t* order_cur;
+  uint32_t* order_nxt;
+  double* hist_cur;
+  const double* hist_prev;
+};
+
+constexpr int BEGIN_ROWS = 4096;   // leaf entries zeroed per block of the batched tree start
+
+__global__ void begin_batched_kernel(const LevelProblem* __restrict__ tab, const int2* __restrict__ map) {
+  const int2 m = map[blockIdx.x];
+  const LevelProblem& P = tab[m.x];
+  const int64_t r0 = static_cast<int64_t>(m.y) * BEGIN_ROWS;
+  const int64_t r1 = min(P.n, r0 + BEGIN_ROWS);
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) P.leaf[r] = 0;
+  if (m.y != 0) return;
+  uint32_t* sw = reinterpret_cast<uint32_t*>(P.seg_root);
+  for (int i = threadIdx.x; i < static_cast<int>(sizeof(Segs) / 4); i += blockDim.x) sw[i] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    P.misc->done = 0;
+    P.misc->done_part = 0;
+    P.misc->forced_score = 0.0;
+    tree_begin_body(P.plan, P.seg_root, static_cast<int>(P.n), P.rows_per_item, P.cs, P.rows_hist);
+  }
+}
+
+__global__ void __launch_bounds__(RD_THREADS) reduce_batched_kernel(const LevelProblem* __restrict__ tab,
+                                                                    const int2* __restrict__ map, int depth) {
+  const int2 m = map[blockIdx.x];
+  const LevelProblem& P = tab[m.x];
+  const int gx = P.G * ((P.max_bins + RD_BINS - 1) / RD_BINS);
+  reduce_body(P.plan, P.partials, P.G, P.F, P.max_bins, P.hist_prev, P.hist_cur, P.sp, depth, P.hist_df, m.y % gx,
+              m.y / gx);
+}
+
+template <int SC_WARPS>
+__global__ void __launch_bounds__(SC_WARPS * 32) score_batched_kernel(const LevelProblem* __restrict__ tab,
+                                                                      const int2* __restrict__ map, int level_leaves,
+                                                                      double l2, int depth) {
+  const int2 m = map[blockIdx.x];
+  const LevelProblem& P = tab[m.x];
+  score_level_body<SC_WARPS>(P.hist_df, level_leaves, P.F, P.max_bins, P.n_borders, l2, P.best, P.misc, -1, -1, depth,
+                             P.sp, m.y, P.F);
+}
+
+__global__ void flags_batched_kernel(const LevelProblem* __restrict__ tab, const int2* __restrict__ map, int depth,
+                                     int write_flags) {
+  const int2 m = map[blockIdx.x];
+  const LevelProblem& P = tab[m.x];
+  part_flags_body(P.bins, P.bins_t, P.n, P.order_cur, P.sp, depth, P.leaf, P.flags, P.tcnt, P.seg_cur, write_flags,
+                  P.n_ptiles, P.seg_nxt, P.plan, P.rows_per_item, P.cs, P.rows_hist, P.misc, P.hist_cur, P.F,
+                  P.max_bins, P.child_totals, m.y, static_cast<int>(P.n_ptiles));
+}
+
+__global__ void scatter_batched_kernel(const LevelProblem* __restrict__ tab, const int2* __restrict__ map, int depth) {
+  const int2 m = map[blockIdx.x];
+  const LevelProblem& P = tab[m.x];
+  part_scatter_body(P.order_cur, P.flags, P.n, P.tcnt, P.seg_cur, depth, P.order_nxt, nullptr, nullptr, nullptr,
+                    nullptr, 0, m.y, static_cast<int>(P.n_ptiles));
+}
+
+template <typename GH>
+__global__ void apply_batched_kernel(const LevelProblem* __restrict__ tab, const int2* __restrict__ map, int depth,
+                                     double l2, double lr) {
+  const int2 m = map[blockIdx.x];
+  const LevelProblem& P = tab[m.x];
+  apply_body<GH>(P.bins, P.n, P.G, P.sp, depth, P.child_totals, nullptr, l2, lr, P.leaf, nullptr, P.pred, P.vals, P.y,
+                 P.loss, static_cast<GH*>(P.g), static_cast<GH*>(P.h), m.y, P.apply_blocks);
+}
+
+__global__ void record_batched_kernel(const LevelProblem* __restrict__ tab, int depth, int trees) {
+  const LevelProblem& P = tab[blockIdx.x];
+  record_tree_body(P.sp, P.vals, depth, P.splits_out, P.values_out, P.counter, trees);
 }
 
 cbg_status check_state(cbg_ctx* ctx, const Layout& L, void* state, size_t bytes) {
@@ -1253,7 +1409,12 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
                  L.threads == L0.threads;
     nb_alloc = std::max(nb_alloc, L.nb_alloc);
   }
-  std::vector<HistProblem*> tables;   // device tables, one per level
+  std::vector<HistProblem*> tables;        // histogram tables, one per level
+  std::vector<LevelProblem*> ltables;      // level tables, one per level
+  std::vector<int2*> reduce_maps;          // block maps of the reduction, one per level
+  int2 *begin_map = nullptr, *score_map = nullptr, *tile_map = nullptr, *apply_map = nullptr;
+  int begin_blocks = 0, score_blocks = 0, tile_blocks = 0, apply_blocks = 0;
+  std::vector<int> reduce_blocks;
   if (batch_hist) {
     cbg_status st = hist_cluster_size(ctx, hist_config(L0), &cs_plan);
     if (st != CBG_OK) return st;
@@ -1263,26 +1424,109 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
     batch_hist = st == CBG_OK;
   }
   if (batch_hist) {
-    const size_t per_level = static_cast<size_t>(n_problems) * sizeof(HistProblem);
-    cbg_status st = ws_reserve(ctx, depth * (per_level + 256) + 256);
+    // host copies of every table and block map, then one upload into the workspace
+    std::vector<Layout> Ls(n_problems);
+    for (int i = 0; i < n_problems; ++i) make_layout(ctx, &problems[i].shape, &Ls[i]);
+    std::vector<std::vector<HistProblem>> hts(depth, std::vector<HistProblem>(n_problems));
+    std::vector<std::vector<LevelProblem>> lts(depth, std::vector<LevelProblem>(n_problems));
+    std::vector<int2> bmap, smap, tmap, amap;
+    std::vector<std::vector<int2>> rmaps(depth);
+    for (int i = 0; i < n_problems; ++i) {
+      const cbg_problem& p = problems[i];
+      const Layout& L = Ls[i];
+      void* S = p.state;
+      const int apply_grid = static_cast<int>(grid_stride_blocks(L.n, 256));
+      for (int b = 0; b < static_cast<int>(ceil_div(L.n, BEGIN_ROWS)); ++b) bmap.push_back(make_int2(i, b));
+      for (int b = 0; b < L.F; ++b) smap.push_back(make_int2(i, b));
+      for (int64_t b = 0; b < L.n_ptiles; ++b) tmap.push_back(make_int2(i, static_cast<int>(b)));
+      for (int b = 0; b < apply_grid; ++b) amap.push_back(make_int2(i, b));
+      for (int d = 0; d < depth; ++d) {
+        hts[d][i] = HistProblem{p.bins, L.n, L.G, L.F,
+                                d == 0 ? nullptr : at<uint32_t>(S, d % 2 == 1 ? L.o_order_a : L.o_order_b),
+                                p.g, p.h, at<Plan>(S, L.o_plan), L.max_bins, at<float>(S, L.o_part)};
+        LevelProblem& q = lts[d][i];
+        q = LevelProblem{};
+        q.bins = p.bins;
+        q.bins_t = p.bins_t;
+        q.n = L.n;
+        q.F = L.F;
+        q.G = L.G;
+        q.max_bins = L.max_bins;
+        q.rows_per_item = L.rows_per_item;
+        q.cs = cs_plan;
+        q.n_ptiles = L.n_ptiles;
+        q.apply_blocks = apply_grid;
+        q.n_borders = p.n_borders;
+        q.y = p.y;
+        q.loss = p.loss;
+        q.pred = p.pred;
+        q.g = p.g;
+        q.h = p.h;
+        q.leaf = p.leaf;
+        q.sp = at<cbg_split>(S, L.o_gsplit);
+        q.vals = at<double>(S, L.o_gvals);
+        q.child_totals = p.child_totals;
+        q.splits_out = p.splits;
+        q.values_out = p.leaf_values;
+        q.counter = reinterpret_cast<unsigned*>(at<char>(S, L.o_gsplit) + sizeof(cbg_split) * MAX_DEPTH);
+        q.plan = at<Plan>(S, L.o_plan);
+        q.partials = at<float>(S, L.o_part);
+        q.hist_df = at<float2>(S, L.o_hdf);
+        q.best = at<BestF>(S, L.o_best);
+        q.misc = at<Misc>(S, L.o_misc);
+        q.flags = at<uint8_t>(S, L.o_flags);
+        q.tcnt = at<uint32_t>(S, L.o_tcnt);
+        q.rows_hist = at<unsigned long long>(S, L.o_count);
+        q.seg_root = at<Segs>(S, L.o_seg_a);
+        q.seg_cur = at<Segs>(S, d % 2 == 0 ? L.o_seg_a : L.o_seg_b);
+        q.seg_nxt = at<Segs>(S, d % 2 == 0 ? L.o_seg_b : L.o_seg_a);
+        q.order_cur = d == 0 ? nullptr : at<uint32_t>(S, d % 2 == 1 ? L.o_order_a : L.o_order_b);
+        q.order_nxt = at<uint32_t>(S, (d + 1) % 2 == 1 ? L.o_order_a : L.o_order_b);
+        q.hist_cur = at<double>(S, d % 2 == 0 ? L.o_hist_a : L.o_hist_b);
+        q.hist_prev = at<double>(S, d % 2 == 0 ? L.o_hist_b : L.o_hist_a);
+        const int n_small = d == 0 ? 1 : (1 << (d - 1));
+        const int rb = L.G * static_cast<int>(ceil_div(L.max_bins, RD_BINS)) * n_small;
+        for (int b = 0; b < rb; ++b) rmaps[d].push_back(make_int2(i, b));
+      }
+    }
+    size_t need = 4096;
+    auto bytes = [](size_t v) { return (v + 255) / 256 * 256; };
+    need += depth * (bytes(sizeof(HistProblem) * n_problems) + bytes(sizeof(LevelProblem) * n_problems));
+    need += bytes(sizeof(int2) * bmap.size()) + bytes(sizeof(int2) * smap.size()) + bytes(sizeof(int2) * tmap.size()) +
+            bytes(sizeof(int2) * amap.size());
+    for (int d = 0; d < depth; ++d) need += bytes(sizeof(int2) * rmaps[d].size());
+    cbg_status st = ws_reserve(ctx, need);
     if (st != CBG_OK) return st;
     Carve cv(ctx->ws);
-    std::vector<HistProblem> host(n_problems);
-    for (int d = 0; d < depth; ++d) {
-      for (int i = 0; i < n_problems; ++i) {
-        const cbg_problem& p = problems[i];
-        Layout L;
-        make_layout(ctx, &p.shape, &L);
-        void* S = p.state;
-        host[i] = HistProblem{p.bins, L.n, L.G, L.F,
-                              d == 0 ? nullptr : at<uint32_t>(S, d % 2 == 1 ? L.o_order_a : L.o_order_b),
-                              p.g, p.h, at<Plan>(S, L.o_plan), L.max_bins, at<float>(S, L.o_part)};
-      }
-      HistProblem* dev = cv.take<HistProblem>(n_problems);
-      CBG_CUDA(ctx, cudaMemcpyAsync(dev, host.data(), per_level, cudaMemcpyHostToDevice, ctx->stream));
-      tables.push_back(dev);
+    auto upload = [&](const void* host, size_t n_bytes, void* dev) -> cbg_status {
+      CBG_CUDA(ctx, cudaMemcpyAsync(dev, host, n_bytes, cudaMemcpyHostToDevice, ctx->stream));
+      return CBG_OK;
+    };
+    for (int d = 0; d < depth && st == CBG_OK; ++d) {
+      tables.push_back(cv.take<HistProblem>(n_problems));
+      st = upload(hts[d].data(), sizeof(HistProblem) * n_problems, tables.back());
+      if (st != CBG_OK) break;
+      ltables.push_back(cv.take<LevelProblem>(n_problems));
+      st = upload(lts[d].data(), sizeof(LevelProblem) * n_problems, ltables.back());
+      if (st != CBG_OK) break;
+      reduce_maps.push_back(cv.take<int2>(rmaps[d].size()));
+      reduce_blocks.push_back(static_cast<int>(rmaps[d].size()));
+      st = upload(rmaps[d].data(), sizeof(int2) * rmaps[d].size(), reduce_maps.back());
     }
-    CBG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the host staging vector is reused
+    begin_map = cv.take<int2>(bmap.size());
+    score_map = cv.take<int2>(smap.size());
+    tile_map = cv.take<int2>(tmap.size());
+    apply_map = cv.take<int2>(amap.size());
+    if (st == CBG_OK) st = upload(bmap.data(), sizeof(int2) * bmap.size(), begin_map);
+    if (st == CBG_OK) st = upload(smap.data(), sizeof(int2) * smap.size(), score_map);
+    if (st == CBG_OK) st = upload(tmap.data(), sizeof(int2) * tmap.size(), tile_map);
+    if (st == CBG_OK) st = upload(amap.data(), sizeof(int2) * amap.size(), apply_map);
+    if (st != CBG_OK) return st;
+    begin_blocks = static_cast<int>(bmap.size());
+    score_blocks = static_cast<int>(smap.size());
+    tile_blocks = static_cast<int>(tmap.size());
+    apply_blocks = static_cast<int>(amap.size());
+    CBG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the host staging vectors go out of scope
   }
   if (!ctx->capture_stream) CBG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
   while (static_cast<int>(ctx->branch_streams.size()) < nb) {
@@ -1340,71 +1584,51 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
       if (st == CBG_OK) record(i);
     }
   } else {
-    for (int i = 0; i < n_problems && st == CBG_OK; ++i) {
-      ctx->stream = ctx->branch_streams[i % nb];
-      st = cbg_tree_begin(ctx, args[i].shape, args[i].state, args[i].state_bytes, args[i].leaf);
-    }
+    // every kernel of the round is one launch over all problems, on the origin stream
+    join();
+    ctx->stream = origin;
+    auto launched = [&](const char* what) {
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess && st == CBG_OK) st = fail(ctx, CBG_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+    };
+    begin_batched_kernel<<<begin_blocks, 256, 0, origin>>>(ltables[0], begin_map);
+    launched("batched tree start");
     for (int d = 0; d < depth && st == CBG_OK; ++d) {
-      join();
-      ctx->stream = origin;
-      if (st == CBG_OK)
-        st = gh_dtype == CBG_F32
-                 ? launch_hist_batched<float>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan)
-                 : launch_hist_batched<__nv_bfloat16>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan);
-      fork();
-      for (int i = 0; i < n_problems && st == CBG_OK; ++i) {
-        const cbg_problem& p = problems[i];
-        Layout L;
-        st = make_layout(ctx, &p.shape, &L);
-        if (st != CBG_OK) break;
-        ctx->stream = ctx->branch_streams[i % nb];
-        cbg_level_args la{};
-        la.shape = &p.shape;
-        la.state = p.state;
-        la.state_bytes = p.state_bytes;
-        la.bins = p.bins;
-        la.bins_t = p.bins_t;
-        la.n_borders = p.n_borders;
-        la.g = p.g;
-        la.h = p.h;
-        la.gh_dtype = gh_dtype;
-        la.depth = d;
-        la.l2 = l2;
-        la.force_feature = -1;
-        la.force_border = -1;
-        la.leaf = p.leaf;
-        la.splits = at<cbg_split>(p.state, L.o_gsplit);
-        la.child_totals = p.child_totals;
-        la.last_level = d == depth - 1;
-        st = build_level_impl(ctx, &la, false);
+      st = gh_dtype == CBG_F32
+               ? launch_hist_batched<float>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan)
+               : launch_hist_batched<__nv_bfloat16>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan);
+      if (st != CBG_OK) break;
+      reduce_batched_kernel<<<reduce_blocks[d], RD_THREADS, 0, origin>>>(ltables[d], reduce_maps[d], d);
+      launched("batched reduction");
+      const int level_leaves = 1 << d;
+      auto score = [&](auto warps) {
+        constexpr int W = decltype(warps)::value;
+        score_batched_kernel<W><<<score_blocks, W * 32, 0, origin>>>(ltables[d], score_map, level_leaves, l2, d);
+      };
+      if (level_leaves >= SC_MAX_WARPS) score(std::integral_constant<int, SC_MAX_WARPS>{});
+      else if (level_leaves >= 8) score(std::integral_constant<int, 8>{});
+      else if (level_leaves >= 4) score(std::integral_constant<int, 4>{});
+      else if (level_leaves >= 2) score(std::integral_constant<int, 2>{});
+      else score(std::integral_constant<int, 1>{});
+      launched("batched scoring");
+      const bool last = d == depth - 1;
+      flags_batched_kernel<<<tile_blocks, PT_THREADS, 0, origin>>>(ltables[d], tile_map, d, last ? 0 : 1);
+      launched("batched partition flags");
+      if (!last) {
+        scatter_batched_kernel<<<tile_blocks, PT_THREADS, 0, origin>>>(ltables[d], tile_map, d);
+        launched("batched partition scatter");
       }
     }
-    for (int i = 0; i < n_problems && st == CBG_OK; ++i) {
-      const cbg_problem& p = problems[i];
-      Layout L;
-      st = make_layout(ctx, &p.shape, &L);
-      if (st != CBG_OK) break;
-      ctx->stream = ctx->branch_streams[i % nb];
-      cbg_apply_args aa{};
-      aa.bins = p.bins;
-      aa.n = p.shape.n;
-      aa.F_pad = p.shape.F_pad;
-      aa.splits = at<cbg_split>(p.state, L.o_gsplit);
-      aa.depth = depth;
-      aa.leaf_totals = p.child_totals;
-      aa.l2 = l2;
-      aa.lr = lr;
-      aa.leaf_in = p.leaf;
-      aa.pred = p.pred;
-      aa.leaf_values_out = at<double>(p.state, L.o_gvals);
-      aa.y = p.y;
-      aa.loss = p.loss;
-      aa.gh_dtype = gh_dtype;
-      aa.g = p.g;
-      aa.h = p.h;
-      st = cbg_apply_tree(ctx, &aa);
-      if (st == CBG_OK) record(i);
+    if (st == CBG_OK) {
+      if (gh_dtype == CBG_F32)
+        apply_batched_kernel<float><<<apply_blocks, 256, 0, origin>>>(ltables[0], apply_map, depth, l2, lr);
+      else
+        apply_batched_kernel<__nv_bfloat16><<<apply_blocks, 256, 0, origin>>>(ltables[0], apply_map, depth, l2, lr);
+      launched("batched apply");
+      record_batched_kernel<<<n_problems, 256, 0, origin>>>(ltables[0], depth, trees);
+      launched("batched record");
     }
+    fork();
   }
   join();
   ctx->stream = origin;
