@@ -79,6 +79,9 @@ def lib():
                                   f64p, i32p, i32p, f64p, f64p, f64p, f64p]),
                 "or_ts_full": (None, [u32p, f32p, i64, f64, f64, u32p, i64, f32p]),
                 "or_predict": (None, [u8p, i64, i32, i32p, i32p, f64p, i32, i32, f64, f64p]),
+                "or_ordered_sup_size": (i64, [i64]),
+                "or_fit_ordered": (None, [u8p, i64, i32, i32, i32p, i32, f32p, i32, i32, i32, f64, f64, u32p, i32,
+                                          f64p, i32p, i32p, f64p, f64p, f64p, f64p, f64p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -270,6 +273,48 @@ def fit(bins, F: int, n_borders, y, loss_name: str, depth: int, trees: int, lr: 
             "leaf_values": lv, "losses": losses, "max_bins": max_bins}
 
 
+def ordered_sup_size(n: int) -> int:
+    """Number of supporting values one permutation keeps: sum_i min(2^(i+1), n)."""
+    return int(lib().or_ordered_sup_size(n))
+
+
+def ordered_sup_offsets(n: int) -> np.ndarray:
+    """Start of each supporting model M'_i in one permutation's values (length I+2)."""
+    I = (n - 1).bit_length() - 1 if n > 1 else 0
+    off = [0]
+    for i in range(I + 1):
+        off.append(off[-1] + min(2 << i, n))
+    return np.array(off, np.int64)
+
+
+def fit_ordered(bins, F: int, n_borders, y, loss_name: str, depth: int, trees: int, lr: float, l2: float,
+                perms, pred=None):
+    """Ordered boosting (Section 3, Algorithm 1 with the log-scale supporting models).
+    bins: [s][n][F_pad], permutation q's bins (row order); perms: [s][n] (position -> row).
+    Returns the dict of fit() plus sup [s][n_sup], the supporting models' values."""
+    bins = _c(bins, np.uint8)
+    s, n, F_pad = bins.shape
+    perms = _c(perms, np.uint32)
+    assert perms.shape == (s, n)
+    nb = _c(n_borders, np.int32)
+    max_bins = int(nb.max()) + 1 if nb.size else 1
+    y = _c(y, np.float32)
+    pred = np.zeros(n, np.float64) if pred is None else _c(pred, np.float64).copy()
+    T, D = trees, depth
+    sf = np.empty((T, D), np.int32)
+    sk = np.empty((T, D), np.int32)
+    ss = np.empty((T, D), np.float64)
+    s2 = np.empty((T, D), np.float64)
+    lv = np.empty((T, 1 << D), np.float64)
+    losses = np.empty(T, np.float64)
+    sup = np.empty((s, ordered_sup_size(n)), np.float64)
+    lib().or_fit_ordered(_p(bins, _u8), n, F_pad, F, _p(nb, _i32), max_bins, _p(y, _f32), LOSS[loss_name], D, T,
+                         lr, l2, _p(perms, _u32), s, _p(pred, _f64), _p(sf, _i32), _p(sk, _i32), _p(ss, _f64),
+                         _p(s2, _f64), _p(lv, _f64), _p(losses, _f64), _p(sup, _f64))
+    return {"pred": pred, "split_f": sf, "split_k": sk, "score": ss, "second": s2,
+            "leaf_values": lv, "losses": losses, "max_bins": max_bins, "sup": sup}
+
+
 def ts_full(cat, y, prior_value: float, a: float, cat_new):
     """Full-data TS of new rows (float32 [m]): every training row counts."""
     cat, y, cat_new = _c(cat, np.uint32), _c(y, np.float32), _c(cat_new, np.uint32)
@@ -306,3 +351,26 @@ def preprocess(workload, F_pad: int):
     borders, nb = select_borders(cols, w.max_borders)
     bins = quantize(cols, borders, nb, F_pad)
     return {"perm": perm, "prior": P, "ts": ts, "borders": borders, "n_borders": nb, "bins": bins}
+
+
+def preprocess_ordered(workload, F_pad: int, s: int):
+    """preprocess() for s permutations: sigma_q from seed + q, the ordered TS of every
+    categorical column along each sigma_q, borders from the float columns and sigma_0's
+    TS, and each permutation's bins with those borders. Returns the dict of preprocess()
+    (permutation 0) plus perms [s][n] and bins_all [s][n][F_pad]."""
+    w = workload
+    base = preprocess(w, F_pad)
+    perms = np.empty((s, w.n), np.uint32)
+    bins_all = np.empty((s, w.n, F_pad), np.uint8)
+    perms[0], bins_all[0] = base["perm"], base["bins"]
+    for q in range(1, s):
+        perms[q] = make_permutation(w.seed + q, w.n)
+        bins_all[q] = base["bins"]
+        if w.n_cat:
+            ts = np.empty((w.n_cat, w.n), np.float32)
+            for c in range(w.n_cat):
+                ts[c] = ordered_ts(w.cat[c], w.y, perms[q], base["prior"], w.a)[0]
+            quantize(ts, base["borders"][w.n_features - w.n_cat:], base["n_borders"][w.n_features - w.n_cat:],
+                     F_pad, f_offset=w.n_features - w.n_cat, bins=bins_all[q])
+    base.update(perms=perms, bins_all=bins_all)
+    return base

@@ -29,6 +29,8 @@
 //                    the statistic of a row that is not in the training permutation
 //   prediction       Section 4 "Fast scorer": a row's model value is the sum over
 //                    trees of the value of the leaf its binary features select
+//   ordered boosting Section 3 "Fighting Gradient Bias", Algorithm 1 with the
+//                    log-scale supporting models M'_i and shared tree structures
 //
 // Parity pins for every function live in tests/test_oracle_*.py.
 
@@ -435,6 +437,117 @@ void or_predict(const uint8_t* bins, int64_t n, int F_pad, const int* split_f, c
     }
     pred[r] = s;
   }
+}
+
+// ---------------------------------------------------------- ordered boosting
+// Ordered boosting (Section 3, Algorithm 1) in the log-scale form the section describes,
+// with these readings where it is silent:
+//  - s permutations sigma_q (perms [s][n], position -> row). Each has its own bins
+//    (bins [s][n][F_pad], row order): the float columns are shared, the categorical
+//    columns hold the ordered TS computed along sigma_q (the section uses the TS
+//    permutations for the gradients too), quantised with one set of borders;
+//  - tree t takes its structure from permutation r = t mod s: bins of sigma_r and the
+//    ordered gradients of sigma_r;
+//  - positions are 0-based. The supporting model M'_{q,i}, i = 0..floor(log2(n-1)), is
+//    trained on positions p < 2^i of sigma_q and holds values for positions
+//    j < min(2^(i+1), n). The gradient at position k >= 1 is taken at
+//    M'_{r, floor(log2 k)}(x_k), trained on positions < 2^floor(log2 k) <= k, so never
+//    on x_k itself; position 0 has no earlier sample and takes the starting value 0;
+//  - the structure is searched greedily level by level on those gradients exactly as in
+//    classic boosting (histograms, score, leaf update);
+//  - the final model's leaf values are Newton steps on the plain gradients of all rows
+//    at its own prediction (the second phase, done the classic way), with leaf indices
+//    on the bins of permutation 0;
+//  - every supporting model of every permutation takes the same structure (leaf indices
+//    on its permutation's bins) and Newton leaf values from the gradients at its own
+//    values on its first 2^i positions, added (times lr) at all positions it holds.
+// Gradients are rounded to FP32 storage as in or_fit. sup_out (optional) receives the
+// supporting values [s][n_sup], n_sup = sum_i min(2^(i+1), n), models in order of i,
+// each model's values by position.
+static int floor_log2(int64_t k) {
+  int r = 0;
+  while ((int64_t(1) << (r + 1)) <= k) ++r;
+  return r;
+}
+
+int64_t or_ordered_sup_size(int64_t n) {
+  if (n <= 0) return 0;
+  const int I = n > 1 ? floor_log2(n - 1) : 0;
+  int64_t tot = 0;
+  for (int i = 0; i <= I; ++i) tot += std::min<int64_t>(int64_t(2) << i, n);
+  return tot;
+}
+
+void or_fit_ordered(const uint8_t* bins, int64_t n, int F_pad, int F, const int* n_borders, int max_bins,
+                    const float* y, int loss, int depth, int trees, double lr, double l2, const uint32_t* perms,
+                    int s, double* pred, int* split_f, int* split_k, double* split_score, double* split_second,
+                    double* leaf_values, double* losses, double* sup_out) {
+  const int L = 1 << depth;
+  const int I = n > 1 ? floor_log2(n - 1) : 0;
+  std::vector<int64_t> off(I + 2, 0);
+  for (int i = 0; i <= I; ++i) off[i + 1] = off[i] + std::min<int64_t>(int64_t(2) << i, n);
+  const int64_t n_sup = off[I + 1];
+  const size_t plane = static_cast<size_t>(n) * F_pad;
+  std::vector<double> sup(static_cast<size_t>(s) * n_sup, 0.0);
+  std::vector<double> go(n), ho(n), gp(n), hp(n);
+  std::vector<uint16_t> leaf(n), leafq(n);
+  std::vector<double> hist(static_cast<size_t>(L / 2 > 0 ? L / 2 : 1) * F * max_bins * 2);
+  std::vector<double> scores(static_cast<size_t>(F) * (max_bins > 1 ? max_bins - 1 : 1));
+  std::vector<double> tot(2 * L), v(L);
+  auto grad = [&](double a, float yv, double* g, double* h) { or_gradients(loss, &yv, &a, 1, 0, g, h); };
+  for (int t = 0; t < trees; ++t) {
+    const int r = t % s;
+    const uint32_t* sig = perms + static_cast<int64_t>(r) * n;
+    const uint8_t* bins_r = bins + r * plane;
+    const double* sup_r = sup.data() + static_cast<size_t>(r) * n_sup;
+    // gradients for the structure: position k from M'_{r, floor(log2 k)}
+    for (int64_t k = 0; k < n; ++k) {
+      const double a = k == 0 ? 0.0 : sup_r[off[floor_log2(k)] + k];
+      grad(a, y[sig[k]], &go[sig[k]], &ho[sig[k]]);
+    }
+    std::fill(leaf.begin(), leaf.end(), 0);
+    for (int d = 0; d < depth; ++d) {
+      int bf, bk;
+      double bs, ss;
+      or_histogram(bins_r, n, F_pad, F, go.data(), ho.data(), leaf.data(), 1 << d, max_bins, hist.data());
+      or_split_scores(hist.data(), 1 << d, F, n_borders, max_bins, l2, scores.data(), &bf, &bk, &bs, &ss);
+      split_f[t * depth + d] = bf;
+      split_k[t * depth + d] = bk;
+      split_score[t * depth + d] = bs;
+      split_second[t * depth + d] = ss;
+      or_update_leaf(bins_r, n, F_pad, bf, bk, d, leaf.data());
+    }
+    const int* tf = split_f + t * depth;
+    const int* tk = split_k + t * depth;
+    // the final model: plain gradients of every row at its prediction
+    or_tree_leaf_index(bins, n, F_pad, tf, tk, depth, leafq.data());
+    or_gradients(loss, y, pred, n, 0, gp.data(), hp.data());
+    or_leaf_totals(gp.data(), hp.data(), leafq.data(), n, L, tot.data());
+    or_leaf_values(tot.data(), L, l2, v.data());
+    for (int l = 0; l < L; ++l) leaf_values[static_cast<int64_t>(t) * L + l] = v[l];
+    or_apply_leaf_values(leafq.data(), n, v.data(), lr, pred);
+    losses[t] = or_loss(loss, y, pred, n);
+    // the supporting models of every permutation
+    for (int q = 0; q < s; ++q) {
+      const uint32_t* sq = perms + static_cast<int64_t>(q) * n;
+      or_tree_leaf_index(bins + q * plane, n, F_pad, tf, tk, depth, leafq.data());
+      double* sm = sup.data() + static_cast<size_t>(q) * n_sup;
+      for (int i = 0; i <= I; ++i) {
+        const int64_t train = std::min<int64_t>(int64_t(1) << i, n);
+        const int64_t held = std::min<int64_t>(int64_t(2) << i, n);
+        std::fill(tot.begin(), tot.end(), 0.0);
+        for (int64_t p = 0; p < train; ++p) {
+          double g, h;
+          grad(sm[off[i] + p], y[sq[p]], &g, &h);
+          tot[2 * leafq[sq[p]]] += g;
+          tot[2 * leafq[sq[p]] + 1] += h;
+        }
+        or_leaf_values(tot.data(), L, l2, v.data());
+        for (int64_t j = 0; j < held; ++j) sm[off[i] + j] += lr * v[leafq[sq[j]]];
+      }
+    }
+  }
+  if (sup_out) std::copy(sup.begin(), sup.end(), sup_out);
 }
 
 }  // extern "C"
