@@ -448,6 +448,83 @@ typedef struct cbg_autotune_args {
 cbg_status cbg_autotune_state_bytes(const cbg_tree_shape* shape, size_t* bytes);
 cbg_status cbg_autotune_tiles(cbg_ctx* ctx, const cbg_autotune_args* args, cbg_tiles* best, double* best_ms);
 
+/* ------------------------------------------------- ordered boosting ---- */
+/* Ordered boosting (Section 3 "Fighting Gradient Bias", Algorithm 1, with the
+ * log-scale supporting models M'_i and tree structures shared by all models).
+ *
+ * There are s permutations sigma_q (position -> row). Each has its own bins: the
+ * float columns are shared and the categorical columns hold the ordered TS
+ * computed along sigma_q, quantised with one set of borders. Every permutation's
+ * data is kept in its own position order (cbg_permute_rows).
+ *
+ * Supporting values of one permutation: cbg_ordered_sup_len(n) floats,
+ * 2^(I+1) + n with I = floor(log2(n-1)) (I = 0 for n = 1). Model M'_i,
+ * i = 0..I, is trained on positions p < 2^i and holds positions
+ * j < min(2^(i+1), n), position j at element 2^(i+1) + j (the last model at
+ * 2^(I+1) + j); elements 0 and 1 are unused. A fresh run starts from zeros. */
+cbg_status cbg_ordered_sup_len(int64_t n, int64_t* len);
+
+/* Bytes of the device work buffer cbg_boost_ordered needs (leaf indices of every
+ * permutation and FP64 leaf totals). */
+cbg_status cbg_ordered_work_bytes(int64_t n, int32_t s, int32_t depth, size_t* bytes);
+
+/* Rows into the position order of perm (device uint32 [n], position -> row):
+ * bins_pos[g][k][.] = bins[g][perm[k]][.] in the grouped layout (F_pad a
+ * multiple of 32, both 16-byte aligned), bins_t_pos[f][k] = bins_t[f][perm[k]]
+ * ([F][n]), y_pos[k] = y[perm[k]]. Each input may be NULL to skip it; outputs
+ * are device buffers of the same sizes, owned by the caller. */
+cbg_status cbg_permute_rows(cbg_ctx* ctx, const uint32_t* perm, int64_t n, int32_t F, int32_t F_pad,
+                            const uint8_t* bins, const uint8_t* bins_t, const float* y, uint8_t* bins_pos,
+                            uint8_t* bins_t_pos, float* y_pos);
+
+/* Arguments of cbg_boost_ordered. All pointers are device memory except shape. */
+typedef struct cbg_ordered_args {
+  const cbg_tree_shape* shape; /* n, F, F_pad, max_bins, max_depth, tiles      */
+  void* state;                 /* tree-state scratch (cbg_tree_state_bytes)    */
+  size_t state_bytes;
+  int32_t s;                   /* permutations, >= 1                           */
+  const uint8_t* bins_pos;     /* [s][F_pad/32][n][32]: permutation q's bins in its position order */
+  const uint8_t* bins_t_pos;   /* [s][F][n] the same, per feature, or NULL     */
+  const float* y_pos;          /* [s][n] labels in each position order         */
+  const uint8_t* bins;         /* grouped, row order: the final model's bins (permutation 0's) */
+  const uint8_t* bins_t;       /* [F][n] row order, or NULL                    */
+  const int32_t* n_borders;    /* [F]                                          */
+  const float* y;              /* [n] row order                                */
+  int32_t loss;                /* CBG_LOSS_RMSE or CBG_LOSS_LOGLOSS            */
+  int32_t gh_dtype;            /* storage of the ordered gradients             */
+  int32_t depth;
+  int32_t trees;
+  int32_t first_tree;          /* tree t of the call takes permutation (first_tree + t) mod s */
+  double lr;
+  double l2;
+  float* pred;                 /* [n] row order, in/out: the final model       */
+  float* sup;                  /* [s][cbg_ordered_sup_len(n)] in/out           */
+  void* g;                     /* [n] scratch of gh_dtype                      */
+  void* h;
+  uint16_t* leaf;              /* [n] scratch                                  */
+  cbg_split* splits;           /* [trees][depth] out                           */
+  double* leaf_values;         /* [trees][2^depth] out, v before lr            */
+  double* child_totals;        /* [2^depth][2] scratch                         */
+  void* work;                  /* cbg_ordered_work_bytes(n, s, depth) bytes    */
+  size_t work_bytes;
+  int32_t use_graph;           /* nonzero: after the first tree, replay one captured tree per permutation */
+} cbg_ordered_args;
+
+/* `trees` iterations of ordered boosting. Tree t (permutation r = (first_tree +
+ * t) mod s):
+ *  1. ordered gradients: position k >= 1 of sigma_r at M'_{r,floor(log2 k)}(x_k),
+ *     position 0 at the start value 0 (stored in gh_dtype, position order);
+ *  2. the structure: cbg_build_level for every level on permutation r's bins;
+ *  3. the final model (the second phase, done the classic way): leaf indices on
+ *     `bins`, FP64 totals of the plain gradients at pred, v = -G/(H+l2),
+ *     pred += float(lr v);
+ *  4. every supporting model of every permutation: leaf indices on its
+ *     permutation's bins, FP64 totals of the gradients at its own values over its
+ *     training positions, v = -G/(H+l2) (0 when H+l2 = 0), and float(lr v) added
+ *     at every position it holds.
+ * Gradients are computed in FP32. */
+cbg_status cbg_boost_ordered(cbg_ctx* ctx, const cbg_ordered_args* args);
+
 #ifdef __cplusplus
 }
 #endif

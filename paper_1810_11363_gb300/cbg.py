@@ -86,6 +86,15 @@ class Problem(C.Structure):
                 ("leaf_values", c_vp), ("child_totals", c_vp)]
 
 
+class OrderedArgs(C.Structure):
+    _fields_ = [("shape", C.POINTER(TreeShape)), ("state", c_vp), ("state_bytes", C.c_size_t), ("s", c_i32),
+                ("bins_pos", c_vp), ("bins_t_pos", c_vp), ("y_pos", c_vp), ("bins", c_vp), ("bins_t", c_vp),
+                ("n_borders", c_vp), ("y", c_vp), ("loss", c_i32), ("gh_dtype", c_i32), ("depth", c_i32),
+                ("trees", c_i32), ("first_tree", c_i32), ("lr", c_f64), ("l2", c_f64), ("pred", c_vp),
+                ("sup", c_vp), ("g", c_vp), ("h", c_vp), ("leaf", c_vp), ("splits", c_vp), ("leaf_values", c_vp),
+                ("child_totals", c_vp), ("work", c_vp), ("work_bytes", C.c_size_t), ("use_graph", c_i32)]
+
+
 # name -> (restype, argtypes); every entry point declared in include/cbg.h
 SIGNATURES = {
     "cbg_version": (C.c_char_p, []),
@@ -116,6 +125,10 @@ SIGNATURES = {
     "cbg_predict": (c_i32, [c_vp, C.POINTER(PredictArgs)]),
     "cbg_autotune_state_bytes": (c_i32, [C.POINTER(TreeShape), C.POINTER(C.c_size_t)]),
     "cbg_autotune_tiles": (c_i32, [c_vp, C.POINTER(AutotuneArgs), C.POINTER(Tiles), C.POINTER(c_f64)]),
+    "cbg_ordered_sup_len": (c_i32, [c_i64, C.POINTER(c_i64)]),
+    "cbg_ordered_work_bytes": (c_i32, [c_i64, c_i32, c_i32, C.POINTER(C.c_size_t)]),
+    "cbg_permute_rows": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "cbg_boost_ordered": (c_i32, [c_vp, C.POINTER(OrderedArgs)]),
 }
 
 _lock = threading.Lock()
@@ -344,3 +357,37 @@ def cbg_boost_batched(ctx: Context, problems, gh_dtype: str, depth: int, trees: 
     arr = (Problem * len(problems))(*problems)
     ctx.check(ctx.lib.cbg_boost_batched(ctx.h, arr, len(problems), DTYPE[gh_dtype], depth, trees, lr, l2, branches),
               "cbg_boost_batched")
+
+
+def cbg_ordered_sup_len(n: int) -> int:
+    out = c_i64()
+    st = load().cbg_ordered_sup_len(n, C.byref(out))
+    if st != CBG_OK:
+        raise CbgError(st, "cbg_ordered_sup_len: n must be in [1, 2^31-1]")
+    return int(out.value)
+
+
+def cbg_ordered_work_bytes(n: int, s: int, depth: int) -> int:
+    out = C.c_size_t()
+    st = load().cbg_ordered_work_bytes(n, s, depth, C.byref(out))
+    if st != CBG_OK:
+        raise CbgError(st, "cbg_ordered_work_bytes: invalid n, s or depth")
+    return int(out.value)
+
+
+def cbg_permute_rows(ctx: Context, perm, n: int, F: int, F_pad: int, bins=None, bins_t=None, y=None, bins_pos=None,
+                     bins_t_pos=None, y_pos=None):
+    ctx.check(ctx.lib.cbg_permute_rows(ctx.h, _p(perm), n, F, F_pad, _p(bins), _p(bins_t), _p(y), _p(bins_pos),
+                                       _p(bins_t_pos), _p(y_pos)), "cbg_permute_rows")
+
+
+def cbg_boost_ordered(ctx: Context, shape: TreeShape, state, s: int, bins_pos, bins_t_pos, y_pos, bins, bins_t,
+                      n_borders, y, loss: str, gh_dtype: str, depth: int, trees: int, first_tree: int, lr: float,
+                      l2: float, pred, sup, g, h, leaf, splits, leaf_values, child_totals, work,
+                      use_graph: bool = False):
+    a = OrderedArgs(C.pointer(shape), _p(state), state.numel() * state.element_size(), s, _p(bins_pos),
+                    _p(bins_t_pos), _p(y_pos), _p(bins), _p(bins_t), _p(n_borders), _p(y), LOSS[loss],
+                    DTYPE[gh_dtype], depth, trees, first_tree, lr, l2, _p(pred), _p(sup), _p(g), _p(h), _p(leaf),
+                    _p(splits), _p(leaf_values), _p(child_totals), _p(work), work.numel() * work.element_size(),
+                    int(use_graph))
+    ctx.check(ctx.lib.cbg_boost_ordered(ctx.h, C.byref(a)), "cbg_boost_ordered")

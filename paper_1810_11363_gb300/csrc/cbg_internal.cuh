@@ -125,6 +125,19 @@ __device__ __forceinline__ void store_gh(__nv_bfloat16* p, int64_t i, float v) {
   p[i] = __float2bfloat16_rn(v);
 }
 
+// First and second derivative of the loss in the model value a (FP32): RMSE a - y and 1;
+// Logloss sigmoid(a) - y and sigmoid(a) (1 - sigmoid(a)).
+__device__ __forceinline__ void loss_grad(int loss, float a, float y, float* g, float* h) {
+  if (loss == CBG_LOSS_RMSE) {
+    *g = a - y;
+    *h = 1.0f;
+  } else {
+    const float s = 1.0f / (1.0f + expf(-a));
+    *g = s - y;
+    *h = s * (1.0f - s);
+  }
+}
+
 // Orderable 32-bit image of a finite float (ascending float order = ascending uint order),
 // with -0.0 mapped to +0.0.
 __device__ __forceinline__ uint32_t float_order_bits(float x) {

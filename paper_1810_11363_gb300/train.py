@@ -89,6 +89,7 @@ class Model:
     pred: object          # float32 [n] training predictions
     depth: int
     lr: float
+    sup: object = None    # ordered boosting: float32 [s][sup_len] supporting values
 
     def host_splits(self) -> np.ndarray:
         return decode_splits(self.splits)
@@ -133,6 +134,70 @@ def fit(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, trees: int, 
                   l2, bufs.pred, bufs.g, bufs.h, bufs.leaf, bufs.splits, bufs.leaf_values, bufs.child_totals,
                   bins_t=prep.bins_t, use_graph=use_graph)
     return Model(bufs.splits[:trees], bufs.leaf_values[:trees], bufs.pred, depth, lr)
+
+
+@dataclass
+class OrderedPrepared:
+    """Inputs of ordered boosting: permutation 0's row-order data (the final model's
+    bins) and every permutation's data in its own position order."""
+    base: Prepared
+    s: int
+    perms: object        # int32 [s][n], position -> row; perms[0] = base.perm
+    bins_pos: object     # uint8 [s][F_pad * n], grouped layout
+    bins_t_pos: object   # uint8 [s][F][n]
+    y_pos: object        # float32 [s][n]
+
+
+def preprocess_ordered(ctx: cbg.Context, x, cat, y, label_kind: str, max_borders: int, s: int, a: float = 1.0,
+                       seed: int = 0, prior: float | None = None) -> OrderedPrepared:
+    """preprocess() for s permutations: sigma_q from seed + q, the ordered TS of every
+    categorical column along sigma_q quantised with permutation 0's borders, and every
+    permutation's bins and labels gathered into its position order."""
+    import torch
+    base = preprocess(ctx, x, cat, y, label_kind, max_borders, a=a, seed=seed, prior=prior)
+    dev, n, F, Ff, F_pad = y.device, base.n, base.F, base.F_float, base.F_pad
+    Cc = F - Ff
+    perms = torch.empty((s, n), dtype=torch.int32, device=dev)
+    bins_pos = torch.empty((s, F_pad * n), dtype=torch.uint8, device=dev)
+    bins_t_pos = torch.empty((s, F, n), dtype=torch.uint8, device=dev)
+    y_pos = torch.empty((s, n), dtype=torch.float32, device=dev)
+    tmp = torch.empty_like(base.bins) if s > 1 else None
+    tmp_t = torch.empty_like(base.bins_t) if s > 1 else None
+    ts = torch.empty((Cc, n), dtype=torch.float32, device=dev)
+    for q in range(s):
+        cbg.cbg_make_permutation(ctx, seed + q, n, perms[q])
+        src, src_t = base.bins, base.bins_t
+        if q > 0:
+            tmp.copy_(base.bins)
+            tmp_t.copy_(base.bins_t)
+            if Cc:
+                cbg.cbg_ordered_ts(ctx, cat, y, n, Cc, perms[q], base.prior, a, label_kind, ts)
+                cbg.cbg_quantize(ctx, ts, n, Cc, base.borders[Ff:], base.n_borders[Ff:], max_borders, tmp, F_pad, Ff,
+                                 tmp_t)
+            src, src_t = tmp, tmp_t
+        cbg.cbg_permute_rows(ctx, perms[q], n, F, F_pad, src, src_t, y, bins_pos[q], bins_t_pos[q], y_pos[q])
+    cbg.cbg_sync(ctx)
+    return OrderedPrepared(base, s, perms, bins_pos, bins_t_pos, y_pos)
+
+
+def fit_ordered(ctx: cbg.Context, op: OrderedPrepared, y, loss: str, depth: int, trees: int, lr: float, l2: float,
+                gh_dtype: str = "f32", tiles: dict | None = None, bufs: FitBuffers | None = None, sup=None,
+                first_tree: int = 0, use_graph: bool = False) -> Model:
+    """Ordered boosting (cbg_boost_ordered). sup (float32 [s][sup_len], zeros for a fresh
+    run) is continued in place when given."""
+    import torch
+    base = op.base
+    if bufs is None:
+        bufs = alloc_fit(base, depth, trees, gh_dtype, tiles)
+    dev = base.bins.device
+    if sup is None:
+        sup = torch.zeros((op.s, cbg.cbg_ordered_sup_len(base.n)), dtype=torch.float32, device=dev)
+    work = torch.empty(cbg.cbg_ordered_work_bytes(base.n, op.s, depth), dtype=torch.uint8, device=dev)
+    cbg.cbg_boost_ordered(ctx, bufs.shape, bufs.state, op.s, op.bins_pos, op.bins_t_pos, op.y_pos, base.bins,
+                          base.bins_t, base.n_borders, y, loss, gh_dtype, depth, trees, first_tree, lr, l2, bufs.pred,
+                          sup, bufs.g, bufs.h, bufs.leaf, bufs.splits, bufs.leaf_values, bufs.child_totals, work,
+                          use_graph=use_graph)
+    return Model(bufs.splits[:trees], bufs.leaf_values[:trees], bufs.pred, depth, lr, sup)
 
 
 def grouped_from_rowmajor(bins_rm: np.ndarray) -> np.ndarray:
