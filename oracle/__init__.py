@@ -80,6 +80,10 @@ def lib():
                 "or_ts_full": (None, [u32p, f32p, i64, f64, f64, u32p, i64, f32p]),
                 "or_predict": (None, [u8p, i64, i32, i32p, i32p, f64p, i32, i32, f64, f64p]),
                 "or_ordered_sup_size": (i64, [i64]),
+                "or_combo_ids": (None, [i32p, i32, u32p, i64, u8p, i32, u32p]),
+                "or_fit_combos": (None, [u8p, i64, i32, i32, i32, i32p, i32, u32p, f32p, i32, i32, i32, f64, f64,
+                                         u32p, f64, f64, i32, i32, f64p, i32p, i32p, f64p, f64p, f64p, f64p, i32p,
+                                         i32p, f32p]),
                 "or_fit_ordered": (None, [u8p, i64, i32, i32, i32p, i32, f32p, i32, i32, i32, f64, f64, u32p, i32,
                                           f64p, i32p, i32p, f64p, f64p, f64p, f64p, f64p]),
             }
@@ -313,6 +317,52 @@ def fit_ordered(bins, F: int, n_borders, y, loss_name: str, depth: int, trees: i
                          _p(s2, _f64), _p(lv, _f64), _p(losses, _f64), _p(sup, _f64))
     return {"pred": pred, "split_f": sf, "split_k": sk, "score": ss, "second": s2,
             "leaf_values": lv, "losses": losses, "max_bins": max_bins, "sup": sup}
+
+
+def combo_ids(items, cat, bins):
+    """Ids of one feature combination for every row (Section 2 "Feature combinations").
+    items: [(kind, a, b)] in canonical order, kind 0 = categorical column a of cat [C][n],
+    kind 1 = the two-valued feature [bins[:, a] > b] of row-major bins [n][F_pad]."""
+    it = _c(np.asarray(items, np.int32).reshape(-1, 3), np.int32)
+    cat = _c(cat, np.uint32)
+    bins = _c(bins, np.uint8)
+    n = bins.shape[0]
+    ids = np.empty(n, np.uint32)
+    lib().or_combo_ids(_p(it, _i32), it.shape[0], _p(cat, _u32), n, _p(bins, _u8), bins.shape[1], _p(ids, _u32))
+    return ids
+
+
+def fit_combos(bins, F: int, F_float: int, n_borders, cat, y, loss_name: str, depth: int, trees: int, lr: float,
+               l2: float, perm, prior_value: float, a: float, max_borders: int, max_complexity: int = 4, pred=None):
+    """Classic boosting with greedy categorical feature combinations (Section 2). bins
+    [n][F_pad] holds the F_float float columns then one TS column per categorical of cat
+    [C][n]. Returns the dict of fit() plus, per (tree, level), the combination chosen
+    there (combo_items [T][D][max_complexity][3], kind -1 = unused; combo_nb [T][D];
+    combo_borders [T][D][max_borders]); a combination split has feature F + j."""
+    bins = _c(bins, np.uint8)
+    n, F_pad = bins.shape
+    nb = _c(n_borders, np.int32)
+    max_bins = int(nb.max()) + 1 if nb.size else 1
+    cat = _c(cat, np.uint32).reshape(-1, n) if np.size(cat) else np.zeros((0, n), np.uint32)
+    y = _c(y, np.float32)
+    perm = _c(perm, np.uint32)
+    pred = np.zeros(n, np.float64) if pred is None else _c(pred, np.float64).copy()
+    T, D = trees, depth
+    sf = np.empty((T, D), np.int32)
+    sk = np.empty((T, D), np.int32)
+    ss = np.empty((T, D), np.float64)
+    s2 = np.empty((T, D), np.float64)
+    lv = np.empty((T, 1 << D), np.float64)
+    losses = np.empty(T, np.float64)
+    items = np.empty((T, D, max_complexity, 3), np.int32)
+    cnb = np.empty((T, D), np.int32)
+    cbr = np.empty((T, D, max(max_borders, 1)), np.float32)
+    lib().or_fit_combos(_p(bins, _u8), n, F_pad, F, F_float, _p(nb, _i32), max_bins, _p(cat, _u32), _p(y, _f32),
+                        LOSS[loss_name], D, T, lr, l2, _p(perm, _u32), prior_value, a, max_borders, max_complexity,
+                        _p(pred, _f64), _p(sf, _i32), _p(sk, _i32), _p(ss, _f64), _p(s2, _f64), _p(lv, _f64),
+                        _p(losses, _f64), _p(items, _i32), _p(cnb, _i32), _p(cbr, _f32))
+    return {"pred": pred, "split_f": sf, "split_k": sk, "score": ss, "second": s2, "leaf_values": lv,
+            "losses": losses, "max_bins": max_bins, "combo_items": items, "combo_nb": cnb, "combo_borders": cbr}
 
 
 def ts_full(cat, y, prior_value: float, a: float, cat_new):

@@ -17,10 +17,10 @@
 //                    the paper names none)
 //   prior            Section 2, the prior P after Eq. 1
 //   ordered TS       Section 2, Eq. 1
-//   borders / bins   Section 4 "Dense numerical features" (fixed number of bins,
+//   borders / bins   Section 5 "Dense numerical features" (fixed number of bins,
 //                    at most 255 per feature, 8 bits per feature)
 //   gradients        Section 3, g = dLoss/da, Algorithm 1
-//   histogram        Section 4, hist[j][b] = sum over rows with f_j = b of g
+//   histogram        Section 5, hist[j][b] = sum over rows with f_j = b of g
 //   split score      Section 3 (enumerate splits, set leaf values, score the
 //                    tree) + Section 4 "Fast scorer" (one split per level)
 //   leaf index       Section 4 "Fast scorer": leaf = sum_i 2^i B(x, f(t,i))
@@ -31,6 +31,8 @@
 //                    trees of the value of the leaf its binary features select
 //   ordered boosting Section 3 "Fighting Gradient Bias", Algorithm 1 with the
 //                    log-scale supporting models M'_i and shared tree structures
+//   combinations     Section 2 "Feature combinations": greedy categorical feature
+//                    combinations, converted to numbers by Eq. 1 on the fly
 //
 // Parity pins for every function live in tests/test_oracle_*.py.
 
@@ -40,6 +42,7 @@
 #include <cstring>
 #include <unordered_map>
 #include <utility>
+#include <set>
 #include <vector>
 
 namespace {
@@ -548,6 +551,171 @@ void or_fit_ordered(const uint8_t* bins, int64_t n, int F_pad, int F, const int*
     }
   }
   if (sup_out) std::copy(sup.begin(), sup.end(), sup_out);
+}
+
+// ----------------------------------------------------- feature combinations
+// Section 2 "Feature combinations" with these readings where it is silent:
+//  - an item is a categorical column c (its ids) or a split (f, k) already in the tree,
+//    taken as a two-valued categorical feature [bin of f > k]; a combination is a set of
+//    items, kept sorted by (kind, a, b) with categorical columns first;
+//  - the value of a combination in a row is a SplitMix64 chain over its items in that
+//    order, h <- splitmix64_at(h, v) from h = 0 (v = the id, or the bit), folded to 32
+//    bits as h ^ (h >> 32); it is converted to a number by Eq. 1 along sigma (the same
+//    prior and a as single columns), and quantised with borders chosen on that column;
+//  - the first level of a tree takes no combinations. At level d >= 1 the items present
+//    in the tree are: for every split so far, the set {c} for a split on the TS column of
+//    categorical c, the set {(f, k)} for a split on a float feature, and the combination
+//    itself for a combination split. Candidates are every present set joined with every
+//    categorical column it lacks, up to max_complexity items, without repeats, in
+//    lexicographic order of their sorted items;
+//  - a candidate's best border is scored on the current leaves exactly as an ordinary
+//    feature; it replaces the ordinary split only with a strictly higher score (ties to the
+//    ordinary split, then to the first candidate, then the smallest border). A chosen
+//    combination is recorded as feature F + j (j-th combination of the tree) and is not
+//    scored again as an ordinary feature.
+namespace {
+struct ComboItem {
+  int kind, a, b;   // kind 0: categorical column a (b = 0); kind 1: [bin of feature a > b]
+  bool operator<(const ComboItem& o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (a != o.a) return a < o.a;
+    return b < o.b;
+  }
+  bool operator==(const ComboItem& o) const { return kind == o.kind && a == o.a && b == o.b; }
+};
+}  // namespace
+
+// Ids of a combination for every row. items: [m][3] (kind, a, b) in canonical order.
+void or_combo_ids(const int* items, int m, const uint32_t* cat, int64_t n, const uint8_t* bins, int F_pad,
+                  uint32_t* ids) {
+  for (int64_t r = 0; r < n; ++r) {
+    uint64_t h = 0;
+    for (int i = 0; i < m; ++i) {
+      const int kind = items[3 * i], a = items[3 * i + 1], b = items[3 * i + 2];
+      const uint64_t v = kind == 0 ? cat[static_cast<int64_t>(a) * n + r] : (bins[r * F_pad + a] > b ? 1u : 0u);
+      h = splitmix64_at(h, v);
+    }
+    ids[r] = static_cast<uint32_t>(h ^ (h >> 32));
+  }
+}
+
+void or_fit_combos(const uint8_t* bins, int64_t n, int F_pad, int F, int F_float, const int* n_borders, int max_bins,
+                   const uint32_t* cat, const float* y, int loss, int depth, int trees, double lr, double l2,
+                   const uint32_t* perm, double prior, double a, int max_borders, int max_complexity, double* pred,
+                   int* split_f, int* split_k, double* split_score, double* split_second, double* leaf_values,
+                   double* losses, int* combo_items, int* combo_nb, float* combo_borders) {
+  const int L = 1 << depth;
+  const int C = F - F_float;
+  const int cmb = max_borders + 1;
+  std::vector<double> g(n), h(n);
+  std::vector<uint16_t> leaf(n);
+  std::vector<double> hist(static_cast<size_t>(L / 2 > 0 ? L / 2 : 1) * F * max_bins * 2);
+  std::vector<double> scores(static_cast<size_t>(F) * (max_bins > 1 ? max_bins - 1 : 1));
+  std::vector<double> chist(static_cast<size_t>(L / 2 > 0 ? L / 2 : 1) * cmb * 2), cscores(cmb);
+  std::vector<double> tot(2 * L), v(L);
+  std::vector<uint32_t> ids(n);
+  std::vector<float> ts(n), cb(max_borders > 0 ? max_borders : 1), best_b(cb.size());
+  std::vector<uint8_t> colbins(static_cast<size_t>(n) * 32, 0), best_bins(static_cast<size_t>(n) * 32, 0);
+  std::vector<int> flat;
+  for (int t = 0; t < trees; ++t) {
+    or_gradients(loss, y, pred, n, 0, g.data(), h.data());
+    std::fill(leaf.begin(), leaf.end(), 0);
+    std::vector<std::vector<ComboItem>> present;
+    int n_combo = 0;
+    for (int d = 0; d < depth; ++d) {
+      const int64_t rec = static_cast<int64_t>(t) * depth + d;
+      for (int i = 0; i < 3 * max_complexity; ++i) combo_items[rec * 3 * max_complexity + i] = -1;
+      combo_nb[rec] = 0;
+      for (int i = 0; i < max_borders; ++i) combo_borders[rec * max_borders + i] = 0.0f;
+      const int nl = 1 << d;
+      int bf, bk;
+      double bs, ss;
+      or_histogram(bins, n, F_pad, F, g.data(), h.data(), leaf.data(), nl, max_bins, hist.data());
+      or_split_scores(hist.data(), nl, F, n_borders, max_bins, l2, scores.data(), &bf, &bk, &bs, &ss);
+      double top1 = -INFINITY, top2 = -INFINITY;
+      auto push = [&](double sc) {
+        if (sc > top1) {
+          top2 = top1;
+          top1 = sc;
+        } else if (sc > top2) {
+          top2 = sc;
+        }
+      };
+      if (bf >= 0) {
+        push(bs);
+        push(ss);
+      }
+      // candidates
+      std::set<std::vector<ComboItem>> cands;
+      if (d >= 1)
+        for (const auto& p : present)
+          for (int c = 0; c < C; ++c) {
+            const ComboItem it{0, c, 0};
+            if (std::find(p.begin(), p.end(), it) != p.end() || static_cast<int>(p.size()) + 1 > max_complexity)
+              continue;
+            std::vector<ComboItem> q = p;
+            q.push_back(it);
+            std::sort(q.begin(), q.end());
+            cands.insert(q);
+          }
+      const std::vector<ComboItem>* win = nullptr;
+      int wk = -1, wnb = 0;
+      double ws = -INFINITY;
+      for (const auto& q : cands) {
+        flat.clear();
+        for (const auto& it : q) flat.insert(flat.end(), {it.kind, it.a, it.b});
+        or_combo_ids(flat.data(), static_cast<int>(q.size()), cat, n, bins, F_pad, ids.data());
+        or_ordered_ts(ids.data(), y, n, perm, prior, a, ts.data(), nullptr, nullptr);
+        const int nb = or_select_borders(ts.data(), n, max_borders, cb.data());
+        if (nb <= 0) continue;
+        or_quantize(ts.data(), n, 1, cb.data(), &nb, max_borders, colbins.data(), 32, 0, nullptr, 0);
+        int cf, ck;
+        double cs, css;
+        or_histogram(colbins.data(), n, 32, 1, g.data(), h.data(), leaf.data(), nl, cmb, chist.data());
+        or_split_scores(chist.data(), nl, 1, &nb, cmb, l2, cscores.data(), &cf, &ck, &cs, &css);
+        if (cf < 0) continue;
+        push(cs);
+        push(css);
+        if (!win || cs > ws) {
+          win = &q;
+          wk = ck;
+          ws = cs;
+          wnb = nb;
+          best_bins.swap(colbins);
+          std::copy(cb.begin(), cb.end(), best_b.begin());
+        }
+      }
+      split_score[rec] = top1;
+      split_second[rec] = top2;
+      if (win && (bf < 0 || ws > bs)) {
+        split_f[rec] = F + n_combo;
+        split_k[rec] = wk;
+        for (size_t i = 0; i < win->size(); ++i) {
+          combo_items[(rec * max_complexity + i) * 3] = (*win)[i].kind;
+          combo_items[(rec * max_complexity + i) * 3 + 1] = (*win)[i].a;
+          combo_items[(rec * max_complexity + i) * 3 + 2] = (*win)[i].b;
+        }
+        combo_nb[rec] = wnb;
+        for (int i = 0; i < wnb; ++i) combo_borders[rec * max_borders + i] = best_b[i];
+        or_update_leaf(best_bins.data(), n, 32, 0, wk, d, leaf.data());
+        if (std::find(present.begin(), present.end(), *win) == present.end()) present.push_back(*win);
+        ++n_combo;
+      } else {
+        split_f[rec] = bf;
+        split_k[rec] = bk;
+        or_update_leaf(bins, n, F_pad, bf, bk, d, leaf.data());
+        if (bf >= 0) {
+          const std::vector<ComboItem> p{bf < F_float ? ComboItem{1, bf, bk} : ComboItem{0, bf - F_float, 0}};
+          if (std::find(present.begin(), present.end(), p) == present.end()) present.push_back(p);
+        }
+      }
+    }
+    or_leaf_totals(g.data(), h.data(), leaf.data(), n, L, tot.data());
+    or_leaf_values(tot.data(), L, l2, v.data());
+    for (int l = 0; l < L; ++l) leaf_values[static_cast<int64_t>(t) * L + l] = v[l];
+    or_apply_leaf_values(leaf.data(), n, v.data(), lr, pred);
+    losses[t] = or_loss(loss, y, pred, n);
+  }
 }
 
 }  // extern "C"
