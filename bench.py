@@ -56,6 +56,12 @@ def parse_args():
     p.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-storage comparison step")
     p.add_argument("--scorer-trees", type=int, default=8000,
                    help="trees of the model-prediction measurement (0 = skip)")
+    p.add_argument("--ordered-trees", type=int, default=200,
+                   help="trees of the ordered-boosting comparison (0 skips it)")
+    p.add_argument("--ordered-s", type=int, default=4, help="permutations of the ordered-boosting comparison")
+    p.add_argument("--combo-trees", type=int, default=10,
+                   help="trees of the feature-combination comparison (0 skips it)")
+    p.add_argument("--combo-borders", type=int, default=15, help="borders of a combination's column")
     p.add_argument("--paper-setting-trees", type=int, default=200,
                    help="trees of the 4e5 x 2000, 15-border, depth-6 measurement (0 = skip)")
     return p.parse_args()
@@ -304,7 +310,7 @@ def scorer_bench(ctx, dev, trees, rows=100_000, F=2000, depth=6, reps=5):
 
 
 def paper_setting_bench(ctx, dev, trees, n=400_000, F=2000, borders=15, depth=6):
-    """Tree construction on the setting of the paper's own GPU timing (Section 5): an
+    """Tree construction on the setting of the paper's own GPU timing (Section 6): an
     Epsilon-shaped dense problem (4e5 x 2000 N(0,1), y ~ Bernoulli(sigmoid(w.x)), w ~
     N(0, 1/2000)), 15 borders, depth 6, classic boosting, no subsampling; histogram
     tiles from the autotuner. Mean construction time per tree with graph replay."""
@@ -339,6 +345,89 @@ def paper_setting_bench(ctx, dev, trees, n=400_000, F=2000, borders=15, depth=6)
                            "rows_per_item": tiles["rows_per_item"]},
             "paper_context": "CatBoost GPU, Epsilon, 15 bins, depth 6, classic scheme: 17.9 ms/tree on "
                              "an NVIDIA P100 (not the same data or hardware)"}
+
+
+def ordered_bench(ctx, dev, x, cat, y, w, trees, s, tiles):
+    """Ordered boosting (Section 3, Algorithm 1 with the log-scale supporting models) on
+    logloss_1m with s permutations, against the classic scheme on the same data, both
+    with graph replay: mean time per tree (after the one-off preprocessing) and the final
+    training loss."""
+    import torch
+    from paper_1810_11363_gb300 import cbg, train
+    stream = torch.cuda.current_stream(dev)
+    op = train.preprocess_ordered(ctx, x, cat, y, "binary", w.max_borders, s, a=w.a, seed=w.seed)
+    out = {"workload": f"logloss_1m (10^6 x 110, 255 bins), depth {w.depth}, {trees} trees, lr {w.lr}, L2 {w.l2}, "
+                       f"s = {s} permutations (own TS per permutation)", "s": s, "trees": trees}
+    for name in ("ordered", "classic"):
+        bufs = train.alloc_fit(op.base, w.depth, trees, tiles=tiles)
+
+        def run(T):
+            bufs.pred.zero_()
+            if name == "ordered":
+                return train.fit_ordered(ctx, op, y, w.loss, w.depth, T, w.lr, w.l2, tiles=tiles, bufs=bufs,
+                                         use_graph=True)
+            return train.fit(ctx, op.base, y, w.loss, w.depth, T, w.lr, w.l2, bufs=bufs, use_graph=True)
+        run(min(trees, 2 * s))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(trees)
+        e1.record(stream)
+        e1.synchronize()
+        cbg.cbg_sync(ctx)
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms_per_tree": ms / trees, "trees_per_s": trees / (ms / 1e3),
+                     "final_loss": training_loss(w.loss, y, bufs.pred)}
+        del bufs
+    out["ordered_time_over_classic"] = out["ordered"]["ms_per_tree"] / out["classic"]["ms_per_tree"]
+    out["paper_context"] = ("the paper's GPU implementation: the bias-fighting (ordered) scheme is 2-3x slower "
+                            "than classic boosting by design (Section 6, GPU training performance)")
+    del op
+    torch.cuda.empty_cache()
+    return out
+
+
+def combos_bench(ctx, dev, x, cat, y, w, trees, max_borders, max_complexity, tiles):
+    """Classic boosting with greedy feature combinations (Section 2) on logloss_1m against
+    plain classic boosting on the same data: mean time per tree (host-driven levels, one
+    synchronisation per level), the combinations taken, and the final training loss."""
+    import torch
+    from paper_1810_11363_gb300 import cbg, train
+    stream = torch.cuda.current_stream(dev)
+    prep = train.preprocess(ctx, x, cat, y, "binary", w.max_borders, a=w.a, seed=w.seed)
+    out = {"workload": f"logloss_1m (10^6 x 110, 255 bins), depth {w.depth}, {trees} trees, lr {w.lr}, L2 {w.l2}; "
+                       f"combinations of up to {max_complexity} items, {max_borders} borders each",
+           "trees": trees}
+    train.fit_combos(ctx, prep, cat, y, "binary", w.loss, w.depth, 1, w.lr, w.l2, max_borders, max_complexity,
+                     a=w.a, tiles=tiles)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = train.fit_combos(ctx, prep, cat, y, "binary", w.loss, w.depth, trees, w.lr, w.l2, max_borders,
+                           max_complexity, a=w.a, tiles=tiles)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    sp = res.model.host_splits()
+    out["combinations"] = {"ms_per_tree": ms / trees, "final_loss": training_loss(w.loss, y, res.model.pred),
+                           "combination_splits": int((sp["feature"] >= prep.F).sum()),
+                           "splits": int(sp["feature"].size)}
+    bufs = train.alloc_fit(prep, w.depth, trees, tiles=tiles)
+    train.fit(ctx, prep, y, w.loss, w.depth, 2, w.lr, w.l2, bufs=bufs, use_graph=True)
+    bufs.pred.zero_()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    train.fit(ctx, prep, y, w.loss, w.depth, trees, w.lr, w.l2, bufs=bufs, use_graph=True)
+    e1.record(stream)
+    e1.synchronize()
+    cbg.cbg_sync(ctx)
+    ms = e0.elapsed_time(e1)
+    out["classic"] = {"ms_per_tree": ms / trees, "final_loss": training_loss(w.loss, y, bufs.pred)}
+    out["paper_context"] = ("the paper calls statistics on feature combinations the slowest and most memory "
+                            "consuming part of its GPU implementation (Section 5, Categorical features)")
+    del prep, bufs, res
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ arms
@@ -525,6 +614,12 @@ def run_ours(args):
     paper_setting = None
     if args.paper_setting_trees > 0 and rank == 0:
         paper_setting = paper_setting_bench(ctx, dev, args.paper_setting_trees)
+    ordered = None
+    if args.ordered_trees > 0 and rank == 0:
+        ordered = ordered_bench(ctx, dev, x, cat, y, w, args.ordered_trees, args.ordered_s, tiles)
+    combos = None
+    if args.combo_trees > 0 and rank == 0:
+        combos = combos_bench(ctx, dev, x, cat, y, w, args.combo_trees, args.combo_borders, 4, tiles)
 
     # kernels of ours per step: the preprocessing launches of logloss_1m (359, counted in
     # its ncu launch list), the first gradients, and per tree: tree_begin, 5 kernels per
@@ -552,6 +647,7 @@ def run_ours(args):
                 "row_feature_bins_per_s": rfb, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "forms": forms, "batched_vs_plain": batched, "scorer": scorer, "paper_setting": paper_setting,
+                "ordered_boosting": ordered, "feature_combinations": combos,
                 "breakdown": {"step_ms": step_ms}}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -5,9 +5,9 @@
  * (Dorogush, Ershov, Gulin; arXiv 1810.11363).
  *
  * The path: ordered target statistics for categorical features (Section 2,
- * Eq. 1); quantisation of every feature into uint8 bins (Section 4, "Dense
+ * Eq. 1); quantisation of every feature into uint8 bins (Section 5, "Dense
  * numerical features"); per-(leaf, feature, bin) gradient/hessian histograms
- * and L2-regularised split search for oblivious trees (Sections 3 and 4); leaf
+ * and L2-regularised split search for oblivious trees (Sections 3 and 5); leaf
  * values, per-row leaf index and the prediction update (Section 3, Section 4
  * "Fast scorer").
  *
@@ -143,7 +143,7 @@ cbg_status cbg_ordered_ts(cbg_ctx* ctx, const uint32_t* cat, const float* y, int
                           const uint32_t* perm, double prior, double a, int label_kind, float* ts,
                           uint32_t* cnt_before, void* sum_before);
 
-/* Quantile borders per feature (Section 4: a fixed number of bins per feature,
+/* Quantile borders per feature (Section 5: a fixed number of bins per feature,
  * at most 255): v = column f sorted ascending; candidate k = 1..max_borders is
  * v[floor(k*n/(max_borders+1))]; the strictly increasing candidates below max(v)
  * are kept (a -0.0 border is stored as +0.0). x: device float [F][n];
@@ -153,7 +153,7 @@ cbg_status cbg_ordered_ts(cbg_ctx* ctx, const uint32_t* cat, const float* y, int
 cbg_status cbg_select_borders(cbg_ctx* ctx, const float* x, int64_t n, int32_t F,
                               int32_t max_borders, float* borders, int32_t* n_borders);
 
-/* Quantisation (Section 4): bin = number of borders strictly below x, written
+/* Quantisation (Section 5): bin = number of borders strictly below x, written
  * as uint8 to feature f_offset + f of row r of bins (grouped layout, F_pad a
  * multiple of 32) and, if bins_t is not NULL, to bins_t[f_offset + f][r]
  * (column-major, row stride n).
@@ -202,6 +202,19 @@ typedef struct cbg_level_args {
   double* child_totals;        /* device [2^(d+1)][2]: (G, H) of every child */
   double* hist_out;            /* optional device [2^d][F][max_bins][2] FP64 */
   int32_t last_level;          /* nonzero: skip re-partitioning the rows     */
+  /* Optional challenger: a split on a column outside bins (a feature combination,
+   * Section 2). When challenger (device cbg_split) is not NULL and its feature is
+   * >= 0, it replaces the best split of bins if its score is strictly higher (or if
+   * bins has no candidate). Its feature must be >= F (it names the column, e.g. F + j
+   * for the j-th combination of the tree); its border k sends rows with
+   * challenger_bins[row] > k to the "1" side (challenger_bins: device uint8 [n], row
+   * order), and its FP64 histogram over the 2^d leaves of the level,
+   * challenger_hist (device double [2^d][challenger_max_bins][2]), gives the child
+   * totals. Ignored when force_feature >= 0. */
+  const cbg_split* challenger;
+  const uint8_t* challenger_bins;
+  const double* challenger_hist;
+  int32_t challenger_max_bins;
 } cbg_level_args;
 
 /* One level d (Sections 3-4): FP64 histograms hist[l][f][b] = sum of (g, h)
@@ -457,8 +470,9 @@ cbg_status cbg_autotune_tiles(cbg_ctx* ctx, const cbg_autotune_args* args, cbg_t
  * computed along sigma_q, quantised with one set of borders. Every permutation's
  * data is kept in its own position order (cbg_permute_rows).
  *
- * Supporting values of one permutation: cbg_ordered_sup_len(n) floats,
- * 2^(I+1) + n with I = floor(log2(n-1)) (I = 0 for n = 1). Model M'_i,
+ * Supporting values of one permutation: cbg_ordered_sup_len(n) floats, the
+ * 2^(I+1) + n used ones (I = floor(log2(n-1)), I = 0 for n = 1) rounded up to a
+ * multiple of 64; sup is [s][cbg_ordered_sup_len(n)]. Model M'_i,
  * i = 0..I, is trained on positions p < 2^i and holds positions
  * j < min(2^(i+1), n), position j at element 2^(i+1) + j (the last model at
  * 2^(I+1) + j); elements 0 and 1 are unused. A fresh run starts from zeros. */
@@ -524,6 +538,81 @@ typedef struct cbg_ordered_args {
  *     at every position it holds.
  * Gradients are computed in FP32. */
 cbg_status cbg_boost_ordered(cbg_ctx* ctx, const cbg_ordered_args* args);
+
+/* ---------------------------------------------- feature combinations ---- */
+/* Greedy categorical feature combinations (Section 2 "Feature combinations";
+ * Section 5 "Categorical features").
+ *
+ * An item is a categorical column or a split already taken in the tree; a
+ * combination is a set of items. kind 0: categorical column a (its ids, b = 0);
+ * kind 1: the two-valued column [bin of feature a > b]. Items are kept sorted by
+ * (kind, a, b). A combination's value in a row is the SplitMix64 chain
+ * h <- splitmix64(seed = h, index = v) over its items in that order from h = 0
+ * (v = the id, or the bit), folded to 32 bits as h ^ (h >> 32); it is converted
+ * to a number by Eq. 1 along perm (prior and a as for single columns) and
+ * quantised with max_borders borders chosen on that column (the border rule of
+ * cbg_select_borders). */
+typedef struct cbg_combo_item {
+  int32_t kind;   /* 0 categorical column, 1 split; -1 marks an unused slot */
+  int32_t a;
+  int32_t b;
+} cbg_combo_item;
+
+/* Bytes of the device work buffer of cbg_boost_combos. */
+cbg_status cbg_combo_work_bytes(int64_t n, int32_t C, int32_t depth, int32_t max_borders, int32_t max_complexity,
+                                size_t* bytes);
+
+/* Arguments of cbg_boost_combos. Device memory unless marked host. */
+typedef struct cbg_combo_args {
+  const cbg_tree_shape* shape; /* host; shape->F = F_float + C             */
+  void* state;                 /* tree-state scratch (cbg_tree_state_bytes) */
+  size_t state_bytes;
+  const uint8_t* bins;         /* grouped: F_float floats, then one TS column per categorical */
+  const uint8_t* bins_t;       /* [F][n], required (splits joined as items)   */
+  const int32_t* n_borders;    /* [F]                                         */
+  const uint32_t* cat;         /* [C][n] raw category ids                     */
+  int32_t C;
+  int32_t F_float;
+  const uint32_t* perm;        /* [n] sigma, position -> row (Eq. 1)          */
+  const float* y;              /* [n]                                         */
+  int32_t label_kind;          /* CBG_LABEL_BINARY or CBG_LABEL_REAL          */
+  int32_t max_borders;         /* borders of a combination's column, 1..254   */
+  double prior;
+  double a;                    /* prior weight of Eq. 1                       */
+  int32_t max_complexity;      /* items per combination, 1..16 (1: none)      */
+  int32_t loss;
+  int32_t gh_dtype;
+  int32_t depth;
+  int32_t trees;
+  int32_t reserved;
+  double lr;
+  double l2;
+  float* pred;                 /* [n] in/out                                  */
+  void* g;                     /* [n] scratch of gh_dtype                     */
+  void* h;
+  uint16_t* leaf;              /* [n] scratch                                 */
+  cbg_split* splits;           /* [trees][depth] out; a combination is F + j  */
+  double* leaf_values;         /* [trees][2^depth] out                        */
+  double* child_totals;        /* [2^depth][2] scratch                        */
+  void* work;                  /* cbg_combo_work_bytes(...) bytes             */
+  size_t work_bytes;
+  cbg_combo_item* combo_items; /* host [trees][depth][max_complexity] out: the combination of a
+                                  combination split, kind -1 elsewhere */
+  int32_t* combo_nb;           /* host [trees][depth] out: its border count   */
+  float* combo_borders;        /* host [trees][depth][max_borders] out: its borders */
+} cbg_combo_args;
+
+/* Classic boosting (as cbg_boost) with greedy feature combinations. The first
+ * level of a tree takes no combination. At level d >= 1 the candidates are
+ * every item set present in the tree -- {c} for a split on categorical c's TS
+ * column, {(f, k)} for a split on float feature f, the combination itself for a
+ * combination split -- joined with every categorical column it lacks, up to
+ * max_complexity items, without repeats, in lexicographic order of their sorted
+ * items. Every candidate's best border is scored on the current leaves like an
+ * ordinary feature (Section 3 score); the best (ties to the first candidate,
+ * then the smallest border) replaces the best ordinary split only with a
+ * strictly higher score. Synchronises the host once per level. */
+cbg_status cbg_boost_combos(cbg_ctx* ctx, const cbg_combo_args* args);
 
 #ifdef __cplusplus
 }

@@ -61,7 +61,8 @@ class LevelArgs(C.Structure):
                 ("bins", c_vp), ("bins_t", c_vp), ("n_borders", c_vp), ("g", c_vp), ("h", c_vp),
                 ("gh_dtype", c_i32), ("depth", c_i32), ("l2", c_f64), ("force_feature", c_i32),
                 ("force_border", c_i32), ("leaf", c_vp), ("splits", c_vp), ("child_totals", c_vp),
-                ("hist_out", c_vp), ("last_level", c_i32)]
+                ("hist_out", c_vp), ("last_level", c_i32), ("challenger", c_vp), ("challenger_bins", c_vp),
+                ("challenger_hist", c_vp), ("challenger_max_bins", c_i32)]
 
 
 class ApplyArgs(C.Structure):
@@ -93,6 +94,21 @@ class OrderedArgs(C.Structure):
                 ("trees", c_i32), ("first_tree", c_i32), ("lr", c_f64), ("l2", c_f64), ("pred", c_vp),
                 ("sup", c_vp), ("g", c_vp), ("h", c_vp), ("leaf", c_vp), ("splits", c_vp), ("leaf_values", c_vp),
                 ("child_totals", c_vp), ("work", c_vp), ("work_bytes", C.c_size_t), ("use_graph", c_i32)]
+
+
+class ComboItem(C.Structure):
+    _fields_ = [("kind", c_i32), ("a", c_i32), ("b", c_i32)]
+
+
+class ComboArgs(C.Structure):
+    _fields_ = [("shape", C.POINTER(TreeShape)), ("state", c_vp), ("state_bytes", C.c_size_t), ("bins", c_vp),
+                ("bins_t", c_vp), ("n_borders", c_vp), ("cat", c_vp), ("C", c_i32), ("F_float", c_i32),
+                ("perm", c_vp), ("y", c_vp), ("label_kind", c_i32), ("max_borders", c_i32), ("prior", c_f64),
+                ("a", c_f64), ("max_complexity", c_i32), ("loss", c_i32), ("gh_dtype", c_i32), ("depth", c_i32),
+                ("trees", c_i32), ("reserved", c_i32), ("lr", c_f64), ("l2", c_f64), ("pred", c_vp), ("g", c_vp),
+                ("h", c_vp), ("leaf", c_vp), ("splits", c_vp), ("leaf_values", c_vp), ("child_totals", c_vp),
+                ("work", c_vp), ("work_bytes", C.c_size_t), ("combo_items", c_vp), ("combo_nb", c_vp),
+                ("combo_borders", c_vp)]
 
 
 # name -> (restype, argtypes); every entry point declared in include/cbg.h
@@ -129,6 +145,8 @@ SIGNATURES = {
     "cbg_ordered_work_bytes": (c_i32, [c_i64, c_i32, c_i32, C.POINTER(C.c_size_t)]),
     "cbg_permute_rows": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "cbg_boost_ordered": (c_i32, [c_vp, C.POINTER(OrderedArgs)]),
+    "cbg_combo_work_bytes": (c_i32, [c_i64, c_i32, c_i32, c_i32, c_i32, C.POINTER(C.c_size_t)]),
+    "cbg_boost_combos": (c_i32, [c_vp, C.POINTER(ComboArgs)]),
 }
 
 _lock = threading.Lock()
@@ -391,3 +409,27 @@ def cbg_boost_ordered(ctx: Context, shape: TreeShape, state, s: int, bins_pos, b
                     _p(splits), _p(leaf_values), _p(child_totals), _p(work), work.numel() * work.element_size(),
                     int(use_graph))
     ctx.check(ctx.lib.cbg_boost_ordered(ctx.h, C.byref(a)), "cbg_boost_ordered")
+
+
+def cbg_combo_work_bytes(n: int, C_: int, depth: int, max_borders: int, max_complexity: int) -> int:
+    out = C.c_size_t()
+    st = load().cbg_combo_work_bytes(n, C_, depth, max_borders, max_complexity, C.byref(out))
+    if st != CBG_OK:
+        raise CbgError(st, "cbg_combo_work_bytes: invalid arguments")
+    return int(out.value)
+
+
+def cbg_boost_combos(ctx: Context, shape: TreeShape, state, bins, bins_t, n_borders, cat, C_: int, F_float: int,
+                     perm, y, label_kind: str, max_borders: int, prior: float, a: float, max_complexity: int,
+                     loss: str, gh_dtype: str, depth: int, trees: int, lr: float, l2: float, pred, g, h, leaf,
+                     splits, leaf_values, child_totals, work, combo_items, combo_nb, combo_borders):
+    """combo_items (numpy int32 [trees][depth][max_complexity][3]), combo_nb (int32
+    [trees][depth]) and combo_borders (float32 [trees][depth][max_borders]) are host
+    outputs."""
+    args = ComboArgs(C.pointer(shape), _p(state), state.numel() * state.element_size(), _p(bins), _p(bins_t),
+                     _p(n_borders), _p(cat), C_, F_float, _p(perm), _p(y), LABEL[label_kind], max_borders, prior, a,
+                     max_complexity, LOSS[loss], DTYPE[gh_dtype], depth, trees, 0, lr, l2, _p(pred), _p(g), _p(h),
+                     _p(leaf), _p(splits), _p(leaf_values), _p(child_totals), _p(work),
+                     work.numel() * work.element_size(), combo_items.ctypes.data, combo_nb.ctypes.data,
+                     combo_borders.ctypes.data)
+    ctx.check(ctx.lib.cbg_boost_combos(ctx.h, C.byref(args)), "cbg_boost_combos")

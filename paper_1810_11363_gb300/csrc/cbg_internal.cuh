@@ -125,6 +125,14 @@ __device__ __forceinline__ void store_gh(__nv_bfloat16* p, int64_t i, float v) {
   p[i] = __float2bfloat16_rn(v);
 }
 
+// SplitMix64 (Steele, Lea & Flood 2014): output i of the generator seeded with `seed`.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
 // First and second derivative of the loss in the model value a (FP32): RMSE a - y and 1;
 // Logloss sigmoid(a) - y and sigmoid(a) (1 - sigmoid(a)).
 __device__ __forceinline__ void loss_grad(int loss, float a, float y, float* g, float* h) {

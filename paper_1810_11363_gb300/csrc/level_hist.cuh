@@ -74,7 +74,7 @@ __device__ __forceinline__ void red_add(uint32_t addr, float v) {
 // memory and writes it to the unit's FP32 partial, so one partial is written per cluster
 // and unit. Lane (j, c): row j of 16, 16-feature chunk c of the group; iteration l
 // updates feature 16c + (l + j) % 16, so the 32 lanes hit 32 different features and banks
-// (the rotation of the paper's Section 4 example, applied to 16-byte loads). Chunks that
+// (the rotation of the paper's Section 5 example, applied to 16-byte loads). Chunks that
 // hold only padding features are skipped.
 // MODE 0: G and H in two planes [2][NB][32], each updated with red.shared.add.f32.
 // MODE 1: (G, H) interleaved as float2 [NB][32], updated with one 64-bit compare-and-swap
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(512, 3) level_hist_batched_kernel(const HistPr
   }
 }
 
-// Warp-private histogram, no atomics (the paper's Section 4 scheme: per-warp partial
+// Warp-private histogram, no atomics (the paper's Section 5 scheme: per-warp partial
 // histograms of a few features, updated without atomic operations; here 16 features and
 // two rows per warp instruction). A warp owns half of a 32-feature group: a (G, H) float2
 // histogram [max_bins][16] in shared memory that no other warp touches. Lane (r, f)
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
 }
 
 // ------------------------------------------- lane-per-feature warp histograms
-// The warp-private scheme of the paper's Section 4 with one feature per lane: a warp owns
+// The warp-private scheme of the paper's Section 5 with one feature per lane: a warp owns
 // the (G, H) float2 histogram [max_bins][32] of one 32-feature group, and lane f updates
 // column f for every row, so the 32 addresses of an update are always distinct and no
 // atomics are needed. Rows come in blocks of 32 staged in shared memory: lane i fetches

@@ -11,10 +11,10 @@
 // model of every permutation takes the same structure and Newton leaf values from its own
 // first 2^i positions.
 //
-// Supporting values of one permutation (FP32, `sup_len(n) = 2^(I+1) + n` floats,
-// I = floor(log2(n-1)), I = 0 for n = 1): model i occupies [2^(i+1), 2^(i+2)) -- the last
-// model [2^(I+1), 2^(I+1) + n) -- and holds position j at 2^(i+1) + j. Elements 0 and 1 are
-// unused. With this layout a model's range starts at a power of two, so a block of 2^b
+// Supporting values of one permutation (FP32, `sup_len(n) = 2^(I+1) + n` floats used,
+// I = floor(log2(n-1)), I = 0 for n = 1, rows of the [s] array padded to a multiple of 64
+// floats): model i occupies [2^(i+1), 2^(i+2)) -- the last model [2^(I+1), 2^(I+1) + n) --
+// and holds position j at 2^(i+1) + j. Elements 0 and 1 are unused. With this layout a model's range starts at a power of two, so a block of 2^b
 // consecutive elements past the first block lies inside one model, and model i's training
 // positions p < 2^i are the first half of its range.
 #include <algorithm>
@@ -42,6 +42,8 @@ __host__ __device__ __forceinline__ int ilog2(int64_t k) {   // floor(log2 k), k
 
 int top_model(int64_t n) { return n > 1 ? ilog2(n - 1) : 0; }
 int64_t sup_len_of(int64_t n) { return (int64_t(2) << top_model(n)) + n; }
+int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
+int64_t sup_stride_of(int64_t n) { return pad64(sup_len_of(n)); }
 
 // ------------------------------------------------------------- row permutation
 // out[g][k][0..31] = in[g][sigma[k]][0..31] for the grouped layout, two 16-byte halves
@@ -108,64 +110,163 @@ __device__ __forceinline__ void load_splits(const cbg_split* __restrict__ sp, in
   }
 }
 
+// Per-leaf (G, H) accumulation used by the totals kernels: every warp adds into its own
+// FP32 copy in shared memory (red.shared.add.f32, contention only within the warp), and
+// the block sums the warps' copies in FP64 before one FP64 atomic per (leaf, statistic)
+// into the global totals. A warp's copy sums at most OB_ITEMS / 8 items.
+constexpr int OB_WARPS = OB_THREADS / 32;
+constexpr int OB_UNROLL = static_cast<int>(OB_ITEMS / OB_THREADS);   // items per thread and block
+
+__device__ __forceinline__ void zero_acc(float* s_acc, int L) {
+  for (int x = threadIdx.x; x < OB_WARPS * 2 * L; x += blockDim.x) s_acc[x] = 0.0f;
+}
+
+__device__ __forceinline__ void flush_acc(const float* s_acc, int L, double* __restrict__ out) {
+  for (int x = threadIdx.x; x < 2 * L; x += blockDim.x) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < OB_WARPS; ++w) v += static_cast<double>(s_acc[w * 2 * L + x]);
+    if (v != 0.0) atomicAdd(&out[x], v);
+  }
+}
+
+// Leaves of the 4 consecutive rows x0..x0+3 from [F][n] bins with one 32-bit load per
+// split (x0 % 4 == 0, n % 4 == 0 and a 4-byte aligned base, so every load is aligned).
+__device__ __forceinline__ void leaf4(const uint8_t* __restrict__ bins_t, int64_t n, int64_t x0, const int* sf,
+                                      const int* sk, int depth, int* l) {
+  l[0] = l[1] = l[2] = l[3] = 0;
+  for (int d = 0; d < depth; ++d) {
+    const int f = sf[d];
+    if (f < 0) continue;
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(bins_t + static_cast<int64_t>(f) * n + x0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (static_cast<int>((w >> (8 * j)) & 0xffu) > sk[d]) l[j] += 1 << d;
+  }
+}
+
 // --------------------------------------------------- final model: leaf totals
-// FP64 (G, H) per leaf of the plain gradients at pred, leaves from the splits on the
-// final model's row-order bins; leaf indices are written for the update that follows.
+// (G, H) per leaf of the plain gradients at pred, leaves from the splits on the final
+// model's row-order bins; leaf indices are written for the update that follows. Each
+// block takes OB_ITEMS consecutive rows per round, OB_UNROLL per thread: with VEC, two
+// runs of 4 consecutive rows read with 32-bit (bins) and 128-bit (pred, y) loads.
+template <bool VEC>
 __global__ void rows_totals_kernel(const uint8_t* __restrict__ bins_t, const uint8_t* __restrict__ bins, int64_t n,
                                    const cbg_split* __restrict__ sp, int depth, const float* __restrict__ y,
                                    const float* __restrict__ pred, int loss, double* __restrict__ tot,
                                    uint16_t* __restrict__ leaf_out) {
-  extern __shared__ double s_tot[];
+  extern __shared__ float s_acc[];
   __shared__ int sf[OB_MAX_DEPTH], sk[OB_MAX_DEPTH];
   const int L = 1 << depth;
-  for (int i = threadIdx.x; i < 2 * L; i += blockDim.x) s_tot[i] = 0.0;
+  zero_acc(s_acc, L);
   load_splits(sp, depth, sf, sk);
   __syncthreads();
-  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
-       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int l = leaf_of(bins_t, bins, n, r, sf, sk, depth);
-    leaf_out[r] = static_cast<uint16_t>(l);
-    float g, h;
-    cbgd::loss_grad(loss, pred[r], y[r], &g, &h);
-    atomicAdd(&s_tot[2 * l], static_cast<double>(g));
-    atomicAdd(&s_tot[2 * l + 1], static_cast<double>(h));
+  float* acc = s_acc + (threadIdx.x >> 5) * 2 * L;
+  for (int64_t r0 = blockIdx.x * OB_ITEMS; r0 < n; r0 += static_cast<int64_t>(gridDim.x) * OB_ITEMS) {
+    int l[OB_UNROLL];
+    float a[OB_UNROLL], yv[OB_UNROLL];
+    if (VEC) {
+#pragma unroll
+      for (int c = 0; c < OB_UNROLL / 4; ++c) {
+        const int64_t x0 = r0 + 4 * threadIdx.x + c * 4 * OB_THREADS;
+        if (x0 < n) {
+          leaf4(bins_t, n, x0, sf, sk, depth, l + 4 * c);
+          const float4 p4 = *reinterpret_cast<const float4*>(pred + x0);
+          const float4 y4 = *reinterpret_cast<const float4*>(y + x0);
+          a[4 * c] = p4.x, a[4 * c + 1] = p4.y, a[4 * c + 2] = p4.z, a[4 * c + 3] = p4.w;
+          yv[4 * c] = y4.x, yv[4 * c + 1] = y4.y, yv[4 * c + 2] = y4.z, yv[4 * c + 3] = y4.w;
+          *reinterpret_cast<ushort4*>(leaf_out + x0) =
+              make_ushort4(static_cast<uint16_t>(l[4 * c]), static_cast<uint16_t>(l[4 * c + 1]),
+                           static_cast<uint16_t>(l[4 * c + 2]), static_cast<uint16_t>(l[4 * c + 3]));
+        } else {
+          l[4 * c] = l[4 * c + 1] = l[4 * c + 2] = l[4 * c + 3] = -1;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < OB_UNROLL; ++k) {
+        const int64_t r = r0 + threadIdx.x + k * OB_THREADS;
+        l[k] = -1;
+        if (r < n) {
+          l[k] = leaf_of(bins_t, bins, n, r, sf, sk, depth);
+          a[k] = pred[r];
+          yv[k] = y[r];
+          leaf_out[r] = static_cast<uint16_t>(l[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < OB_UNROLL; ++k) {
+      if (l[k] < 0) continue;
+      float g, h;
+      cbgd::loss_grad(loss, a[k], yv[k], &g, &h);
+      atomicAdd(&acc[2 * l[k]], g);
+      atomicAdd(&acc[2 * l[k] + 1], h);
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * L; i += blockDim.x)
-    if (s_tot[i] != 0.0) atomicAdd(&tot[i], s_tot[i]);
+  flush_acc(s_acc, L, tot);
 }
 
 // ------------------------------------------ supporting models: leaf by position
-// leaf_pos[q][k] for every permutation q, from the splits on q's position-ordered bins.
+// leaf_pos[q][k] (row stride lp_stride) for every permutation q, from the splits on q's
+// position-ordered bins; OB_UNROLL positions per thread and round (with VEC, two runs of 4
+// read with 32-bit loads and written with one 64-bit store each).
+template <bool VEC>
 __global__ void leaf_pos_kernel(const uint8_t* __restrict__ bins_t_pos, const uint8_t* __restrict__ bins_pos,
                                 int64_t n, int F, int F_pad, const cbg_split* __restrict__ sp, int depth,
-                                uint16_t* __restrict__ leaf_pos) {
+                                uint16_t* __restrict__ leaf_pos, int64_t lp_stride) {
   __shared__ int sf[OB_MAX_DEPTH], sk[OB_MAX_DEPTH];
   load_splits(sp, depth, sf, sk);
   __syncthreads();
   const int q = blockIdx.y;
   const uint8_t* bt = bins_t_pos ? bins_t_pos + static_cast<int64_t>(q) * F * n : nullptr;
   const uint8_t* bg = bins_pos + static_cast<int64_t>(q) * F_pad * n;
-  uint16_t* lq = leaf_pos + static_cast<int64_t>(q) * n;
-  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
-       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    lq[k] = static_cast<uint16_t>(leaf_of(bt, bg, n, k, sf, sk, depth));
+  uint16_t* lq = leaf_pos + static_cast<int64_t>(q) * lp_stride;
+  for (int64_t k0 = blockIdx.x * OB_ITEMS; k0 < n; k0 += static_cast<int64_t>(gridDim.x) * OB_ITEMS) {
+    if (VEC) {
+      int l[OB_UNROLL];
+#pragma unroll
+      for (int c = 0; c < OB_UNROLL / 4; ++c) {
+        const int64_t x0 = k0 + 4 * threadIdx.x + c * 4 * OB_THREADS;
+        if (x0 < n) leaf4(bt, n, x0, sf, sk, depth, l + 4 * c);
+      }
+#pragma unroll
+      for (int c = 0; c < OB_UNROLL / 4; ++c) {
+        const int64_t x0 = k0 + 4 * threadIdx.x + c * 4 * OB_THREADS;
+        if (x0 < n)
+          *reinterpret_cast<ushort4*>(lq + x0) =
+              make_ushort4(static_cast<uint16_t>(l[4 * c]), static_cast<uint16_t>(l[4 * c + 1]),
+                           static_cast<uint16_t>(l[4 * c + 2]), static_cast<uint16_t>(l[4 * c + 3]));
+      }
+    } else {
+      int l[OB_UNROLL];
+#pragma unroll
+      for (int k = 0; k < OB_UNROLL; ++k) {
+        const int64_t x = k0 + threadIdx.x + k * OB_THREADS;
+        l[k] = x < n ? leaf_of(bt, bg, n, x, sf, sk, depth) : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < OB_UNROLL; ++k)
+        if (l[k] >= 0) lq[k0 + threadIdx.x + k * OB_THREADS] = static_cast<uint16_t>(l[k]);
+    }
+  }
 }
 
 // ------------------------------------------------- supporting models: totals
 // Training items of permutation q are u in [1, 2^(I+1)): model i = floor(log2 u), position
 // p = u - 2^i, value at element u + 2^i. Block b > 0 covers u in [b B, (b+1) B), all in one
-// model, and sums in shared FP64 before adding to tot[q][i][l]; block 0 (the models with
-// fewer than B training positions) adds straight to tot.
-__global__ void sup_totals_kernel(const float* __restrict__ sup, int64_t sup_len, const float* __restrict__ y_pos,
-                                  const uint16_t* __restrict__ leaf_pos, int64_t n, int n_models, int depth, int loss,
-                                  double* __restrict__ tot) {
-  extern __shared__ double s_tot[];
+// model (B = OB_ITEMS, a power of two); block 0 (the models with fewer than B training
+// positions) adds its few items straight to the FP64 totals.
+__global__ void sup_totals_kernel(const float* __restrict__ sup, int64_t sup_stride, const float* __restrict__ y_pos,
+                                  const uint16_t* __restrict__ leaf_pos, int64_t lp_stride, int64_t n, int n_models,
+                                  int depth, int loss, double* __restrict__ tot) {
+  extern __shared__ float s_acc[];
   const int L = 1 << depth;
   const int q = blockIdx.y;
-  const float* sq = sup + static_cast<int64_t>(q) * sup_len;
+  const float* sq = sup + static_cast<int64_t>(q) * sup_stride;
   const float* yq = y_pos + static_cast<int64_t>(q) * n;
-  const uint16_t* lq = leaf_pos + static_cast<int64_t>(q) * n;
+  const uint16_t* lq = leaf_pos + static_cast<int64_t>(q) * lp_stride;
   double* tq = tot + static_cast<int64_t>(q) * n_models * L * 2;
   const int64_t u_end = min((blockIdx.x + 1) * OB_ITEMS, int64_t(1) << n_models);
   if (blockIdx.x == 0) {
@@ -183,20 +284,31 @@ __global__ void sup_totals_kernel(const float* __restrict__ sup, int64_t sup_len
   const int64_t u0 = blockIdx.x * OB_ITEMS;
   const int i = ilog2(u0);
   const int64_t half = int64_t(1) << i;
-  for (int x = threadIdx.x; x < 2 * L; x += blockDim.x) s_tot[x] = 0.0;
+  zero_acc(s_acc, L);
   __syncthreads();
-  for (int64_t u = u0 + threadIdx.x; u < u_end; u += blockDim.x) {
-    const int64_t p = u - half;
+  float* acc = s_acc + (threadIdx.x >> 5) * 2 * L;
+  float a[OB_UNROLL], yv[OB_UNROLL];
+  int l[OB_UNROLL];
+#pragma unroll
+  for (int k = 0; k < OB_UNROLL; ++k) {
+    const int64_t u = u0 + threadIdx.x + k * OB_THREADS;
+    l[k] = -1;
+    if (u < u_end) {
+      a[k] = sq[u + half];
+      yv[k] = yq[u - half];
+      l[k] = lq[u - half];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < OB_UNROLL; ++k) {
+    if (l[k] < 0) continue;
     float g, h;
-    cbgd::loss_grad(loss, sq[u + half], yq[p], &g, &h);
-    const int l = lq[p];
-    atomicAdd(&s_tot[2 * l], static_cast<double>(g));
-    atomicAdd(&s_tot[2 * l + 1], static_cast<double>(h));
+    cbgd::loss_grad(loss, a[k], yv[k], &g, &h);
+    atomicAdd(&acc[2 * l[k]], g);
+    atomicAdd(&acc[2 * l[k] + 1], h);
   }
   __syncthreads();
-  double* ti = tq + static_cast<int64_t>(i) * L * 2;
-  for (int x = threadIdx.x; x < 2 * L; x += blockDim.x)
-    if (s_tot[x] != 0.0) atomicAdd(&ti[x], s_tot[x]);
+  flush_acc(s_acc, L, tq + static_cast<int64_t>(i) * L * 2);
 }
 
 __device__ __forceinline__ float newton_step_lr(const double* t, double l2, double lr) {
@@ -208,14 +320,14 @@ __device__ __forceinline__ float newton_step_lr(const double* t, double l2, doub
 // -------------------------------------------------- supporting models: update
 // Element e in [2, sup_len) belongs to model i = floor(log2 e) - 1 at position
 // j = e - 2^(i+1); it gains float(lr v) of its leaf, v = -G/(H + l2) (0 when H + l2 = 0).
-__global__ void sup_apply_kernel(float* __restrict__ sup, int64_t sup_len, const uint16_t* __restrict__ leaf_pos,
-                                 int64_t n, int n_models, int depth, const double* __restrict__ tot, double l2,
-                                 double lr) {
+__global__ void sup_apply_kernel(float* __restrict__ sup, int64_t sup_stride, int64_t sup_len,
+                                 const uint16_t* __restrict__ leaf_pos, int64_t lp_stride, int n_models, int depth,
+                                 const double* __restrict__ tot, double l2, double lr) {
   extern __shared__ float s_lrv[];
   const int L = 1 << depth;
   const int q = blockIdx.y;
-  float* sq = sup + static_cast<int64_t>(q) * sup_len;
-  const uint16_t* lq = leaf_pos + static_cast<int64_t>(q) * n;
+  float* sq = sup + static_cast<int64_t>(q) * sup_stride;
+  const uint16_t* lq = leaf_pos + static_cast<int64_t>(q) * lp_stride;
   const double* tq = tot + static_cast<int64_t>(q) * n_models * L * 2;
   const int64_t e_end = min((blockIdx.x + 1) * OB_ITEMS, sup_len);
   if (blockIdx.x == 0) {
@@ -232,7 +344,20 @@ __global__ void sup_apply_kernel(float* __restrict__ sup, int64_t sup_len, const
   for (int l = threadIdx.x; l < L; l += blockDim.x)
     s_lrv[l] = newton_step_lr(tq + (static_cast<int64_t>(i) * L + l) * 2, l2, lr);
   __syncthreads();
-  for (int64_t e = e0 + threadIdx.x; e < e_end; e += blockDim.x) sq[e] += s_lrv[lq[e - base]];
+  float v[OB_UNROLL];
+  int l[OB_UNROLL];
+#pragma unroll
+  for (int k = 0; k < OB_UNROLL; ++k) {
+    const int64_t e = e0 + threadIdx.x + k * OB_THREADS;
+    l[k] = -1;
+    if (e < e_end) {
+      v[k] = sq[e];
+      l[k] = lq[e - base];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < OB_UNROLL; ++k)
+    if (l[k] >= 0) sq[e0 + threadIdx.x + k * OB_THREADS] = v[k] + s_lrv[l[k]];
 }
 
 // Copies one tree's splits and leaf values from the graph's fixed scratch to slot t of the
@@ -258,7 +383,7 @@ unsigned stride_grid(int64_t n) {
 }
 
 struct Work {
-  uint16_t* leaf_pos;   // [s][n]
+  uint16_t* leaf_pos;   // [s][pad64(n)]
   uint16_t* leaf_rows;  // [n]
   double* tot_final;    // [L][2]
   double* tot_sup;      // [s][n_models][L][2], directly after tot_final
@@ -272,7 +397,7 @@ Work carve_work(void* base, int64_t n, int s, int depth) {
   Carve c(base);
   Work w;
   const int L = 1 << depth;
-  w.leaf_pos = c.take<uint16_t>(static_cast<size_t>(s) * n);
+  w.leaf_pos = c.take<uint16_t>(static_cast<size_t>(s) * pad64(n));
   w.leaf_rows = c.take<uint16_t>(static_cast<size_t>(n));
   w.tot_final = c.take<double>(static_cast<size_t>(2 * L));
   w.tot_sup = c.take<double>(static_cast<size_t>(s) * (top_model(n) + 1) * L * 2, 8);
@@ -289,7 +414,7 @@ extern "C" {
 
 cbg_status cbg_ordered_sup_len(int64_t n, int64_t* len) {
   if (!len || n < 1 || n > INT32_MAX) return CBG_EINVAL;
-  *len = sup_len_of(n);
+  *len = sup_stride_of(n);
   return CBG_OK;
 }
 
@@ -336,13 +461,17 @@ cbg_status ordered_tree(cbg_ctx* ctx, const cbg_ordered_args* a, const Work& w, 
   const int L = 1 << D;
   const int n_models = top_model(n) + 1;
   const int64_t sup_len = sup_len_of(n);
+  const int64_t sup_stride = sup_stride_of(n);
+  const int64_t lp_stride = pad64(n);
   const int64_t plane = static_cast<int64_t>(sh->F_pad) * n;
   const unsigned grid_n = stride_grid(n);
+  const unsigned grid_rows = static_cast<unsigned>(std::min<int64_t>(ceil_div(n, OB_ITEMS), 152LL * 8));
   const dim3 grid_tot(static_cast<unsigned>(ceil_div(int64_t(1) << n_models, OB_ITEMS)), a->s);
   const dim3 grid_app(static_cast<unsigned>(ceil_div(sup_len, OB_ITEMS)), a->s);
-  const dim3 grid_leaf(std::max(1u, grid_n / a->s + 1), a->s);
+  const dim3 grid_leaf(static_cast<unsigned>(std::min<int64_t>(ceil_div(n, OB_ITEMS), 152LL * 8 / a->s + 1)), a->s);
   const size_t tot_bytes = sizeof(double) * 2 * L * (1 + static_cast<size_t>(a->s) * n_models);
-  const float* sup_r = a->sup + r * sup_len;
+  const size_t acc_bytes = sizeof(float) * OB_WARPS * 2 * L;
+  const float* sup_r = a->sup + r * sup_stride;
   const float* y_r = a->y_pos + r * n;
   if (a->gh_dtype == CBG_F32)
     ordered_grad_kernel<float><<<grid_n, OB_THREADS, 0, ctx->stream>>>(sup_r, y_r, n, a->loss, static_cast<float*>(a->g),
@@ -378,8 +507,17 @@ cbg_status ordered_tree(cbg_ctx* ctx, const cbg_ordered_args* a, const Work& w, 
   }
   // the final model: plain gradients of every row, leaf values, prediction update
   CBG_CUDA(ctx, cudaMemsetAsync(w.tot_final, 0, tot_bytes, ctx->stream));
-  rows_totals_kernel<<<grid_n, OB_THREADS, sizeof(double) * 2 * L, ctx->stream>>>(
-      a->bins_t, a->bins, n, sp, D, a->y, a->pred, a->loss, w.tot_final, w.leaf_rows);
+  const bool vec_rows = a->bins_t && n % 4 == 0 && ((reinterpret_cast<uintptr_t>(a->bins_t) |
+                                                      reinterpret_cast<uintptr_t>(a->y) |
+                                                      reinterpret_cast<uintptr_t>(a->pred)) & 15) == 0;
+  if (vec_rows)
+    rows_totals_kernel<true><<<grid_rows, OB_THREADS, acc_bytes, ctx->stream>>>(a->bins_t, a->bins, n, sp, D, a->y,
+                                                                               a->pred, a->loss, w.tot_final,
+                                                                               w.leaf_rows);
+  else
+    rows_totals_kernel<false><<<grid_rows, OB_THREADS, acc_bytes, ctx->stream>>>(a->bins_t, a->bins, n, sp, D, a->y,
+                                                                                a->pred, a->loss, w.tot_final,
+                                                                                w.leaf_rows);
   CBG_CHECK_LAUNCH(ctx);
   cbg_apply_args aa{};
   aa.bins = a->bins;
@@ -396,14 +534,20 @@ cbg_status ordered_tree(cbg_ctx* ctx, const cbg_ordered_args* a, const Work& w, 
   st = cbg_apply_tree(ctx, &aa);
   if (st != CBG_OK) return st;
   // the supporting models of every permutation
-  leaf_pos_kernel<<<grid_leaf, OB_THREADS, 0, ctx->stream>>>(a->bins_t_pos, a->bins_pos, n, sh->F, sh->F_pad, sp, D,
-                                                            w.leaf_pos);
+  const bool vec_pos = a->bins_t_pos && n % 4 == 0 && (reinterpret_cast<uintptr_t>(a->bins_t_pos) & 3) == 0;
+  if (vec_pos)
+    leaf_pos_kernel<true><<<grid_leaf, OB_THREADS, 0, ctx->stream>>>(a->bins_t_pos, a->bins_pos, n, sh->F, sh->F_pad,
+                                                                    sp, D, w.leaf_pos, lp_stride);
+  else
+    leaf_pos_kernel<false><<<grid_leaf, OB_THREADS, 0, ctx->stream>>>(a->bins_t_pos, a->bins_pos, n, sh->F, sh->F_pad,
+                                                                     sp, D, w.leaf_pos, lp_stride);
   CBG_CHECK_LAUNCH(ctx);
-  sup_totals_kernel<<<grid_tot, OB_THREADS, sizeof(double) * 2 * L, ctx->stream>>>(
-      a->sup, sup_len, a->y_pos, w.leaf_pos, n, n_models, D, a->loss, w.tot_sup);
+  sup_totals_kernel<<<grid_tot, OB_THREADS, acc_bytes, ctx->stream>>>(a->sup, sup_stride, a->y_pos, w.leaf_pos,
+                                                                     lp_stride, n, n_models, D, a->loss, w.tot_sup);
   CBG_CHECK_LAUNCH(ctx);
-  sup_apply_kernel<<<grid_app, OB_THREADS, sizeof(float) * L, ctx->stream>>>(a->sup, sup_len, w.leaf_pos, n, n_models,
-                                                                            D, w.tot_sup, a->l2, a->lr);
+  sup_apply_kernel<<<grid_app, OB_THREADS, sizeof(float) * L, ctx->stream>>>(a->sup, sup_stride, sup_len, w.leaf_pos,
+                                                                            lp_stride, n_models, D, w.tot_sup, a->l2,
+                                                                            a->lr);
   CBG_CHECK_LAUNCH(ctx);
   return CBG_OK;
 }
@@ -463,6 +607,12 @@ cbg_status cbg_boost_ordered(cbg_ctx* ctx, const cbg_ordered_args* a) {
   CBG_REQUIRE(ctx, a->work_bytes >= w.bytes, "work holds %zu bytes, %zu needed", a->work_bytes, w.bytes);
   DeviceGuard guard(ctx->device);
   const int L = 1 << D;
+  const int acc_bytes = static_cast<int>(sizeof(float)) * OB_WARPS * 2 * L;   // 64 KB at depth 10
+  if (acc_bytes > 48 * 1024) {
+    CBG_CUDA(ctx, cudaFuncSetAttribute(rows_totals_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, acc_bytes));
+    CBG_CUDA(ctx, cudaFuncSetAttribute(rows_totals_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, acc_bytes));
+    CBG_CUDA(ctx, cudaFuncSetAttribute(sup_totals_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, acc_bytes));
+  }
   if (!a->use_graph || a->trees <= 1) {
     for (int t = 0; t < a->trees; ++t) {
       cbg_status st = ordered_tree(ctx, a, w, (a->first_tree + t) % a->s, a->splits + static_cast<int64_t>(t) * D,

@@ -1,5 +1,5 @@
 // One-off steps of the path: permutation, prior, ordered target statistics (Section 2,
-// Eq. 1), quantile borders and uint8 quantisation (Section 4, "Dense numerical
+// Eq. 1), quantile borders and uint8 quantisation (Section 5, "Dense numerical
 // features").
 #include "cbg_internal.cuh"
 
@@ -11,18 +11,10 @@ namespace {
 
 constexpr int BLOCK = 256;
 
-// SplitMix64 (Steele, Lea & Flood 2014): output i of the generator seeded with `seed`.
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
-  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  return z ^ (z >> 31);
-}
-
 __global__ void perm_keys_kernel(uint64_t seed, int64_t n, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    keys[i] = splitmix64_at(seed, static_cast<uint64_t>(i));
+    keys[i] = cbgd::splitmix64_at(seed, static_cast<uint64_t>(i));
     vals[i] = static_cast<uint32_t>(i);
   }
 }

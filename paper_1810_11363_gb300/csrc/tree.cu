@@ -267,7 +267,8 @@ constexpr int SC_BINS_PER_LANE = 8;   // 32 lanes x 8 = 256 bins
 template <int SC_WARPS>
 __device__ __forceinline__ void score_level_body(const float2* __restrict__ hist_df, int level_leaves, int F, int max_bins,
                        const int32_t* __restrict__ n_borders, double l2, BestF* __restrict__ best, Misc* misc,
-                       int force_f, int force_k, int depth, cbg_split* __restrict__ splits, int bid, int nblk) {
+                       int force_f, int force_k, int depth, cbg_split* __restrict__ splits, int bid, int nblk,
+                       const cbg_split* __restrict__ chal) {
   constexpr int NT = SC_WARPS * 32;
   __shared__ DF s_acc[SC_WARPS][256];
   __shared__ double r_s[NT];
@@ -394,6 +395,11 @@ __device__ __forceinline__ void score_level_body(const float2* __restrict__ hist
       cf = force_f;
       ck = force_k;
       cs = *(volatile double*)&misc->forced_score;
+    } else if (chal != nullptr && chal->feature >= 0 && (cf < 0 || chal->score > cs)) {
+      // a split on a column outside bins (a feature combination) with a strictly higher score
+      cf = chal->feature;
+      ck = chal->border;
+      cs = chal->score;
     }
     splits[depth].feature = cf;
     splits[depth].border = cf >= 0 ? ck : -1;
@@ -406,8 +412,9 @@ template <int SC_WARPS>
 __global__ void __launch_bounds__(SC_WARPS * 32)
     score_level_kernel(const float2* __restrict__ hist_df, int level_leaves, int F, int max_bins,
                        const int32_t* __restrict__ n_borders, double l2, BestF* __restrict__ best, Misc* misc,
-                       int force_f, int force_k, int depth, cbg_split* __restrict__ splits) {
-  score_level_body<SC_WARPS>(hist_df, level_leaves, F, max_bins, n_borders, l2, best, misc, force_f, force_k, depth, splits, blockIdx.x, gridDim.x);
+                       int force_f, int force_k, int depth, cbg_split* __restrict__ splits,
+                       const cbg_split* __restrict__ chal) {
+  score_level_body<SC_WARPS>(hist_df, level_leaves, F, max_bins, n_borders, l2, best, misc, force_f, force_k, depth, splits, blockIdx.x, gridDim.x, chal);
 }
 
 // FP64 child totals of the level's split for leaf l, one warp: bins <= k stay in leaf l,
@@ -641,7 +648,9 @@ __device__ __forceinline__ void part_flags_body(const uint8_t* __restrict__ bins
                                   Segs* __restrict__ nxt, Plan* __restrict__ plan, int rows_per_item, int cs,
                                   unsigned long long* __restrict__ rows_hist, Misc* misc,
                                   const double* __restrict__ hist, int F, int max_bins,
-                                  double* __restrict__ child_totals, int bid, int nblk) {
+                                  double* __restrict__ child_totals, int bid, int nblk,
+                                  const uint8_t* __restrict__ chal_bins, const double* __restrict__ chal_hist,
+                                  int chal_max_bins) {
   __shared__ uint32_t wsum[PT_THREADS / 32];
   __shared__ uint32_t sh_ones[1 << MAX_DEPTH];
   __shared__ int sh_pos[1 << (MAX_DEPTH - 1)], sh_leaf[1 << (MAX_DEPTH - 1)];
@@ -652,9 +661,15 @@ __device__ __forceinline__ void part_flags_body(const uint8_t* __restrict__ bins
   load_seg_table(seg, L, sh_pos, sh_leaf);
   __syncthreads();
   const int f = splits[depth].feature, k = splits[depth].border;
+  // a feature index >= F is the challenger's column (outside bins), with its own histogram
+  const bool chal = f >= F && chal_bins != nullptr;
   // the FP64 child totals of the split, one warp per leaf of the level
-  for (int l = bid * (PT_THREADS / 32) + (threadIdx.x >> 5); l < L; l += nblk * (PT_THREADS / 32))
-    child_totals_warp(hist, l, L, F, max_bins, f, k, child_totals);
+  for (int l = bid * (PT_THREADS / 32) + (threadIdx.x >> 5); l < L; l += nblk * (PT_THREADS / 32)) {
+    if (chal)
+      child_totals_warp(chal_hist, l, L, 1, chal_max_bins, 0, k, child_totals);
+    else
+      child_totals_warp(hist, l, L, F, max_bins, f, k, child_totals);
+  }
   const int64_t base = static_cast<int64_t>(bid) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
   int si = seg_find(sh_pos, L, base);
   uint32_t cnt = 0, run = 0;
@@ -664,7 +679,7 @@ __device__ __forceinline__ void part_flags_body(const uint8_t* __restrict__ bins
     const int64_t pos = base + i;
     if (pos < n) {
       const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
-      const int bit = split_bit(bins, bins_t, n, row, f, k);
+      const int bit = chal ? (chal_bins[row] > k ? 1 : 0) : split_bit(bins, bins_t, n, row, f, k);
       while (si + 1 < L && sh_pos[si + 1] <= pos) ++si;
       const int lf = sh_leaf[si];
       if (bit) leaf[row] = static_cast<uint16_t>(lf + L);   // rows of leaf lf already hold lf
@@ -710,8 +725,9 @@ __global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_
                                   Segs* __restrict__ nxt, Plan* __restrict__ plan, int rows_per_item, int cs,
                                   unsigned long long* __restrict__ rows_hist, Misc* misc,
                                   const double* __restrict__ hist, int F, int max_bins,
-                                  double* __restrict__ child_totals) {
-  part_flags_body(bins, bins_t, n, order, splits, depth, leaf, flags, tile_cnt, seg, write_flags, n_ptiles, nxt, plan, rows_per_item, cs, rows_hist, misc, hist, F, max_bins, child_totals, blockIdx.x, gridDim.x);
+                                  double* __restrict__ child_totals, const uint8_t* __restrict__ chal_bins,
+                                  const double* __restrict__ chal_hist, int chal_max_bins) {
+  part_flags_body(bins, bins_t, n, order, splits, depth, leaf, flags, tile_cnt, seg, write_flags, n_ptiles, nxt, plan, rows_per_item, cs, rows_hist, misc, hist, F, max_bins, child_totals, blockIdx.x, gridDim.x, chal_bins, chal_hist, chal_max_bins);
 }
 
 // C: stable partition of every segment: the row at position i moves to
@@ -960,7 +976,7 @@ __global__ void __launch_bounds__(SC_WARPS * 32) score_batched_kernel(const Leve
   const int2 m = map[blockIdx.x];
   const LevelProblem& P = tab[m.x];
   score_level_body<SC_WARPS>(P.hist_df, level_leaves, P.F, P.max_bins, P.n_borders, l2, P.best, P.misc, -1, -1, depth,
-                             P.sp, m.y, P.F);
+                             P.sp, m.y, P.F, nullptr);
 }
 
 __global__ void flags_batched_kernel(const LevelProblem* __restrict__ tab, const int2* __restrict__ map, int depth,
@@ -969,7 +985,7 @@ __global__ void flags_batched_kernel(const LevelProblem* __restrict__ tab, const
   const LevelProblem& P = tab[m.x];
   part_flags_body(P.bins, P.bins_t, P.n, P.order_cur, P.sp, depth, P.leaf, P.flags, P.tcnt, P.seg_cur, write_flags,
                   P.n_ptiles, P.seg_nxt, P.plan, P.rows_per_item, P.cs, P.rows_hist, P.misc, P.hist_cur, P.F,
-                  P.max_bins, P.child_totals, m.y, static_cast<int>(P.n_ptiles));
+                  P.max_bins, P.child_totals, m.y, static_cast<int>(P.n_ptiles), nullptr, nullptr, 0);
 }
 
 __global__ void scatter_batched_kernel(const LevelProblem* __restrict__ tab, const int2* __restrict__ map, int depth) {
@@ -1081,6 +1097,9 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   CBG_REQUIRE(ctx, a->force_feature < L.F, "force_feature out of range");
   CBG_REQUIRE(ctx, a->force_feature < 0 || (a->force_border >= 0 && a->force_border < L.max_bins - 1),
               "force_border out of range");
+  CBG_REQUIRE(ctx, !a->challenger || (a->challenger_bins && a->challenger_hist && a->challenger_max_bins >= 2 &&
+                                      a->challenger_max_bins <= 256),
+              "a challenger needs its bins, its histogram and 2 <= challenger_max_bins <= 256");
   DeviceGuard guard(ctx->device);
   void* S = a->state;
   Plan* plan = at<Plan>(S, L.o_plan);
@@ -1134,7 +1153,7 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
       constexpr int W = decltype(warps)::value;
       score_level_kernel<W><<<L.F, W * 32, 0, ctx->stream>>>(hist_df, level_leaves, L.F, L.max_bins, a->n_borders,
                                                            a->l2, best, misc, a->force_feature, a->force_border, d,
-                                                           a->splits);
+                                                           a->splits, a->challenger);
     };
     if (level_leaves >= SC_MAX_WARPS) launch(std::integral_constant<int, SC_MAX_WARPS>{});
     else if (level_leaves >= 8) launch(std::integral_constant<int, 8>{});
@@ -1157,7 +1176,7 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   part_flags_kernel<<<static_cast<unsigned>(L.n_ptiles), PT_THREADS, 0, ctx->stream>>>(
       a->bins, a->bins_t, L.n, order_cur, a->splits, d, a->leaf, flags, tcnt, seg_cur, last ? 0 : 1, L.n_ptiles,
       seg_nxt, plan, L.rows_per_item, cs, at<unsigned long long>(S, L.o_count), misc, hist_cur, L.F, L.max_bins,
-      a->child_totals);
+      a->child_totals, a->challenger ? a->challenger_bins : nullptr, a->challenger_hist, a->challenger_max_bins);
   CBG_CHECK_LAUNCH(ctx);
   if (!last) {
     part_scatter_kernel<<<static_cast<unsigned>(L.n_ptiles), PT_THREADS, 0, ctx->stream>>>(

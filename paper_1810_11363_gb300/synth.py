@@ -1,6 +1,6 @@
 """Seeded synthetic workloads shaped like the paper's benchmarks.
 
-The paper measures on Epsilon (4e5 x 2000 dense, Section 5 "GPU vs CPU training
+The paper measures on Epsilon (4e5 x 2000 dense, Section 6 "GPU vs CPU training
 performance"), Criteo (36e6 rows, 26 categorical + 13 numerical) and the eight
 Table 1 datasets; none of them is available here, so these generators stand in
 for them by shape: row and feature counts, bin counts, categorical

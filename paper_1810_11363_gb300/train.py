@@ -1,8 +1,8 @@
 """Training driver: sequences the library's C-ABI calls over torch-owned device memory.
 
 preprocess(): permutation sigma, prior, ordered target statistics (Section 2, Eq. 1),
-quantile borders and uint8 quantisation of float and TS columns (Section 4).
-fit(): classic boosting of oblivious trees through cbg_boost (Sections 3-4).
+quantile borders and uint8 quantisation of float and TS columns (Section 5).
+fit(): classic boosting of oblivious trees through cbg_boost (Sections 3-5).
 ts_tables() / preprocess_new() / predict(): the inference path: full-data statistics of
 new rows, quantisation with the training borders, and the model value (Section 4,
 "Fast scorer").
@@ -198,6 +198,37 @@ def fit_ordered(ctx: cbg.Context, op: OrderedPrepared, y, loss: str, depth: int,
                           sup, bufs.g, bufs.h, bufs.leaf, bufs.splits, bufs.leaf_values, bufs.child_totals, work,
                           use_graph=use_graph)
     return Model(bufs.splits[:trees], bufs.leaf_values[:trees], bufs.pred, depth, lr, sup)
+
+
+@dataclass
+class CombosModel:
+    """Classic boosting with feature combinations: the model plus, per (tree, level), the
+    combination a combination split (feature >= F) uses."""
+    model: Model
+    combo_items: np.ndarray     # int32 [T][D][max_complexity][3] (kind, a, b); kind -1 = unused
+    combo_nb: np.ndarray        # int32 [T][D]
+    combo_borders: np.ndarray   # float32 [T][D][max_borders]
+
+
+def fit_combos(ctx: cbg.Context, prep: Prepared, cat, y, label_kind: str, loss: str, depth: int, trees: int,
+               lr: float, l2: float, max_borders: int, max_complexity: int = 4, a: float = 1.0,
+               gh_dtype: str = "f32", tiles: dict | None = None) -> CombosModel:
+    """Greedy feature combinations (cbg_boost_combos) over preprocess()'s data; cat holds
+    the raw category ids [C][n] the TS columns were computed from."""
+    import torch
+    bufs = alloc_fit(prep, depth, trees, gh_dtype, tiles)
+    C_ = prep.F - prep.F_float
+    work = torch.empty(cbg.cbg_combo_work_bytes(prep.n, C_, depth, max_borders, max_complexity), dtype=torch.uint8,
+                       device=prep.bins.device)
+    items = np.empty((max(trees, 1), depth, max_complexity, 3), np.int32)
+    nb = np.empty((max(trees, 1), depth), np.int32)
+    borders = np.empty((max(trees, 1), depth, max_borders), np.float32)
+    cbg.cbg_boost_combos(ctx, bufs.shape, bufs.state, prep.bins, prep.bins_t, prep.n_borders, cat, C_, prep.F_float,
+                         prep.perm, y, label_kind, max_borders, prep.prior, a, max_complexity, loss, gh_dtype, depth,
+                         trees, lr, l2, bufs.pred, bufs.g, bufs.h, bufs.leaf, bufs.splits, bufs.leaf_values,
+                         bufs.child_totals, work, items, nb, borders)
+    model = Model(bufs.splits[:trees], bufs.leaf_values[:trees], bufs.pred, depth, lr)
+    return CombosModel(model, items[:trees], nb[:trees], borders[:trees])
 
 
 def grouped_from_rowmajor(bins_rm: np.ndarray) -> np.ndarray:

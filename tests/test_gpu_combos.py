@@ -1,0 +1,101 @@
+"""GPU parity of greedy feature combinations (Section 2 "Feature combinations") against
+the oracle, which prepares its own inputs and runs its own boosting with combinations.
+
+Splits (ordinary or combination: the items and the border), the combination's borders
+and the leaf values are compared tree by tree; a split may differ only where the
+oracle's best and runner-up scores are within 1e-5 relative, and the runs are compared up
+to there. Binary labels make every TS, border and bin exact; predictions within 1e-4."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import to_dev, to_host
+from paper_1810_11363_gb300 import cbg, synth, train
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = cbg.Context(0)
+    yield c
+    c.close()
+
+
+def _run_both(ctx, w, depth, trees, max_borders, mc, lr=0.2, l2=1.0):
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), w.label_kind, w.max_borders, a=w.a,
+                            seed=w.seed)
+    got = train.fit_combos(ctx, prep, to_dev(w.cat), to_dev(w.y), w.label_kind, w.loss, depth, trees, lr, l2,
+                           max_borders, mc, a=w.a)
+    cbg.cbg_sync(ctx)
+    ref_prep = oracle.preprocess(w, prep.F_pad)
+    assert np.array_equal(train.rowmajor_from_grouped(to_host(prep.bins), w.n, prep.F_pad), ref_prep["bins"])
+    res = oracle.fit_combos(ref_prep["bins"], w.n_features, w.n_float, ref_prep["n_borders"], w.cat, w.y, w.loss,
+                            depth, trees, lr, l2, ref_prep["perm"], ref_prep["prior"], w.a, max_borders, mc)
+    return got, res
+
+
+def _compare(got, res, F, depth, trees, near=1e-5):
+    sp = got.model.host_splits()
+    n_combo = 0
+    for t in range(trees):
+        for d in range(depth):
+            same = (sp[t, d]["feature"], sp[t, d]["border"]) == (res["split_f"][t, d], res["split_k"][t, d])
+            if same and res["split_f"][t, d] >= F:
+                same = (np.array_equal(got.combo_items[t, d], res["combo_items"][t, d])
+                        and got.combo_nb[t, d] == res["combo_nb"][t, d])
+            if not same:
+                assert res["score"][t, d] - res["second"][t, d] <= near * abs(res["score"][t, d]), (t, d)
+                return t, n_combo
+            if res["split_f"][t, d] >= F:
+                n_combo += 1
+                nb = res["combo_nb"][t, d]
+                assert np.array_equal(got.combo_borders[t, d, :nb].view(np.uint32),
+                                      res["combo_borders"][t, d, :nb].view(np.uint32))
+        assert np.allclose(to_host(got.model.leaf_values[t]), res["leaf_values"][t], rtol=1e-4, atol=1e-6), t
+    assert np.all(np.abs(to_host(got.model.pred) - res["pred"]) <= 1e-4)
+    return trees, n_combo
+
+
+def _interaction_workload(n, seed=0):
+    """Three categorical columns (4 categories, Zipf-free) and two floats; the label
+    depends on the parity of c0 XOR the parity of c1, which no single column carries."""
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(2, n)).astype(np.float32)
+    k = rng.integers(0, 4, size=(3, n))
+    cat = (k * 1000003 + 5).astype(np.uint32)
+    z = (k[0] % 2) ^ (k[1] % 2)
+    y = (rng.random(n) < np.where(z == 1, 0.85, 0.15)).astype(np.float32)
+    return synth.Workload("interaction", x, cat, y, "logloss", 15, 4, 3, 0.2, 1.0, 1.0, seed)
+
+
+@pytest.mark.parametrize("n", [3000, 20001])
+def test_combinations_match_oracle_on_an_interaction(ctx, n):
+    w = _interaction_workload(n)
+    got, res = _run_both(ctx, w, depth=4, trees=3, max_borders=15, mc=3)
+    assert (res["split_f"] >= w.n_features).any()       # the oracle does take combinations here
+    compared, n_combo = _compare(got, res, w.n_features, 4, 3)
+    assert compared >= 1 and n_combo >= 1
+
+
+@pytest.mark.parametrize("depth,mc", [(3, 2), (5, 4)])
+def test_combinations_match_oracle_on_logloss_shaped_data(ctx, depth, mc):
+    w = synth.logloss_1m(n=12000, trees=3)
+    got, res = _run_both(ctx, w, depth=depth, trees=3, max_borders=31, mc=mc)
+    compared, _ = _compare(got, res, w.n_features, depth, 3)
+    assert compared >= 1
+
+
+def test_max_complexity_one_is_classic_boosting(ctx):
+    w = synth.logloss_1m(n=8000, trees=3)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    got = train.fit_combos(ctx, prep, to_dev(w.cat), to_dev(w.y), "binary", "logloss", 4, 3, 0.1, 3.0, 15, 1)
+    plain = train.fit(ctx, prep, to_dev(w.y), "logloss", 4, 3, 0.1, 3.0)
+    cbg.cbg_sync(ctx)
+    a, b = got.model.host_splits(), plain.host_splits()
+    assert np.array_equal(a["feature"], b["feature"]) and np.array_equal(a["border"], b["border"])
+    assert np.allclose(to_host(got.model.pred), to_host(plain.pred), atol=1e-6)
+    assert np.all(got.combo_items == -1)

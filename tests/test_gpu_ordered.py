@@ -38,8 +38,8 @@ def _sup_to_oracle_layout(sup_gpu, n):
 def test_sup_len_and_work_bytes():
     for n in [1, 2, 3, 4, 5, 1000, 1 << 20, (1 << 20) + 1]:
         I = (n - 1).bit_length() - 1 if n > 1 else 0
-        assert cbg.cbg_ordered_sup_len(n) == (2 << I) + n
-        assert cbg.cbg_ordered_sup_len(n) - 2 >= oracle.ordered_sup_size(n)
+        assert cbg.cbg_ordered_sup_len(n) == ((2 << I) + n + 63) // 64 * 64
+        assert (2 << I) + n - 2 >= oracle.ordered_sup_size(n)
     assert cbg.cbg_ordered_work_bytes(1000, 3, 6) >= 3 * 1000 * 2 + 1000 * 2 + 64 * 16 * (1 + 3 * 10)
 
 
@@ -157,8 +157,8 @@ def _forced(ctx, n, s, seed):
     return op, bins_all, perms, y, yd
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 2048, 2049, 4097, 70001])
-@pytest.mark.parametrize("depth", [1, 3])
+@pytest.mark.parametrize("n,depth", [(n, d) for n in [1, 2, 3, 4, 5, 2048, 2049, 4097, 70001] for d in (1, 3)]
+                         + [(5000, 10), (2049, 8)])
 def test_supporting_models_match_oracle_at_ragged_sizes(ctx, n, depth):
     s, trees = 2, 6
     op, bins_all, perms, y, yd = _forced(ctx, n, s, n + depth)

@@ -1,5 +1,5 @@
 """GPU parity of the one-off steps against the oracle: permutation, prior, ordered TS
-(Eq. 1), borders and quantisation (Section 4). Integer and selection results are
+(Eq. 1), borders and quantisation (Section 5). Integer and selection results are
 bit-exact; real-label TS sums within 1e-12 of the prefix sum of |y|."""
 import numpy as np
 import pytest
