@@ -76,8 +76,9 @@ typedef struct cbg_split {
  * histograms of 16 features updated without atomics, 3 = one shared histogram
  * per CTA with (G, H) updated by one 64-bit compare-and-swap, 4 = lane-per-
  * feature warp-private histograms with store forwarding (bins must be 16-byte
- * aligned), 5 = the same with G and H in separate warps. Zero fields take
- * library defaults. */
+ * aligned), 5 = the same with G and H in separate warps, 6 = lane-per-feature
+ * over the 4-bit packed bins of cbg_pack_bins4 (max_bins <= 16; the level
+ * arguments carry bins4). Zero fields take library defaults. */
 typedef struct cbg_tiles {
   int32_t slab_chunks;
   int32_t rows_per_item;
@@ -215,6 +216,9 @@ typedef struct cbg_level_args {
   const uint8_t* challenger_bins;
   const double* challenger_hist;
   int32_t challenger_max_bins;
+  /* 4-bit packed bins of the same rows (cbg_pack_bins4), read by the histogram when
+   * shape->tiles.kernel is 6; NULL otherwise. */
+  const uint8_t* bins4;
 } cbg_level_args;
 
 /* One level d (Sections 3-4): FP64 histograms hist[l][f][b] = sum of (g, h)
@@ -288,6 +292,7 @@ typedef struct cbg_boost_args {
   double* leaf_values;
   double* child_totals;   /* device [2^depth][2] scratch */
   int32_t use_graph;
+  const uint8_t* bins4;        /* device 4-bit packed bins or NULL (tiles kernel 6 needs them) */
 } cbg_boost_args;
 cbg_status cbg_boost(cbg_ctx* ctx, const cbg_boost_args* args);
 
@@ -429,8 +434,9 @@ cbg_status cbg_predict(cbg_ctx* ctx, const cbg_predict_args* args);
  * ctx stream, CUDA events), and writes the fastest to *best and its mean device
  * time per tree (ms) to *best_ms. The candidates vary:
  *  - the histogram kernel: shared-memory reductions (1), lane-per-feature warp
- *    histograms (4) and their one-statistic-per-warp form (5), or 16-feature
- *    warp-private histograms (2);
+ *    histograms (4) and their one-statistic-per-warp form (5), 16-feature
+ *    warp-private histograms (2), and with bins4 and max_bins <= 16 the packed
+ *    lane-per-feature kernel (6);
  *  - CTAs per cluster;
  *  - rows per CTA of a work unit.
  * Ownership and layout follow cbg_build_level. args->shape->tiles is ignored.
@@ -455,7 +461,18 @@ typedef struct cbg_autotune_args {
   cbg_split* splits;           /* device [max_depth] scratch                  */
   double* child_totals;        /* device [2^depth][2] scratch                 */
   int32_t reps;
+  const uint8_t* bins4;        /* device 4-bit packed bins (cbg_pack_bins4) or NULL; with
+                                  max_bins <= 16 the packed kernel is a candidate too */
 } cbg_autotune_args;
+
+/* 4-bit packed bins (Section 5 "Dense numerical features": features with at most
+ * 15 borders take 4 bits): bins4[q][r][i] holds feature 64q + i of row r in its
+ * low nibble and feature 64q + 32 + i in its high nibble (device uint8
+ * [ceil(F_pad/64)][n][32], caller-owned, 16-byte aligned like bins). Every bin
+ * of bins must be below 16; a larger one makes the next cbg_sync() return
+ * CBG_EDATA. The packed records are half the bytes of the grouped layout; the
+ * histogram kernel 6 (tiles.kernel) reads them. */
+cbg_status cbg_pack_bins4(cbg_ctx* ctx, const uint8_t* bins, int64_t n, int32_t F_pad, uint8_t* bins4);
 
 /* Tree-state bytes large enough for every autotuner candidate of `shape`. */
 cbg_status cbg_autotune_state_bytes(const cbg_tree_shape* shape, size_t* bytes);
@@ -557,6 +574,14 @@ typedef struct cbg_combo_item {
   int32_t a;
   int32_t b;
 } cbg_combo_item;
+
+/* Values of one combination for n rows (device uint32 ids [n]): items (host,
+ * n_items of them, 1..16, sorted by (kind, a, b) without repeats) over cat
+ * (device uint32 [C][n], kind 0) and bins_t (device uint8 [F][n], kind 1). The
+ * same chain as the training path, for applying a combination split to new rows
+ * (with cbg_ts_table / cbg_ts_apply / cbg_quantize). Synchronises the stream. */
+cbg_status cbg_combo_ids(cbg_ctx* ctx, const cbg_combo_item* items, int32_t n_items, const uint32_t* cat, int32_t C,
+                         const uint8_t* bins_t, int32_t F, int64_t n, uint32_t* ids);
 
 /* Bytes of the device work buffer of cbg_boost_combos. */
 cbg_status cbg_combo_work_bytes(int64_t n, int32_t C, int32_t depth, int32_t max_borders, int32_t max_complexity,

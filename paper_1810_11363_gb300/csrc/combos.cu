@@ -333,6 +333,46 @@ cbg_status cbg_combo_work_bytes(int64_t n, int32_t C, int32_t depth, int32_t max
   return CBG_OK;
 }
 
+cbg_status cbg_combo_ids(cbg_ctx* ctx, const cbg_combo_item* items, int32_t n_items, const uint32_t* cat, int32_t C,
+                         const uint8_t* bins_t, int32_t F, int64_t n, uint32_t* ids) {
+  if (!ctx) return CBG_EINVAL;
+  CBG_REQUIRE(ctx, items != nullptr && n_items >= 1 && n_items <= CB_MAX_ITEMS, "need 1..16 items");
+  CBG_REQUIRE(ctx, n >= 1 && n <= INT32_MAX && ids != nullptr, "need n in [1, 2^31-1] and ids");
+  std::vector<int> flat(3 * static_cast<size_t>(n_items));
+  for (int i = 0; i < n_items; ++i) {
+    const cbg_combo_item& it = items[i];
+    CBG_REQUIRE(ctx, (it.kind == 0 && it.a >= 0 && it.a < C && cat) || (it.kind == 1 && it.a >= 0 && it.a < F && bins_t),
+                "item %d names no column of cat or bins_t", i);
+    bool ordered = true;
+    if (i > 0) {
+      Item prev, cur;
+      prev.kind = items[i - 1].kind;
+      prev.a = items[i - 1].a;
+      prev.b = items[i - 1].b;
+      cur.kind = it.kind;
+      cur.a = it.a;
+      cur.b = it.b;
+      ordered = prev < cur;
+    }
+    CBG_REQUIRE(ctx, ordered, "items must be sorted by (kind, a, b) without repeats");
+    flat[3 * i] = it.kind;
+    flat[3 * i + 1] = it.a;
+    flat[3 * i + 2] = it.b;
+  }
+  DeviceGuard guard(ctx->device);
+  cbg_status st = ws_reserve(ctx, 4096);
+  if (st != CBG_OK) return st;
+  int* d_items = static_cast<int*>(ctx->ws);
+  int* d_n = d_items + 3 * CB_MAX_ITEMS;
+  CBG_CUDA(ctx, cudaMemcpyAsync(d_items, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CBG_CUDA(ctx, cudaMemcpyAsync(d_n, &n_items, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  combo_ids_kernel<<<dim3(grid_for(n, 1), 1), CB_THREADS, 0, ctx->stream>>>(d_items, d_n, n_items, cat, bins_t, n, ids);
+  CBG_CHECK_LAUNCH(ctx);
+  // the host arrays above must outlive the copies: wait for them
+  CBG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return CBG_OK;
+}
+
 cbg_status cbg_boost_combos(cbg_ctx* ctx, const cbg_combo_args* a) {
   if (!ctx) return CBG_EINVAL;
   CBG_REQUIRE(ctx, a != nullptr && a->shape != nullptr, "args is NULL");

@@ -643,6 +643,231 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
   }
 }
 
+// ------------------------------------ lane-per-feature over 4-bit packed bins
+// The packed layout of Section 5 for features with at most 16 bins: byte i of a row's
+// 32-byte record in packed group q holds feature 64q + i in its low nibble and feature
+// 64q + 32 + i in its high nibble (bins4 [ceil(G/2)][n][32], 64 features per record, half
+// the bytes of the uint8 layout). The kernel is the lane kernel above with two update
+// chains per lane: lane i owns column i of both 32-feature halves, in a warp histogram
+// [max_bins][2][32] float2 whose halves are exactly the histograms of uint8 groups 2q and
+// 2q + 1, so the partials and the reduction are unchanged. A 32-row block is worked in
+// two halves of 16 rows to bound the registers of the precomputed cell addresses.
+constexpr int L4_SUB = 16;
+
+inline size_t l4_warp_bytes(int max_bins) {
+  return static_cast<size_t>(max_bins) * 2 * GROUP * sizeof(float2) + static_cast<size_t>(LH_STAGES) * LH_ROWS * GROUP +
+         LH_ROWS * sizeof(float2);
+}
+inline int l4_warps(int max_bins, int requested_threads) {
+  int w = static_cast<int>((227 * 1024) / l4_warp_bytes(max_bins));
+  if (w > LH_MAX_WARPS) w = LH_MAX_WARPS;
+  if (requested_threads > 0 && requested_threads / 32 < w) w = requested_threads / 32;
+  return w < 1 ? 1 : w;
+}
+inline size_t l4_smem_bytes(int max_bins, int warps) { return static_cast<size_t>(warps) * l4_warp_bytes(max_bins); }
+
+template <typename GH>
+__global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
+    level_hist_lane4_kernel(const uint8_t* __restrict__ bins4, int64_t n, int G, int F,
+                            const uint32_t* __restrict__ order, const GH* __restrict__ gpos,
+                            const GH* __restrict__ hpos, const Plan* __restrict__ plan, int max_bins,
+                            float* __restrict__ partials) {
+  namespace cgr = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char l4sh[];
+  constexpr int MAX_CS = 16;
+  constexpr uint32_t NONE = 0xffffffffu;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int cs = static_cast<int>(cl.num_blocks());
+  const int rank = static_cast<int>(cl.block_rank());
+  const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int G4 = (G + 1) / 2;
+  const int per_warp = max_bins * 2 * GROUP;   // float2 cells of one warp histogram
+  float2* hist_all = reinterpret_cast<float2*>(l4sh);
+  float2* my = hist_all + static_cast<int64_t>(warp) * per_warp;
+  unsigned char* stages = l4sh + static_cast<size_t>(W) * per_warp * sizeof(float2);
+  unsigned char* my_stage = stages + static_cast<size_t>(warp) * LH_STAGES * LH_ROWS * GROUP;
+  float2* my_gh = reinterpret_cast<float2*>(stages + static_cast<size_t>(W) * LH_STAGES * LH_ROWS * GROUP) +
+                  warp * LH_ROWS;
+  const uint32_t stage_s = static_cast<uint32_t>(__cvta_generic_to_shared(my_stage));
+  const uint32_t hbase_lo = static_cast<uint32_t>(__cvta_generic_to_shared(my + lane));
+  const uint32_t hbase_hi = hbase_lo + GROUP * 8u;
+  const uint32_t bin_stride = 2u * GROUP * 8u;   // bytes between bins of one column
+  const int maxb1 = max_bins - 1;
+  const float2* peer0[MAX_CS];
+  for (int r = 0; r < cs && r < MAX_CS; ++r) peer0[r] = cl.map_shared_rank(hist_all, r);
+  const int total_items = plan->total_units * G4;
+  const int n_small = plan->n_small;
+  for (int item = cid; item < total_items; item += ncl) {
+    const int unit = item / G4, q4 = item - unit * G4;
+    int lo = 0, hi = n_small - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (plan->unit_begin[mid] <= unit) lo = mid; else hi = mid - 1;
+    }
+    const int jj = lo;
+    const int chunk = unit - plan->unit_begin[jj];
+    const int seg_s = plan->seg_start[jj], seg_c = plan->seg_cnt[jj];
+    const int cr = plan->chunk_rows[jj];
+    const int p0 = seg_s + (chunk * cs + rank) * cr;
+    const int p1 = min(seg_s + seg_c, p0 + cr);
+    {
+      float4* z = reinterpret_cast<float4*>(my);
+      for (int i = lane; i < per_warp / 2; i += 32) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    const int nblk = p1 > p0 ? (p1 - p0 + LH_ROWS - 1) / LH_ROWS : 0;
+    const int my_blocks = nblk > warp ? (nblk - warp + W - 1) / W : 0;
+    const bool act_lo = lane < F - q4 * 2 * GROUP;            // lanes of padding features do no updates
+    const bool act_hi = lane < F - q4 * 2 * GROUP - GROUP;
+    const uint8_t* gb = bins4 + static_cast<int64_t>(q4) * n * GROUP;
+    if (my_blocks > 0) {
+      uint32_t rid[LH_AHEAD + 1];
+      float gr[LH_AHEAD + 1], hr[LH_AHEAD + 1];
+      auto fetch = [&](int j, uint32_t& row, float& gv, float& hv) {
+        const int pos = p0 + (warp + j * W) * LH_ROWS + lane;
+        if (j < my_blocks && pos < p1) {
+          row = order ? __ldg(order + pos) : static_cast<uint32_t>(pos);
+          gv = cbgd::load_gh(gpos, pos);
+          hv = cbgd::load_gh(hpos, pos);
+        } else {
+          row = NONE;   // a row past the end: zero record, zero (g, h)
+          gv = 0.f;
+          hv = 0.f;
+        }
+      };
+      auto copy_bins = [&](int j, uint32_t row) {
+        const uint32_t dst = stage_s + static_cast<uint32_t>(((j % LH_STAGES) * LH_ROWS + lane) * GROUP);
+        if (row != NONE) {
+          const uint8_t* src = gb + static_cast<int64_t>(row) * GROUP;
+          cp_async16(dst, src);
+          cp_async16(dst + 16, src + 16);
+        } else {
+          asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n\tst.shared.v4.u32 [%2], {%1, %1, %1, %1};" ::"r"(dst),
+                       "r"(0u), "r"(dst + 16u)
+                       : "memory");
+        }
+      };
+#pragma unroll
+      for (int q = 0; q < LH_AHEAD; ++q) fetch(q, rid[q], gr[q], hr[q]);
+      copy_bins(0, rid[0]);
+      cp_async_commit();
+      if (1 < my_blocks) copy_bins(1, rid[1]);
+      cp_async_commit();
+      for (int j = 0; j < my_blocks; ++j) {
+        fetch(j + LH_AHEAD, rid[LH_AHEAD], gr[LH_AHEAD], hr[LH_AHEAD]);
+        if (j + 2 < my_blocks) copy_bins(j + 2, rid[2]);
+        cp_async_commit();
+        my_gh[lane] = make_float2(gr[0], hr[0]);
+        cp_async_wait<2>();
+        __syncwarp();
+        const unsigned char* sb = my_stage + (j % LH_STAGES) * LH_ROWS * GROUP + lane;
+        const float4* gh4 = reinterpret_cast<const float4*>(my_gh);
+#pragma unroll
+        for (int s0 = 0; s0 < LH_ROWS; s0 += L4_SUB) {
+          uint32_t alo[L4_SUB], ahi[L4_SUB];
+#pragma unroll
+          for (int i = 0; i < L4_SUB; ++i) {
+            const unsigned byte = sb[(s0 + i) * GROUP];
+            alo[i] = hbase_lo + static_cast<uint32_t>(min(static_cast<int>(byte & 15u), maxb1)) * bin_stride;
+            ahi[i] = hbase_hi + static_cast<uint32_t>(min(static_cast<int>(byte >> 4), maxb1)) * bin_stride;
+          }
+          // one update chain per nibble, each with the lane kernel's store forwarding
+          auto chain = [&](const uint32_t* a) {
+            float2 v[LH_FWD];
+#pragma unroll
+            for (int i = 0; i < LH_FWD; ++i) v[i] = lds_f2(a[i]);
+            float2 nw[LH_FWD];
+#pragma unroll
+            for (int i = 0; i < L4_SUB; ++i) {
+              float2 nxt = make_float2(0.f, 0.f);
+              if (i + LH_FWD < L4_SUB) nxt = lds_f2(a[i + LH_FWD]);
+              float2 cur = v[i % LH_FWD];
+#pragma unroll
+              for (int q = LH_FWD; q >= 1; --q)
+                if (i - q >= 0 && a[i] == a[i - q]) cur = nw[(i - q) % LH_FWD];
+              const int row = s0 + i;
+              const float4 gq = gh4[row >> 1];
+              cur.x += (row & 1) ? gq.z : gq.x;
+              cur.y += (row & 1) ? gq.w : gq.y;
+              sts_f2(a[i], cur);
+              nw[i % LH_FWD] = cur;
+              v[i % LH_FWD] = nxt;
+            }
+          };
+          if (act_lo) chain(alo);
+          if (act_hi) chain(ahi);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < LH_AHEAD; ++q) {
+          rid[q] = rid[q + 1];
+          gr[q] = gr[q + 1];
+          hr[q] = hr[q + 1];
+        }
+      }
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    // the CTA's warps, summed in warp order into warp 0's histogram
+    if (W > 1) {
+      for (int e = threadIdx.x; e < per_warp; e += blockDim.x) {
+        float2 s = hist_all[e];
+        for (int w = 1; w < W; ++w) {
+          const float2 v = hist_all[static_cast<int64_t>(w) * per_warp + e];
+          s.x += v.x;
+          s.y += v.y;
+        }
+        hist_all[e] = s;
+      }
+    }
+    cl.sync();
+    // this CTA's slice of bins, summed over the cluster's CTAs in rank order, written as
+    // the partials of uint8 groups 2 q4 and 2 q4 + 1
+    const int bs = (max_bins + cs - 1) / cs;
+    const int b0 = rank * bs;
+    const int nbs = max(0, min(max_bins, b0 + bs) - b0);
+    for (int i = threadIdx.x; i < nbs * 2 * GROUP; i += blockDim.x) {
+      const int b = b0 + i / (2 * GROUP), half = (i / GROUP) & 1, col = i & (GROUP - 1);
+      const int grp = 2 * q4 + half;
+      if (grp >= G) continue;
+      const int e = (b * 2 + half) * GROUP + col;
+      float sx = 0.f, sy = 0.f;
+      for (int r = 0; r < cs; ++r) {
+        const float2 v = peer0[r][e];
+        sx += v.x;
+        sy += v.y;
+      }
+      float* dst = partials + (static_cast<int64_t>(unit) * G + grp) * (2 * max_bins * GROUP);
+      dst[b * GROUP + col] = sx;
+      dst[max_bins * GROUP + b * GROUP + col] = sy;
+    }
+    cl.sync();
+  }
+}
+
+// bins4[q][r][i] = bins[2q][r][i] | bins[2q+1][r][i] << 4 (the second group read as 0 past
+// the last one); every bin must be below 16.
+__global__ void pack_bins4_kernel(const uint8_t* __restrict__ bins, int64_t n, int G, uint8_t* __restrict__ bins4,
+                                  unsigned int* __restrict__ status) {
+  const int G4 = (G + 1) / 2;
+  const int64_t total = static_cast<int64_t>(G4) * n * 2;   // 16-byte halves of the packed records
+  bool bad = false;
+  for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+       x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t rec = x >> 1, q = rec / n, r = rec - q * n;
+    const int half = static_cast<int>(x & 1);
+    const uint4 lo = reinterpret_cast<const uint4*>(bins)[((2 * q) * n + r) * 2 + half];
+    uint4 hi = make_uint4(0u, 0u, 0u, 0u);
+    if (2 * q + 1 < G) hi = reinterpret_cast<const uint4*>(bins)[((2 * q + 1) * n + r) * 2 + half];
+    bad |= ((lo.x | lo.y | lo.z | lo.w | hi.x | hi.y | hi.z | hi.w) & 0xf0f0f0f0u) != 0u;
+    // bytes of lo stay in the low nibbles, bytes of hi move to the high nibbles
+    reinterpret_cast<uint4*>(bins4)[x] = make_uint4(lo.x | (hi.x << 4), lo.y | (hi.y << 4), lo.z | (hi.z << 4),
+                                                    lo.w | (hi.w << 4));
+  }
+  if (bad) atomicOr(status, ::cbg::STATUS_NONFINITE);
+}
+
 // ---------------------------------------- lane-per-feature, one statistic per warp
 // The lane kernel with G and H split over a pair of warps: warp 2p accumulates G and warp
 // 2p + 1 accumulates H of the same rows, each in a private FP32 histogram [max_bins][32]
@@ -1046,14 +1271,17 @@ cbg_status wp_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   return CBG_OK;
 }
 
-// Geometry of the lane-per-feature kernels (PAIR: one statistic per warp): one CTA per SM
+// Geometry of the lane-per-feature kernels (V: 0 one warp per 32 features, 1 one statistic
+// per warp, 2 the 4-bit packed records): one CTA per SM
 // with as many warp histograms as fit, and the cluster size (<= the requested one) that
 // keeps the most CTAs resident.
-template <typename GH, bool PAIR>
+template <typename GH, int V>
 cbg_status lane_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   static std::mutex mu;
   static std::map<std::tuple<int, int, int, int, int>, HistGeom> cache;
-  const int warps = PAIR ? lp_warps(L.max_bins, L.threads) : lh_warps(L.max_bins, L.threads);
+  const int warps = V == 1 ? lp_warps(L.max_bins, L.threads)
+                  : V == 2 ? l4_warps(L.max_bins, L.threads)
+                           : lh_warps(L.max_bins, L.threads);
   const auto key = std::make_tuple(ctx->device, L.max_bins, warps, L.cluster, static_cast<int>(sizeof(GH)));
   {
     std::lock_guard<std::mutex> lk(mu);
@@ -1063,8 +1291,10 @@ cbg_status lane_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
       return CBG_OK;
     }
   }
-  auto kern = PAIR ? level_hist_pair_kernel<GH> : level_hist_lane_kernel<GH>;
-  const size_t smem = PAIR ? lp_smem_bytes(L.max_bins, warps) : lh_smem_bytes(L.max_bins, warps);
+  auto kern = V == 1 ? level_hist_pair_kernel<GH> : V == 2 ? level_hist_lane4_kernel<GH> : level_hist_lane_kernel<GH>;
+  const size_t smem = V == 1   ? lp_smem_bytes(L.max_bins, warps)
+                      : V == 2 ? l4_smem_bytes(L.max_bins, warps)
+                               : lh_smem_bytes(L.max_bins, warps);
   CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   HistGeom geom;
   for (int cs = L.cluster; cs >= 1; cs >>= 1) {
@@ -1102,8 +1332,9 @@ cbg_status lane_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
 cbg_status hist_cluster_size(cbg_ctx* ctx, const HistConfig& L, int* cs) {
   HistGeom g;
   cbg_status st = L.kind == 0   ? wp_geom<float>(ctx, L, &g)
-                  : L.kind == 4 ? lane_geom<float, false>(ctx, L, &g)
-                  : L.kind == 5 ? lane_geom<float, true>(ctx, L, &g)
+                  : L.kind == 4 ? lane_geom<float, 0>(ctx, L, &g)
+                  : L.kind == 5 ? lane_geom<float, 1>(ctx, L, &g)
+                  : L.kind == 6 ? lane_geom<float, 2>(ctx, L, &g)
                                 : hist_geom<float>(ctx, L, &g);
   if (st != CBG_OK) return st;
   *cs = g.cs;
@@ -1116,8 +1347,9 @@ template <typename GH>
 cbg_status hist_warm(cbg_ctx* ctx, const HistConfig& L) {
   HistGeom g;
   cbg_status st = L.kind == 0   ? wp_geom<GH>(ctx, L, &g)
-                  : L.kind == 4 ? lane_geom<GH, false>(ctx, L, &g)
-                  : L.kind == 5 ? lane_geom<GH, true>(ctx, L, &g)
+                  : L.kind == 4 ? lane_geom<GH, 0>(ctx, L, &g)
+                  : L.kind == 5 ? lane_geom<GH, 1>(ctx, L, &g)
+                  : L.kind == 6 ? lane_geom<GH, 2>(ctx, L, &g)
                                 : hist_geom<GH>(ctx, L, &g);
   if (st != CBG_OK) return st;
   int cs = 1;
@@ -1269,17 +1501,21 @@ cbg_status launch_hist(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins, c
                                      L.max_bins, partials));
     return CBG_OK;
   }
-  if (L.kind == 4 || L.kind == 5) {
-    const bool pair = L.kind == 5;
+  if (L.kind == 4 || L.kind == 5 || L.kind == 6) {
+    const bool pair = L.kind == 5, packed = L.kind == 6;
     HistGeom geom;
-    st = pair ? lane_geom<GH, true>(ctx, L, &geom) : lane_geom<GH, false>(ctx, L, &geom);
+    st = pair ? lane_geom<GH, 1>(ctx, L, &geom) : packed ? lane_geom<GH, 2>(ctx, L, &geom) : lane_geom<GH, 0>(ctx, L, &geom);
     if (st != CBG_OK) return st;
     if (geom.cs != cs) return ::cbg::fail(ctx, CBG_ECUDA, "histogram cluster size changed between plan and launch");
-    const int warps = pair ? lp_warps(L.max_bins, L.threads) : lh_warps(L.max_bins, L.threads);
+    const int warps = pair ? lp_warps(L.max_bins, L.threads)
+                    : packed ? l4_warps(L.max_bins, L.threads)
+                             : lh_warps(L.max_bins, L.threads);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(geom.cs * geom.clusters));
     cfg.blockDim = dim3(static_cast<unsigned>(32 * warps));
-    cfg.dynamicSmemBytes = pair ? lp_smem_bytes(L.max_bins, warps) : lh_smem_bytes(L.max_bins, warps);
+    cfg.dynamicSmemBytes = pair ? lp_smem_bytes(L.max_bins, warps)
+                         : packed ? l4_smem_bytes(L.max_bins, warps)
+                                  : lh_smem_bytes(L.max_bins, warps);
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1288,8 +1524,12 @@ cbg_status launch_hist(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins, c
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, pair ? level_hist_pair_kernel<GH> : level_hist_lane_kernel<GH>, bins, L.n,
-                                     L.G, L.F, order, gg, hh, plan, L.max_bins, partials));
+    // for the packed kernel `bins` is the 4-bit layout (bins4)
+    CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg,
+                                     pair     ? level_hist_pair_kernel<GH>
+                                     : packed ? level_hist_lane4_kernel<GH>
+                                              : level_hist_lane_kernel<GH>,
+                                     bins, L.n, L.G, L.F, order, gg, hh, plan, L.max_bins, partials));
     return CBG_OK;
   }
   if (L.kind == 3) {

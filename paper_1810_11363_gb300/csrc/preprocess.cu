@@ -3,6 +3,7 @@
 // features").
 #include "cbg_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 using namespace cbg;
@@ -55,22 +56,27 @@ __global__ void prior_final_kernel(const double* __restrict__ partial, int npart
 }
 
 // ------------------------------------------------------------ ordered TS
-__global__ void ts_gather_kernel(const uint32_t* __restrict__ cat_col, const uint32_t* __restrict__ perm,
-                                 int64_t n, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
-       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+// Several columns at once: element i = c n + p holds column c at permutation position p,
+// keyed (c << 32) | id. A stable sort by key keeps positions in order within every
+// (column, category) group, so a segmented scan over the sorted elements gives, for every
+// element, the count and label sum of the earlier positions of its group.
+__global__ void ts_gather_kernel(const uint32_t* __restrict__ cat, const uint32_t* __restrict__ perm, int64_t n,
+                                 int64_t total, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t c = i / n, p = i - c * n;
     const uint32_t r = perm[p];
-    keys[p] = r < n ? cat_col[r] : 0u;
-    vals[p] = static_cast<uint32_t>(p);
+    keys[i] = (static_cast<uint64_t>(c) << 32) | (r < n ? cat[c * n + r] : 0u);
+    vals[i] = static_cast<uint32_t>(p);
   }
 }
 
-// Sorted by (category, position): mark segment heads and fetch each element's label.
-__global__ void ts_heads_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+// Sorted by (column, category, position): mark group heads and fetch each element's label.
+__global__ void ts_heads_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                                 const uint32_t* __restrict__ perm, const float* __restrict__ y, int64_t n,
-                                int label_kind, uint8_t* __restrict__ heads, double* __restrict__ lab,
+                                int64_t total, int label_kind, uint8_t* __restrict__ heads, double* __restrict__ lab,
                                 unsigned int* __restrict__ status) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     heads[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
     const uint32_t r = perm[vals[i]];
@@ -80,14 +86,15 @@ __global__ void ts_heads_kernel(const uint32_t* __restrict__ keys, const uint32_
   }
 }
 
-// Eq. 1: (S + a*P) / (N + a), FP64 without contraction, rounded to float, scattered to rows.
-__global__ void ts_final_kernel(const uint8_t* __restrict__ heads, const uint32_t* __restrict__ incl_cnt,
-                                const double* __restrict__ incl_sum, const uint32_t* __restrict__ vals,
-                                const uint32_t* __restrict__ perm, int64_t n, double prior, double a,
-                                int label_kind, float* __restrict__ ts, uint32_t* __restrict__ cnt_before,
-                                void* __restrict__ sum_before) {
+// Eq. 1: (S + a*P) / (N + a), FP64 without contraction, rounded to float, scattered to
+// rows of the element's column.
+__global__ void ts_final_kernel(const uint64_t* __restrict__ keys, const uint8_t* __restrict__ heads,
+                                const uint32_t* __restrict__ incl_cnt, const double* __restrict__ incl_sum,
+                                const uint32_t* __restrict__ vals, const uint32_t* __restrict__ perm, int64_t n,
+                                int64_t total, double prior, double a, int label_kind, float* __restrict__ ts,
+                                uint32_t* __restrict__ cnt_before, void* __restrict__ sum_before) {
   const double aP = __dmul_rn(a, prior);
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     uint32_t N = incl_cnt[i] - 1u;
     double S = heads[i] ? 0.0 : incl_sum[i - 1];
@@ -95,18 +102,18 @@ __global__ void ts_final_kernel(const uint8_t* __restrict__ heads, const uint32_
     double den = __dadd_rn(static_cast<double>(N), a);
     uint32_t row = perm[vals[i]];
     if (row >= n) continue;
-    ts[row] = __double2float_rn(__ddiv_rn(num, den));
-    if (cnt_before) cnt_before[row] = N;
+    const int64_t at = static_cast<int64_t>(keys[i] >> 32) * n + row;
+    ts[at] = __double2float_rn(__ddiv_rn(num, den));
+    if (cnt_before) cnt_before[at] = N;
     if (sum_before) {
       if (label_kind == CBG_LABEL_BINARY)
-        static_cast<uint32_t*>(sum_before)[row] = static_cast<uint32_t>(S);
+        static_cast<uint32_t*>(sum_before)[at] = static_cast<uint32_t>(S);
       else
-        static_cast<double*>(sum_before)[row] = S;
+        static_cast<double*>(sum_before)[at] = S;
     }
   }
 }
 
-// ----------------------------------------------------------------- borders
 __global__ void border_keys_kernel(const float* __restrict__ x, int64_t n, int64_t total,
                                    uint64_t* __restrict__ keys, unsigned int* __restrict__ status) {
   bool bad = false;
@@ -272,38 +279,46 @@ cbg_status cbg_ordered_ts(cbg_ctx* ctx, const uint32_t* cat, const float* y, int
   if (C == 0) return CBG_OK;
   CBG_REQUIRE(ctx, cat && y && perm && ts, "NULL argument");
   DeviceGuard guard(ctx->device);
-  size_t need = 4 * (n * sizeof(uint32_t) + 256) + (n + 256) + 2 * (n * sizeof(double) + 256) +
-                (n * sizeof(uint32_t) + 256) + radix_temp_bytes(n) + segscan_temp_bytes(n) + 512;
+  // columns in chunks of at most 2^26 elements, each chunk sorted once by (column, id)
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(C, (int64_t(1) << 26) / n));
+  const int64_t cap = chunk * n;
+  int cbits = 0;
+  while ((int64_t(1) << cbits) < chunk) ++cbits;
+  size_t need = 2 * (cap * sizeof(uint64_t) + 256) + 2 * (cap * sizeof(uint32_t) + 256) + (cap + 256) +
+                2 * (cap * sizeof(double) + 256) + (cap * sizeof(uint32_t) + 256) + radix_temp_bytes(cap) +
+                segscan_temp_bytes(cap) + 512;
   cbg_status st = ws_reserve(ctx, need);
   if (st != CBG_OK) return st;
   Carve cv(ctx->ws);
-  uint32_t* ka = cv.take<uint32_t>(n);
-  uint32_t* kb = cv.take<uint32_t>(n);
-  uint32_t* va = cv.take<uint32_t>(n);
-  uint32_t* vb = cv.take<uint32_t>(n);
-  uint8_t* heads = cv.take<uint8_t>(n);
-  double* lab = cv.take<double>(n);
-  double* isum = cv.take<double>(n);
-  uint32_t* icnt = cv.take<uint32_t>(n);
-  void* rtmp = cv.take<char>(radix_temp_bytes(n));
-  void* stmp = cv.take<char>(segscan_temp_bytes(n));
-  for (int c = 0; c < C; ++c) {
-    const int64_t off = static_cast<int64_t>(c) * n;
-    ts_gather_kernel<<<grid_for(n), BLOCK, 0, ctx->stream>>>(cat + off, perm, n, ka, va);
+  uint64_t* ka = cv.take<uint64_t>(cap);
+  uint64_t* kb = cv.take<uint64_t>(cap);
+  uint32_t* va = cv.take<uint32_t>(cap);
+  uint32_t* vb = cv.take<uint32_t>(cap);
+  uint8_t* heads = cv.take<uint8_t>(cap);
+  double* lab = cv.take<double>(cap);
+  double* isum = cv.take<double>(cap);
+  uint32_t* icnt = cv.take<uint32_t>(cap);
+  void* rtmp = cv.take<char>(radix_temp_bytes(cap));
+  void* stmp = cv.take<char>(segscan_temp_bytes(cap));
+  for (int64_t c0 = 0; c0 < C; c0 += chunk) {
+    const int64_t cc = std::min<int64_t>(chunk, C - c0);
+    const int64_t total = cc * n, off = c0 * n;
+    ts_gather_kernel<<<grid_for(total), BLOCK, 0, ctx->stream>>>(cat + off, perm, n, total, ka, va);
     CBG_CHECK_LAUNCH(ctx);
-    st = radix_sort_u32(ctx, ka, kb, va, vb, n, 32, rtmp);
+    st = radix_sort_u64(ctx, ka, kb, va, vb, total, 32 + cbits, rtmp);
     if (st != CBG_OK) return st;
-    ts_heads_kernel<<<grid_for(n), BLOCK, 0, ctx->stream>>>(ka, va, perm, y, n, label_kind, heads, lab,
-                                                           ctx->d_status);
+    ts_heads_kernel<<<grid_for(total), BLOCK, 0, ctx->stream>>>(ka, va, perm, y, n, total, label_kind, heads, lab,
+                                                               ctx->d_status);
     CBG_CHECK_LAUNCH(ctx);
-    st = segscan_cnt_sum(ctx, heads, lab, n, icnt, isum, stmp);
+    st = segscan_cnt_sum(ctx, heads, lab, total, icnt, isum, stmp);
     if (st != CBG_OK) return st;
     void* sb = nullptr;
     if (sum_before)
       sb = label_kind == CBG_LABEL_BINARY ? static_cast<void*>(static_cast<uint32_t*>(sum_before) + off)
                                           : static_cast<void*>(static_cast<double*>(sum_before) + off);
-    ts_final_kernel<<<grid_for(n), BLOCK, 0, ctx->stream>>>(heads, icnt, isum, va, perm, n, prior, a, label_kind,
-                                                           ts + off, cnt_before ? cnt_before + off : nullptr, sb);
+    ts_final_kernel<<<grid_for(total), BLOCK, 0, ctx->stream>>>(ka, heads, icnt, isum, va, perm, n, total, prior, a,
+                                                               label_kind, ts + off,
+                                                               cnt_before ? cnt_before + off : nullptr, sb);
     CBG_CHECK_LAUNCH(ctx);
   }
   return CBG_OK;

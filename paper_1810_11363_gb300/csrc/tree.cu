@@ -83,11 +83,12 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
   L->nb_alloc = pow2_at_least(L->max_bins);
   L->D = s->max_depth;
   CBG_REQUIRE(ctx, t.cluster >= 0 && t.cluster <= 16, "cluster must be in [0, 16]");
-  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 5, "kernel must be 0 (default), 1 (shared reductions), 2 "
-              "(warp-private, 16 features per warp), 3 (64-bit compare-and-swap), 4 (lane per feature) or 5 (lane "
-              "per feature, one statistic per warp)");
+  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 6, "kernel must be 0 (default), 1 (shared reductions), 2 "
+              "(warp-private, 16 features per warp), 3 (64-bit compare-and-swap), 4 (lane per feature), 5 (lane "
+              "per feature, one statistic per warp) or 6 (lane per feature over 4-bit packed bins)");
+  CBG_REQUIRE(ctx, t.kernel != 6 || s->max_bins <= 16, "the 4-bit packed kernel needs max_bins <= 16");
   L->kind = t.kernel == 2 ? 0 : (t.kernel >= 3 ? t.kernel : 1);
-  const bool lane_kind = L->kind == 4 || L->kind == 5;
+  const bool lane_kind = L->kind == 4 || L->kind == 5 || L->kind == 6;
   L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : (lane_kind ? 8192 : 2048);
   L->cluster = t.cluster > 0 ? t.cluster : (lane_kind ? 2 : 8);
   L->threads = t.threads > 0 ? t.threads : 512;
@@ -1092,6 +1093,8 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   CBG_REQUIRE(ctx, a->bins && a->n_borders && a->g && a->h && a->leaf && a->splits && a->child_totals, "NULL argument");
   CBG_REQUIRE(ctx, (L.kind != 4 && L.kind != 5) || (reinterpret_cast<uintptr_t>(a->bins) & 15) == 0,
               "bins must be 16-byte aligned for the lane-per-feature histogram kernel");
+  CBG_REQUIRE(ctx, L.kind != 6 || (a->bins4 != nullptr && (reinterpret_cast<uintptr_t>(a->bins4) & 15) == 0),
+              "the 4-bit packed histogram kernel needs bins4 (16-byte aligned, cbg_pack_bins4)");
   CBG_REQUIRE(ctx, a->gh_dtype == CBG_F32 || a->gh_dtype == CBG_BF16, "bad gh_dtype");
   CBG_REQUIRE(ctx, a->l2 >= 0.0 && std::isfinite(a->l2), "l2 must be finite and >= 0");
   CBG_REQUIRE(ctx, a->force_feature < L.F, "force_feature out of range");
@@ -1125,7 +1128,8 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   // the lane-per-feature kernels read (g, h) by position: the caller's arrays at the root
   // (positions are rows), then the copies the previous level's partition moved along (for
   // the shared-reduction kernel the copy costs the partition more than it saves)
-  const bool by_pos = L.kind == 4 || L.kind == 5;
+  const bool by_pos = L.kind == 4 || L.kind == 5 || L.kind == 6;
+  const uint8_t* hist_bins = L.kind == 6 ? a->bins4 : a->bins;
   const void* g_pos = d == 0 ? a->g : at<char>(S, d % 2 == 1 ? L.o_gp_a : L.o_gp_b);
   const void* h_pos = d == 0 ? a->h : at<char>(S, d % 2 == 1 ? L.o_hp_a : L.o_hp_b);
   void* g_pos_nxt = at<char>(S, (d + 1) % 2 == 1 ? L.o_gp_a : L.o_gp_b);
@@ -1134,8 +1138,8 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   const void* h_hist = by_pos ? h_pos : a->h;
   if (do_hist) {
     st = a->gh_dtype == CBG_F32
-             ? launch_hist<float>(ctx, hist_config(L), a->bins, order_cur, g_hist, h_hist, plan, partials)
-             : launch_hist<__nv_bfloat16>(ctx, hist_config(L), a->bins, order_cur, g_hist, h_hist, plan, partials);
+             ? launch_hist<float>(ctx, hist_config(L), hist_bins, order_cur, g_hist, h_hist, plan, partials)
+             : launch_hist<__nv_bfloat16>(ctx, hist_config(L), hist_bins, order_cur, g_hist, h_hist, plan, partials);
     if (st != CBG_OK) return st;
     st = prof_end(ctx, ev1);
     if (st != CBG_OK) return st;
@@ -1263,6 +1267,7 @@ cbg_status boost_one_tree(cbg_ctx* ctx, const cbg_boost_args* a, cbg_split* sp, 
     la.child_totals = a->child_totals;
     la.hist_out = nullptr;
     la.last_level = d == D - 1;
+    la.bins4 = a->bins4;
     st = cbg_build_level(ctx, &la);
     if (st != CBG_OK) return st;
   }
@@ -1673,14 +1678,31 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
 
 }  // extern "C"
 
+cbg_status cbg_pack_bins4(cbg_ctx* ctx, const uint8_t* bins, int64_t n, int32_t F_pad, uint8_t* bins4) {
+  if (!ctx) return CBG_EINVAL;
+  CBG_REQUIRE(ctx, n >= 1 && n <= INT32_MAX, "n must be in [1, 2^31-1]");
+  CBG_REQUIRE(ctx, F_pad >= GROUP && F_pad % GROUP == 0, "F_pad must be a positive multiple of 32");
+  CBG_REQUIRE(ctx, bins && bins4, "NULL argument");
+  CBG_REQUIRE(ctx, ((reinterpret_cast<uintptr_t>(bins) | reinterpret_cast<uintptr_t>(bins4)) & 15) == 0,
+              "bins and bins4 must be 16-byte aligned");
+  DeviceGuard guard(ctx->device);
+  const int G = F_pad / GROUP;
+  pack_bins4_kernel<<<grid_stride_blocks(static_cast<int64_t>((G + 1) / 2) * n * 2, 256), 256, 0, ctx->stream>>>(
+      bins, n, G, bins4, ctx->d_status);
+  CBG_CHECK_LAUNCH(ctx);
+  return CBG_OK;
+}
+
 // ------------------------------------------------------------------ autotuner
 namespace {
 
 // The tilings the autotuner times: the shared-reduction kernel with clusters of 1, 2, 4
 // or 8 and 2048 or 4096 rows per CTA of a unit; the lane-per-feature kernel with clusters of 2
 // and 8192 or 16384 rows; its one-statistic-per-warp form with clusters of 2 or 4 and
-// 8192 or 16384 rows; the 16-feature warp-private kernel once.
-std::vector<cbg_tiles> autotune_candidates() {
+// 8192 or 16384 rows; the 16-feature warp-private kernel once; with 4-bit packed bins
+// (at most 16 bins), the packed lane-per-feature kernel with clusters of 2 and 8192 or
+// 16384 rows.
+std::vector<cbg_tiles> autotune_candidates(bool packed) {
   std::vector<cbg_tiles> c;
   auto add = [&](int kernel, int cluster, int rows) {
     cbg_tiles t{};
@@ -1695,6 +1717,8 @@ std::vector<cbg_tiles> autotune_candidates() {
   for (int cl : {2, 4})
     for (int r : {8192, 16384}) add(5, cl, r);
   add(2, 2, 8192);
+  if (packed)
+    for (int r : {8192, 16384}) add(6, 2, r);
   return c;
 }
 
@@ -1720,6 +1744,7 @@ cbg_status tune_tree(cbg_ctx* ctx, const cbg_tree_shape* s, const cbg_autotune_a
     la.splits = a->splits;
     la.child_totals = a->child_totals;
     la.last_level = d == a->depth - 1;
+    la.bins4 = a->bins4;
     st = cbg_build_level(ctx, &la);
     if (st != CBG_OK) return st;
   }
@@ -1731,7 +1756,7 @@ cbg_status tune_tree(cbg_ctx* ctx, const cbg_tree_shape* s, const cbg_autotune_a
 cbg_status cbg_autotune_state_bytes(const cbg_tree_shape* shape, size_t* bytes) {
   if (!shape || !bytes) return CBG_EINVAL;
   size_t mx = 0;
-  for (const cbg_tiles& t : autotune_candidates()) {
+  for (const cbg_tiles& t : autotune_candidates(shape->max_bins <= 16)) {
     cbg_tree_shape s = *shape;
     s.tiles = t;
     Layout L;
@@ -1762,7 +1787,7 @@ cbg_status cbg_autotune_tiles(cbg_ctx* ctx, const cbg_autotune_args* a, cbg_tile
   double best_t = INFINITY;
   cbg_tiles best_c{};
   cbg_status result = CBG_OK;
-  for (const cbg_tiles& cand : autotune_candidates()) {
+  for (const cbg_tiles& cand : autotune_candidates(a->bins4 != nullptr && a->shape->max_bins <= 16)) {
     cbg_tree_shape s = *a->shape;
     s.tiles = cand;
     Layout L;

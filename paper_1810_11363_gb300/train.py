@@ -43,6 +43,7 @@ class Prepared:
     bins: object
     bins_t: object
     max_bins: int
+    bins4: object = None   # 4-bit packed bins (cbg_pack_bins4) when max_bins <= 16
 
 
 def preprocess(ctx: cbg.Context, x, cat, y, label_kind: str, max_borders: int, a: float = 1.0,
@@ -79,7 +80,11 @@ def preprocess(ctx: cbg.Context, x, cat, y, label_kind: str, max_borders: int, a
         cbg.cbg_quantize(ctx, ts, n, Cc, borders[Ff:], nb[Ff:], max_borders, bins, F_pad, Ff, bins_t)
     cbg.cbg_sync(ctx)
     max_bins = int(nb.max().item()) + 1
-    return Prepared(n, F, Ff, F_pad, perm, prior, ts, borders, nb, bins, bins_t, max_bins)
+    bins4 = None
+    if max_bins <= 16:
+        bins4 = torch.empty(((F_pad // 32 + 1) // 2) * 32 * n, dtype=torch.uint8, device=dev)
+        cbg.cbg_pack_bins4(ctx, bins, n, F_pad, bins4)
+    return Prepared(n, F, Ff, F_pad, perm, prior, ts, borders, nb, bins, bins_t, max_bins, bins4)
 
 
 @dataclass
@@ -132,7 +137,7 @@ def fit(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, trees: int, 
         bufs = alloc_fit(prep, depth, trees, gh_dtype, tiles)
     cbg.cbg_boost(ctx, bufs.shape, bufs.state, prep.bins, prep.n_borders, y, loss, gh_dtype, depth, trees, lr,
                   l2, bufs.pred, bufs.g, bufs.h, bufs.leaf, bufs.splits, bufs.leaf_values, bufs.child_totals,
-                  bins_t=prep.bins_t, use_graph=use_graph)
+                  bins_t=prep.bins_t, use_graph=use_graph, bins4=prep.bins4)
     return Model(bufs.splits[:trees], bufs.leaf_values[:trees], bufs.pred, depth, lr)
 
 
@@ -231,6 +236,53 @@ def fit_combos(ctx: cbg.Context, prep: Prepared, cat, y, label_kind: str, loss: 
     return CombosModel(model, items[:trees], nb[:trees], borders[:trees])
 
 
+def predict_combos(ctx: cbg.Context, cm: CombosModel, prep: Prepared, cat, y, label_kind: str, bins_t_new, cat_new,
+                   a: float = 1.0, max_borders: int | None = None):
+    """Model value of new rows for a model with combination splits. Every combination the
+    model uses becomes one extra column of the new rows: its full-data statistic (Eq. 1 with
+    every training row before the new ones) from the training rows' combination values
+    (cat [C][n], prep.bins_t, y), applied to the new rows' values (cat_new [C][m],
+    bins_t_new [F][m]) and quantised with the combination's borders. The model's combination
+    splits are renumbered to those columns and cbg_predict scores the rows.
+    Returns float32 [m]."""
+    import torch
+    dev = bins_t_new.device
+    F, m, n = prep.F, int(bins_t_new.shape[1]), prep.n
+    C_ = F - prep.F_float
+    mb = max_borders or cm.combo_borders.shape[-1]
+    sp = cm.model.host_splits().copy()
+    T, D = sp.shape
+    cols = {}
+    for t in range(T):
+        for d in range(D):
+            if sp[t, d]["feature"] >= F:
+                key = tuple(tuple(int(v) for v in it) for it in cm.combo_items[t, d] if it[0] >= 0)
+                if key not in cols:
+                    cols[key] = (len(cols), t, d)
+                sp[t, d]["feature"] = F + cols[key][0]
+    K = len(cols)
+    ext = torch.empty((F + K, m), dtype=torch.uint8, device=dev)
+    ext[:F].copy_(bins_t_new)
+    if K:
+        ids_tr = torch.empty(n, dtype=torch.int32, device=dev)
+        ids_new = torch.empty((1, m), dtype=torch.int32, device=dev)
+        scratch = torch.empty(32 * m, dtype=torch.uint8, device=dev)
+        for key, (k, t, d) in cols.items():
+            cbg.cbg_combo_ids(ctx, key, cat, C_, prep.bins_t, F, n, ids_tr)
+            cbg.cbg_combo_ids(ctx, key, cat_new, C_, bins_t_new, F, m, ids_new[0])
+            tables = ts_tables(ctx, ids_tr[None], y, label_kind)
+            ts_new = ts_apply(ctx, tables, ids_new, prep.prior, a)
+            nb = int(cm.combo_nb[t, d])
+            borders = torch.from_numpy(np.ascontiguousarray(cm.combo_borders[t, d, :mb])).to(dev)
+            cbg.cbg_quantize(ctx, ts_new, m, 1, borders, torch.tensor([nb], dtype=torch.int32, device=dev), mb,
+                             scratch, 32, 0, ext[F + k])
+    rec = np.ascontiguousarray(sp).view(np.float64).reshape(T, D, 2)
+    splits = torch.from_numpy(rec.copy()).to(dev)
+    pred = torch.zeros(m, dtype=torch.float32, device=dev)
+    cbg.cbg_predict(ctx, ext, m, F + K, splits, cm.model.leaf_values, T, D, cm.model.lr, pred)
+    return pred
+
+
 def grouped_from_rowmajor(bins_rm: np.ndarray) -> np.ndarray:
     """[n][F_pad] row-major bins -> the library's grouped layout (flat uint8)."""
     n, F_pad = bins_rm.shape
@@ -257,7 +309,7 @@ def autotune(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, l2: flo
     splits = torch.empty((depth, 2), dtype=torch.float64, device=dev)
     child = torch.empty((1 << depth, 2), dtype=torch.float64, device=dev)
     return cbg.cbg_autotune_tiles(ctx, shape, state, prep.bins, prep.n_borders, g, h, gh_dtype, depth, l2, leaf,
-                                  splits, child, bins_t=prep.bins_t, reps=reps)
+                                  splits, child, bins_t=prep.bins_t, reps=reps, bins4=prep.bins4)
 
 
 # Tilings timed on a whole batch: the shared-reduction kernel (whose histograms of a level

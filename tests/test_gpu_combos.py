@@ -99,3 +99,52 @@ def test_max_complexity_one_is_classic_boosting(ctx):
     assert np.array_equal(a["feature"], b["feature"]) and np.array_equal(a["border"], b["border"])
     assert np.allclose(to_host(got.model.pred), to_host(plain.pred), atol=1e-6)
     assert np.all(got.combo_items == -1)
+
+
+def test_new_rows_with_combinations_match_oracle(ctx):
+    """Train with combinations on part of the interaction workload and score the rest: the
+    GPU path (full-data TS of every used combination, quantised with its borders, as extra
+    columns for cbg_predict) against the oracle doing the same steps with its own model."""
+    import dataclasses
+    w = _interaction_workload(24000, seed=3)
+    n_tr = 20000
+    w_tr = dataclasses.replace(w, x=np.ascontiguousarray(w.x[:, :n_tr]), cat=np.ascontiguousarray(w.cat[:, :n_tr]),
+                               y=np.ascontiguousarray(w.y[:n_tr]))
+    x_te, c_te = np.ascontiguousarray(w.x[:, n_tr:]), np.ascontiguousarray(w.cat[:, n_tr:])
+    depth, trees, lr, l2, mb, mc = 4, 3, 0.2, 1.0, 15, 3
+    got, res = _run_both(ctx, w_tr, depth, trees, mb, mc, lr=lr, l2=l2)
+    compared, n_combo = _compare(got, res, w.n_features, depth, trees)
+    if compared < trees:
+        return                      # a near-tie: the models differ from there on
+    assert n_combo >= 1
+    # GPU: the new rows' bins, then the combinations as extra columns
+    prep = train.preprocess(ctx, to_dev(w_tr.x), to_dev(w_tr.cat), to_dev(w_tr.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    tables = train.ts_tables(ctx, to_dev(w_tr.cat), to_dev(w_tr.y), "binary")
+    bins_t_new = train.preprocess_new(ctx, prep, tables, to_dev(x_te), to_dev(c_te), a=w.a)
+    pred = to_host(train.predict_combos(ctx, got, prep, to_dev(w_tr.cat), to_dev(w_tr.y), "binary", bins_t_new,
+                                        to_dev(c_te), a=w.a)).astype(np.float64)
+    cbg.cbg_sync(ctx)
+    # oracle: the same steps on its own preprocessing and model
+    ref = oracle.preprocess(w_tr, prep.F_pad)
+    ts_new = np.stack([oracle.ts_full(w_tr.cat[c], w_tr.y, ref["prior"], w.a, c_te[c]) for c in range(w.n_cat)])
+    F = w.n_features
+    bins_new = oracle.quantize(np.concatenate([x_te, ts_new]), ref["borders"], ref["n_borders"], 64)
+    sf = res["split_f"].copy()
+    cols = {}
+    for t in range(trees):
+        for d in range(depth):
+            if sf[t, d] >= F:
+                key = tuple(tuple(int(v) for v in it) for it in res["combo_items"][t, d] if it[0] >= 0)
+                if key not in cols:
+                    cols[key] = (len(cols), t, d)
+                sf[t, d] = F + cols[key][0]
+    for key, (k, t, d) in cols.items():
+        ids_tr = oracle.combo_ids(key, w_tr.cat, ref["bins"])
+        ids_new = oracle.combo_ids(key, c_te, bins_new)
+        ts = oracle.ts_full(ids_tr, w_tr.y, ref["prior"], w.a, ids_new)
+        nb = res["combo_nb"][t, d]
+        oracle.quantize(ts[None, :], res["combo_borders"][t, d][None, :], np.array([nb], np.int32), 64,
+                        f_offset=F + k, bins=bins_new)
+    ref_pred = oracle.predict(bins_new, sf, res["split_k"], res["leaf_values"], lr)
+    assert np.all(np.abs(pred - ref_pred) <= 1e-4)

@@ -69,6 +69,10 @@ class Tree:
         self.state = torch.empty(cbg.cbg_tree_state_bytes(self.shape), dtype=torch.uint8, device="cuda")
         self.bins = to_dev(train.grouped_from_rowmajor(bins_rm))
         self.bins_t = to_dev(np.ascontiguousarray(bins_rm[:, :self.F].T)) if with_bins_t else None
+        self.bins4 = None
+        if tiles and tiles.get("kernel") == 6:
+            self.bins4 = torch.empty(((F_pad // 32 + 1) // 2) * 32 * n, dtype=torch.uint8, device="cuda")
+            cbg.cbg_pack_bins4(ctx, self.bins, n, F_pad, self.bins4)
         self.nb = to_dev(nb.astype(np.int32))
         tdt = torch.float32 if dtype == "f32" else torch.bfloat16
         self.dtype = dtype
@@ -85,7 +89,7 @@ class Tree:
         hist = torch.empty(((1 << d), self.F, self.max_bins, 2), dtype=torch.float64, device="cuda")
         cbg.cbg_build_level(self.ctx, self.shape, self.state, self.bins, self.nb, self.g, self.h, self.dtype, d, l2,
                             self.leaf, self.splits, self.child, bins_t=self.bins_t, force=force, hist_out=hist,
-                            last_level=last)
+                            last_level=last, bins4=self.bins4)
         cbg.cbg_sync(self.ctx)
         sp = train.decode_splits(self.splits)[d]
         return to_host(hist), int(sp["feature"]), int(sp["border"]), float(sp["score"]), \
@@ -376,3 +380,82 @@ def test_histogram_kernel_variants_match_oracle(ctx, case, cluster, kernel):
             assert hist_tolerance_ok(hist, ref, np.maximum(ref_abs, root_abs[None])), d
         leaf = oracle.update_leaf(bins, forced[d][0], forced[d][1], d, leaf)
         assert np.array_equal(gl, leaf), d
+
+
+PACKED_CASES = [
+    # n, F, F_pad, max_bins, depth, integer_grads, dtype, bins_t
+    (5003, 40, 64, 16, 6, True, "f32", True),
+    (50000, 70, 96, 16, 6, False, "f32", True),     # 3 uint8 groups: the last packed record has one half
+    (777, 1, 32, 2, 3, False, "f32", True),
+    (20000, 33, 64, 9, 5, False, "bf16", False),
+    (1, 3, 32, 5, 2, False, "f32", True),
+]
+
+
+def test_pack_bins4_layout(ctx):
+    import torch
+    rng = np.random.default_rng(3)
+    for n, F_pad in [(1, 32), (1000, 96), (4097, 128)]:
+        rm = rng.integers(0, 16, size=(n, F_pad)).astype(np.uint8)
+        bins = to_dev(train.grouped_from_rowmajor(rm))
+        G4 = (F_pad // 32 + 1) // 2
+        out = torch.empty(G4 * 32 * n, dtype=torch.uint8, device="cuda")
+        cbg.cbg_pack_bins4(ctx, bins, n, F_pad, out)
+        cbg.cbg_sync(ctx)
+        got = to_host(out).reshape(G4, n, 32)
+        pad = np.zeros((n, G4 * 64), np.uint8)
+        pad[:, :F_pad] = rm
+        want = np.stack([pad[:, 64 * q:64 * q + 32] | (pad[:, 64 * q + 32:64 * q + 64] << 4) for q in range(G4)])
+        assert np.array_equal(got, want), (n, F_pad)
+
+
+@pytest.mark.parametrize("case", PACKED_CASES)
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_packed_histogram_kernel_matches_oracle(ctx, case, cluster):
+    """The lane-per-feature kernel over 4-bit packed bins (tiles.kernel = 6) on forced
+    levels against the oracle, and bit for bit against the uint8 lane kernel (4): both
+    add every row's (g, h) into the same cells in the same order."""
+    n, F, F_pad, max_bins, depth, intg, dtype, bt = case
+    bins, nb, g, h, forced = synth.random_level_case(n + F + 11, n, F, F_pad, max_bins, depth, integer_grads=intg)
+    if dtype == "bf16":
+        g, h = _bf16(g), _bf16(h)
+    tiles = {"kernel": 6, "cluster": cluster, "rows_per_item": 8192}
+    t = Tree(ctx, bins, nb, g, h, depth, dtype, tiles=tiles, with_bins_t=bt)
+    u = Tree(ctx, bins, nb, g, h, depth, dtype, tiles=dict(tiles, kernel=4), with_bins_t=bt)
+    g64, h64 = g.astype(np.float64), h.astype(np.float64)
+    leaf = np.zeros(n, np.uint16)
+    root_abs = None
+    for d in range(depth):
+        hist, sf, sk, _, gl, child = t.level(d, 3.0, force=forced[d], last=(d == depth - 1))
+        hist_u, *_, child_u = u.level(d, 3.0, force=forced[d], last=(d == depth - 1))
+        assert np.array_equal(hist, hist_u), d
+        assert np.array_equal(child, child_u), d
+        ref = oracle.histogram(bins, F, g64, h64, leaf, 1 << d, t.max_bins)
+        ref_abs = oracle.histogram(bins, F, np.abs(g64), np.abs(h64), leaf, 1 << d, t.max_bins)
+        if root_abs is None:
+            root_abs = ref_abs[0]
+        if intg:
+            assert np.array_equal(hist, ref), d
+        else:
+            assert hist_tolerance_ok(hist, ref, np.maximum(ref_abs, root_abs[None])), d
+        leaf = oracle.update_leaf(bins, forced[d][0], forced[d][1], d, leaf)
+        assert np.array_equal(gl, leaf), d
+
+
+def test_packed_kernel_trains_like_the_oracle(ctx):
+    """Whole boosting runs with tiles.kernel = 6 on a 15-border workload, against the oracle."""
+    import dataclasses
+    w = dataclasses.replace(synth.logloss_1m(n=40000, trees=8), max_borders=15)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    assert prep.max_bins <= 16 and prep.bins4 is not None
+    y = to_dev(w.y)
+    model = train.fit(ctx, prep, y, w.loss, w.depth, w.trees, w.lr, w.l2,
+                      tiles={"kernel": 6, "cluster": 2, "rows_per_item": 8192}, use_graph=True)
+    cbg.cbg_sync(ctx)
+    ref_prep = oracle.preprocess(w, prep.F_pad)
+    res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, w.depth, w.trees, w.lr, w.l2)
+    compared, _ = _compare_fit(res, model.host_splits(), to_host(model.pred), w.trees, w.depth)
+    assert compared >= w.depth
+    tiles, ms = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2)
+    assert tiles["kernel"] in (1, 2, 4, 5, 6) and ms > 0
