@@ -106,7 +106,7 @@ def test_new_rows_with_combinations_match_oracle(ctx):
     GPU path (full-data TS of every used combination, quantised with its borders, as extra
     columns for cbg_predict) against the oracle doing the same steps with its own model."""
     import dataclasses
-    w = _interaction_workload(24000, seed=3)
+    w = _interaction_workload(24000, seed=7)     # the oracle's best and runner-up differ by >= 2.5e-4 everywhere
     n_tr = 20000
     w_tr = dataclasses.replace(w, x=np.ascontiguousarray(w.x[:, :n_tr]), cat=np.ascontiguousarray(w.cat[:, :n_tr]),
                                y=np.ascontiguousarray(w.y[:n_tr]))
@@ -114,9 +114,7 @@ def test_new_rows_with_combinations_match_oracle(ctx):
     depth, trees, lr, l2, mb, mc = 4, 3, 0.2, 1.0, 15, 3
     got, res = _run_both(ctx, w_tr, depth, trees, mb, mc, lr=lr, l2=l2)
     compared, n_combo = _compare(got, res, w.n_features, depth, trees)
-    if compared < trees:
-        return                      # a near-tie: the models differ from there on
-    assert n_combo >= 1
+    assert compared == trees and n_combo >= 1
     # GPU: the new rows' bins, then the combinations as extra columns
     prep = train.preprocess(ctx, to_dev(w_tr.x), to_dev(w_tr.cat), to_dev(w_tr.y), "binary", w.max_borders, a=w.a,
                             seed=w.seed)
