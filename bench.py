@@ -62,6 +62,8 @@ def parse_args():
     p.add_argument("--combo-trees", type=int, default=10,
                    help="trees of the feature-combination comparison (0 skips it)")
     p.add_argument("--combo-borders", type=int, default=15, help="borders of a combination's column")
+    p.add_argument("--paper-setting-rows", type=int, default=400_000,
+                   help="rows of the paper-setting workload (400000 as in the paper; smaller for profiling)")
     p.add_argument("--paper-setting-trees", type=int, default=200,
                    help="trees of the 4e5 x 2000, 15-border, depth-6 measurement (0 = skip)")
     return p.parse_args()
@@ -613,7 +615,7 @@ def run_ours(args):
         scorer = scorer_bench(ctx, dev, args.scorer_trees)
     paper_setting = None
     if args.paper_setting_trees > 0 and rank == 0:
-        paper_setting = paper_setting_bench(ctx, dev, args.paper_setting_trees)
+        paper_setting = paper_setting_bench(ctx, dev, args.paper_setting_trees, n=args.paper_setting_rows)
     ordered = None
     if args.ordered_trees > 0 and rank == 0:
         ordered = ordered_bench(ctx, dev, x, cat, y, w, args.ordered_trees, args.ordered_s, tiles)
