@@ -146,3 +146,22 @@ def test_new_rows_with_combinations_match_oracle(ctx):
                         f_offset=F + k, bins=bins_new)
     ref_pred = oracle.predict(bins_new, sf, res["split_k"], res["leaf_values"], lr)
     assert np.all(np.abs(pred - ref_pred) <= 1e-4)
+
+
+def test_bad_arguments_are_rejected(ctx):
+    import torch
+    ids = torch.empty(10, dtype=torch.int32, device="cuda")
+    cat = torch.zeros((2, 10), dtype=torch.int32, device="cuda")
+    bt = torch.zeros((3, 10), dtype=torch.uint8, device="cuda")
+    for items in ([(0, 1, 0), (0, 0, 0)],          # not in canonical order
+                  [(0, 2, 0)],                     # no such categorical column
+                  [(1, 3, 0)],                     # no such feature
+                  []):
+        with pytest.raises(cbg.CbgError) as e:
+            cbg.cbg_combo_ids(ctx, items, cat, 2, bt, 3, 10, ids)
+        assert e.value.status == cbg.CBG_EINVAL
+    cbg.cbg_combo_ids(ctx, [(0, 0, 0), (1, 2, 0)], cat, 2, bt, 3, 10, ids)
+    cbg.cbg_sync(ctx)
+    assert torch.all(ids == ids[0])                  # constant columns: one value
+    with pytest.raises(cbg.CbgError):
+        cbg.cbg_combo_work_bytes(10, 2, 6, 255, 4)    # at most 254 borders

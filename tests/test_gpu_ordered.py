@@ -217,3 +217,28 @@ def test_graph_replay_equals_direct_launches(ctx, s):
     assert np.array_equal(a["feature"], b["feature"]) and np.array_equal(a["border"], b["border"])
     assert np.allclose(to_host(direct.leaf_values), to_host(graph.leaf_values), rtol=1e-6, atol=1e-9)
     assert np.allclose(to_host(direct.pred), to_host(graph.pred), atol=1e-5)
+
+
+def test_bad_arguments_are_rejected(ctx):
+    """Invalid calls return CBG_EINVAL with a message and launch nothing."""
+    import torch
+    op, bins_all, perms, y, yd = _forced(ctx, 100, 2, 1)
+    with pytest.raises(cbg.CbgError) as e:             # work buffer too small
+        bufs = train.alloc_fit(op.base, 2, 1)
+        sup = torch.zeros((2, cbg.cbg_ordered_sup_len(100)), dtype=torch.float32, device="cuda")
+        cbg.cbg_boost_ordered(ctx, bufs.shape, bufs.state, 2, op.bins_pos, op.bins_t_pos, op.y_pos, op.base.bins,
+                              op.base.bins_t, op.base.n_borders, yd, "logloss", "f32", 2, 1, 0, 0.1, 1.0, bufs.pred,
+                              sup, bufs.g, bufs.h, bufs.leaf, bufs.splits, bufs.leaf_values, bufs.child_totals,
+                              torch.empty(8, dtype=torch.uint8, device="cuda"))
+    assert e.value.status == cbg.CBG_EINVAL and "work" in str(e.value)
+    with pytest.raises(cbg.CbgError) as e:             # no permutation
+        train.fit_ordered(ctx, train.OrderedPrepared(op.base, 0, None, op.bins_pos, op.bins_t_pos, op.y_pos), yd,
+                          "logloss", 2, 1, 0.1, 1.0)
+    assert e.value.status == cbg.CBG_EINVAL
+    with pytest.raises(cbg.CbgError):
+        cbg.cbg_ordered_sup_len(0)
+    with pytest.raises(cbg.CbgError) as e:             # misaligned grouped bins
+        b = torch.empty(32 * 100 + 16, dtype=torch.uint8, device="cuda")
+        cbg.cbg_permute_rows(ctx, to_dev(perms[0]), 100, 1, 32, b[1:], None, None, b[1:], None, None)
+    assert e.value.status == cbg.CBG_EINVAL
+    cbg.cbg_sync(ctx)
