@@ -8,7 +8,8 @@
 // without repeats, in lexicographic order of their sorted items. On the GPU, for all
 // candidates at once:
 //   1. combo_ids_kernel: a SplitMix64 chain over the items' values of every row;
-//   2. cbg_ordered_ts, cbg_select_borders, cbg_quantize on the [Nc][n] id columns;
+//   2. cbg_ordered_ts, cbg_select_borders, cbg_quantize on the [Nc][n] id columns (only for
+//      candidates new to the tree: the columns of earlier levels' candidates are kept);
 //   3. cand_hist_kernel: FP64 (G, H) histograms of every candidate over the current leaves
 //      (FP32 per block of rows in shared memory, FP64 across blocks);
 //   4. cand_score_kernel: the best border of every candidate (Section 3 score, FP64);
@@ -64,16 +65,17 @@ __global__ void combo_ids_kernel(const int* __restrict__ items, const int* __res
   }
 }
 
-// hist[j][l][b][2] += (g, h) of the rows of leaf l with bin b of candidate j. SHARED: the
-// block's rows are summed in FP32 shared cells first (level_leaves * cmb float2 cells).
+// hist[j][l][b][2] += (g, h) of the rows of leaf l with bin b of the level's candidate j,
+// whose column is slot slots[j] of the tree's candidate cache. SHARED: the block's rows
+// are summed in FP32 shared cells first (level_leaves * cmb float2 cells).
 template <typename GH, bool SHARED>
-__global__ void cand_hist_kernel(const uint8_t* __restrict__ cbins_t, int64_t n, const uint16_t* __restrict__ leaf,
-                                 int level_leaves, const GH* __restrict__ g, const GH* __restrict__ h, int cmb,
-                                 double* __restrict__ hist) {
+__global__ void cand_hist_kernel(const uint8_t* __restrict__ cbins_t, const int* __restrict__ slots, int64_t n,
+                                 const uint16_t* __restrict__ leaf, int level_leaves, const GH* __restrict__ g,
+                                 const GH* __restrict__ h, int cmb, double* __restrict__ hist) {
   extern __shared__ float2 s_h[];
   const int j = blockIdx.y;
   const int cells = level_leaves * cmb;
-  const uint8_t* col = cbins_t + static_cast<int64_t>(j) * n;
+  const uint8_t* col = cbins_t + static_cast<int64_t>(slots[j]) * n;
   double* hj = hist + static_cast<int64_t>(j) * cells * 2;
   const int64_t r0 = blockIdx.x * CB_HIST_ROWS;
   const int64_t r1 = min(r0 + CB_HIST_ROWS, n);
@@ -110,13 +112,14 @@ __device__ __forceinline__ double score_term(double G, double H, double l2) {
 // Best border of candidate j (one block, thread k scores border k): the sum over leaves of
 // G_L^2/(H_L+l2) + G_R^2/(H_R+l2), left sums in increasing bin order and right sums from the
 // top bin down; ties to the smallest border. best[j] = (score, k) or (-inf, -1).
-__global__ void cand_score_kernel(const double* __restrict__ hist, const int32_t* __restrict__ nb, int level_leaves,
-                                  int cmb, double l2, double2* __restrict__ best) {
+__global__ void cand_score_kernel(const double* __restrict__ hist, const int32_t* __restrict__ nb,
+                                  const int* __restrict__ slots, int level_leaves, int cmb, double l2,
+                                  double2* __restrict__ best) {
   __shared__ double row[256][2];
   __shared__ double r_s[CB_THREADS];
   __shared__ int r_k[CB_THREADS];
   const int j = blockIdx.x;
-  const int nbj = min(nb[j], cmb - 1);
+  const int nbj = min(nb[slots[j]], cmb - 1);
   const double* hj = hist + static_cast<int64_t>(j) * level_leaves * cmb * 2;
   const int k = threadIdx.x;
   double sc = 0.0;
@@ -179,12 +182,12 @@ __global__ void cand_select_kernel(const double2* __restrict__ best, int n_cand,
 }
 
 // Copies the winning candidate's bins column and histogram next to the challenger split.
-__global__ void cand_copy_kernel(const int* __restrict__ chal_idx, const uint8_t* __restrict__ cbins_t, int64_t n,
-                                 const double* __restrict__ hist, int64_t hist_elems, uint8_t* __restrict__ chal_bins,
-                                 double* __restrict__ chal_hist) {
+__global__ void cand_copy_kernel(const int* __restrict__ chal_idx, const int* __restrict__ slots,
+                                 const uint8_t* __restrict__ cbins_t, int64_t n, const double* __restrict__ hist,
+                                 int64_t hist_elems, uint8_t* __restrict__ chal_bins, double* __restrict__ chal_hist) {
   const int j = *chal_idx;
   if (j < 0) return;
-  const uint8_t* col = cbins_t + static_cast<int64_t>(j) * n;
+  const uint8_t* col = cbins_t + static_cast<int64_t>(slots[j]) * n;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n; r += stride)
     chal_bins[r] = col[r];
@@ -204,6 +207,7 @@ struct ComboWork {
   uint8_t* cbins_t;    // [Nc_max][n]
   double* hist;        // [Nc_max][2^(depth-1)][cmb][2]
   double2* best;       // [Nc_max]
+  int* slots;          // [Nc_max] cache slot of each candidate of the level
   cbg_split* chal;
   int* chal_idx;
   uint8_t* chal_bins;  // [n]
@@ -229,6 +233,7 @@ ComboWork carve_combo(void* base, int64_t n, int C, int depth, int max_borders, 
   w.cbins_t = c.take<uint8_t>(static_cast<size_t>(nc) * n);
   w.hist = c.take<double>(static_cast<size_t>(nc) * lh * cmb * 2);
   w.best = c.take<double2>(nc);
+  w.slots = c.take<int>(nc);
   w.chal = c.take<cbg_split>(1);
   w.chal_idx = c.take<int>(1);
   w.chal_bins = c.take<uint8_t>(static_cast<size_t>(n));
@@ -256,35 +261,69 @@ std::vector<std::vector<Item>> candidates(const std::vector<std::vector<Item>>& 
   return std::vector<std::vector<Item>>(out.begin(), out.end());
 }
 
-// Runs steps 1-5 of the file comment for one level; the challenger is left in w.chal.
-cbg_status challenger_for_level(cbg_ctx* ctx, const cbg_combo_args* a, const ComboWork& w,
-                                const std::vector<std::vector<Item>>& cands, int d, int feature) {
+// The columns of a tree's candidates are cached: a candidate's ids, TS, borders and bins
+// depend only on its items, so each is computed once per tree, at the first level that
+// lists it, into the next free slot (slots are handed out in order, so the new columns of a
+// level are contiguous). The histograms, scores and the choice run over all of the level's
+// candidates. Runs steps 1-5 of the file comment; the challenger is left in w.chal.
+struct CandidateCache {
+  std::vector<std::vector<Item>> by_slot;
+  int find(const std::vector<Item>& q) const {
+    for (size_t i = 0; i < by_slot.size(); ++i)
+      if (by_slot[i] == q) return static_cast<int>(i);
+    return -1;
+  }
+};
+
+cbg_status challenger_for_level(cbg_ctx* ctx, const cbg_combo_args* a, const ComboWork& w, CandidateCache& cache,
+                                const std::vector<std::vector<Item>>& cands, int d, int feature,
+                                std::vector<int>* slots_out) {
   const int64_t n = a->shape->n;
   const int nc = static_cast<int>(cands.size());
   const int mc = a->max_complexity;
   const int cmb = a->max_borders + 1;
   const int level_leaves = 1 << d;
-  std::vector<int> items(static_cast<size_t>(nc) * mc * 3, -1), n_items(nc);
+  std::vector<int>& slots = *slots_out;
+  slots.assign(nc, -1);
+  const int slot0 = static_cast<int>(cache.by_slot.size());
+  std::vector<int> items, n_items;
   for (int j = 0; j < nc; ++j) {
-    n_items[j] = static_cast<int>(cands[j].size());
-    for (size_t i = 0; i < cands[j].size(); ++i) {
-      items[(static_cast<size_t>(j) * mc + i) * 3] = cands[j][i].kind;
-      items[(static_cast<size_t>(j) * mc + i) * 3 + 1] = cands[j][i].a;
-      items[(static_cast<size_t>(j) * mc + i) * 3 + 2] = cands[j][i].b;
+    slots[j] = cache.find(cands[j]);
+    if (slots[j] >= 0) continue;
+    slots[j] = static_cast<int>(cache.by_slot.size());
+    cache.by_slot.push_back(cands[j]);
+    n_items.push_back(static_cast<int>(cands[j].size()));
+    for (int i = 0; i < mc; ++i) {
+      const bool used = i < static_cast<int>(cands[j].size());
+      items.push_back(used ? cands[j][i].kind : -1);
+      items.push_back(used ? cands[j][i].a : -1);
+      items.push_back(used ? cands[j][i].b : -1);
     }
   }
-  CBG_CUDA(ctx, cudaMemcpyAsync(w.items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-  CBG_CUDA(ctx, cudaMemcpyAsync(w.n_items, n_items.data(), n_items.size() * sizeof(int), cudaMemcpyHostToDevice,
+  const int n_new = static_cast<int>(n_items.size());
+  CBG_REQUIRE(ctx, slot0 + n_new <= max_candidates(a->C, a->depth), "candidate cache overflow");
+  if (n_new > 0) {
+    CBG_CUDA(ctx, cudaMemcpyAsync(w.items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    CBG_CUDA(ctx, cudaMemcpyAsync(w.n_items, n_items.data(), n_items.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    uint32_t* ids = w.ids + static_cast<int64_t>(slot0) * n;
+    float* ts = w.ts + static_cast<int64_t>(slot0) * n;
+    combo_ids_kernel<<<dim3(grid_for(n, n_new), n_new), CB_THREADS, 0, ctx->stream>>>(w.items, w.n_items, mc, a->cat,
+                                                                                      a->bins_t, n, ids);
+    CBG_CHECK_LAUNCH(ctx);
+    cbg_status st = cbg_ordered_ts(ctx, ids, a->y, n, n_new, a->perm, a->prior, a->a, a->label_kind, ts, nullptr,
+                                   nullptr);
+    if (st != CBG_OK) return st;
+    st = cbg_select_borders(ctx, ts, n, n_new, a->max_borders, w.borders + static_cast<int64_t>(slot0) * a->max_borders,
+                            w.nb + slot0);
+    if (st != CBG_OK) return st;
+    st = cbg_quantize(ctx, ts, n, n_new, w.borders + static_cast<int64_t>(slot0) * a->max_borders, w.nb + slot0,
+                      a->max_borders, w.cbins, (n_new + 31) / 32 * 32, 0, w.cbins_t + static_cast<int64_t>(slot0) * n);
+    if (st != CBG_OK) return st;
+  }
+  CBG_CUDA(ctx, cudaMemcpyAsync(w.slots, slots.data(), slots.size() * sizeof(int), cudaMemcpyHostToDevice,
                                 ctx->stream));
-  combo_ids_kernel<<<dim3(grid_for(n, nc), nc), CB_THREADS, 0, ctx->stream>>>(w.items, w.n_items, mc, a->cat,
-                                                                             a->bins_t, n, w.ids);
-  CBG_CHECK_LAUNCH(ctx);
-  cbg_status st = cbg_ordered_ts(ctx, w.ids, a->y, n, nc, a->perm, a->prior, a->a, a->label_kind, w.ts, nullptr, nullptr);
-  if (st != CBG_OK) return st;
-  st = cbg_select_borders(ctx, w.ts, n, nc, a->max_borders, w.borders, w.nb);
-  if (st != CBG_OK) return st;
-  st = cbg_quantize(ctx, w.ts, n, nc, w.borders, w.nb, a->max_borders, w.cbins, (nc + 31) / 32 * 32, 0, w.cbins_t);
-  if (st != CBG_OK) return st;
   const int64_t hist_elems = static_cast<int64_t>(level_leaves) * cmb * 2;
   CBG_CUDA(ctx, cudaMemsetAsync(w.hist, 0, sizeof(double) * hist_elems * nc, ctx->stream));
   const dim3 hgrid(static_cast<unsigned>(ceil_div(n, CB_HIST_ROWS)), nc);
@@ -293,29 +332,29 @@ cbg_status challenger_for_level(cbg_ctx* ctx, const cbg_combo_args* a, const Com
   if (smem <= CB_HIST_SMEM) {
     if (f32)
       cand_hist_kernel<float, true><<<hgrid, CB_THREADS, smem, ctx->stream>>>(
-          w.cbins_t, n, a->leaf, level_leaves, static_cast<const float*>(a->g), static_cast<const float*>(a->h), cmb,
-          w.hist);
+          w.cbins_t, w.slots, n, a->leaf, level_leaves, static_cast<const float*>(a->g),
+          static_cast<const float*>(a->h), cmb, w.hist);
     else
       cand_hist_kernel<__nv_bfloat16, true><<<hgrid, CB_THREADS, smem, ctx->stream>>>(
-          w.cbins_t, n, a->leaf, level_leaves, static_cast<const __nv_bfloat16*>(a->g),
+          w.cbins_t, w.slots, n, a->leaf, level_leaves, static_cast<const __nv_bfloat16*>(a->g),
           static_cast<const __nv_bfloat16*>(a->h), cmb, w.hist);
   } else {
     if (f32)
       cand_hist_kernel<float, false><<<hgrid, CB_THREADS, 0, ctx->stream>>>(
-          w.cbins_t, n, a->leaf, level_leaves, static_cast<const float*>(a->g), static_cast<const float*>(a->h), cmb,
-          w.hist);
+          w.cbins_t, w.slots, n, a->leaf, level_leaves, static_cast<const float*>(a->g),
+          static_cast<const float*>(a->h), cmb, w.hist);
     else
       cand_hist_kernel<__nv_bfloat16, false><<<hgrid, CB_THREADS, 0, ctx->stream>>>(
-          w.cbins_t, n, a->leaf, level_leaves, static_cast<const __nv_bfloat16*>(a->g),
+          w.cbins_t, w.slots, n, a->leaf, level_leaves, static_cast<const __nv_bfloat16*>(a->g),
           static_cast<const __nv_bfloat16*>(a->h), cmb, w.hist);
   }
   CBG_CHECK_LAUNCH(ctx);
-  cand_score_kernel<<<nc, CB_THREADS, 0, ctx->stream>>>(w.hist, w.nb, level_leaves, cmb, a->l2, w.best);
+  cand_score_kernel<<<nc, CB_THREADS, 0, ctx->stream>>>(w.hist, w.nb, w.slots, level_leaves, cmb, a->l2, w.best);
   CBG_CHECK_LAUNCH(ctx);
   cand_select_kernel<<<1, 32, 0, ctx->stream>>>(w.best, nc, feature, w.chal, w.chal_idx);
   CBG_CHECK_LAUNCH(ctx);
-  cand_copy_kernel<<<grid_for(n, 1), CB_THREADS, 0, ctx->stream>>>(w.chal_idx, w.cbins_t, n, w.hist, hist_elems,
-                                                                  w.chal_bins, w.chal_hist);
+  cand_copy_kernel<<<grid_for(n, 1), CB_THREADS, 0, ctx->stream>>>(w.chal_idx, w.slots, w.cbins_t, n, w.hist,
+                                                                  hist_elems, w.chal_bins, w.chal_hist);
   CBG_CHECK_LAUNCH(ctx);
   return CBG_OK;
 }
@@ -410,6 +449,8 @@ cbg_status cbg_boost_combos(cbg_ctx* ctx, const cbg_combo_args* a) {
     st = cbg_tree_begin(ctx, sh, a->state, a->state_bytes, a->leaf);
     if (st != CBG_OK) return st;
     std::vector<std::vector<Item>> present;
+    CandidateCache cache;
+    std::vector<int> slots;
     int n_combo = 0;
     for (int d = 0; d < D; ++d) {
       const int64_t rec = static_cast<int64_t>(t) * D + d;
@@ -419,7 +460,7 @@ cbg_status cbg_boost_combos(cbg_ctx* ctx, const cbg_combo_args* a) {
       std::vector<std::vector<Item>> cands;
       if (d >= 1 && C > 0) cands = candidates(present, C, mc);
       if (!cands.empty()) {
-        st = challenger_for_level(ctx, a, w, cands, d, F + n_combo);
+        st = challenger_for_level(ctx, a, w, cache, cands, d, F + n_combo, &slots);
         if (st != CBG_OK) return st;
       }
       cbg_level_args la{};
@@ -460,11 +501,12 @@ cbg_status cbg_boost_combos(cbg_ctx* ctx, const cbg_combo_args* a) {
         const auto& q = cands[win];
         for (size_t i = 0; i < q.size(); ++i) a->combo_items[rec * mc + i] = cbg_combo_item{q[i].kind, q[i].a, q[i].b};
         int32_t nb = 0;
-        CBG_CUDA(ctx, cudaMemcpy(&nb, w.nb + win, sizeof(nb), cudaMemcpyDeviceToHost));
+        const int slot = slots[win];
+        CBG_CUDA(ctx, cudaMemcpy(&nb, w.nb + slot, sizeof(nb), cudaMemcpyDeviceToHost));
         a->combo_nb[rec] = nb;
         if (nb > 0)
           CBG_CUDA(ctx, cudaMemcpy(a->combo_borders + rec * a->max_borders,
-                                   w.borders + static_cast<int64_t>(win) * a->max_borders, sizeof(float) * nb,
+                                   w.borders + static_cast<int64_t>(slot) * a->max_borders, sizeof(float) * nb,
                                    cudaMemcpyDeviceToHost));
         if (std::find(present.begin(), present.end(), q) == present.end()) present.push_back(q);
         ++n_combo;
