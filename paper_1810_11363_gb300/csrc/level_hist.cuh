@@ -1093,7 +1093,18 @@ __device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const
     if (b < max_bins) {
       const float* src = partials + (static_cast<int64_t>(u0) * G + grp) * item_elems +
                          static_cast<int64_t>(st) * max_bins * GROUP + b * GROUP + fl;
-      for (int u = u0; u < u1; ++u, src += G * item_elems) s += static_cast<double>(*src);
+      const int64_t step = G * item_elems;
+      // four independent FP64 chains so that the unit loads overlap
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int u = u0;
+      for (; u + 4 <= u1; u += 4, src += 4 * step) {
+        s0 += static_cast<double>(src[0]);
+        s1 += static_cast<double>(src[step]);
+        s2 += static_cast<double>(src[2 * step]);
+        s3 += static_cast<double>(src[3 * step]);
+      }
+      for (; u < u1; ++u, src += step) s0 += static_cast<double>(*src);
+      s = (s0 + s1) + (s2 + s3);
     }
     tile[fl][bl][st] = s;
   }
