@@ -38,6 +38,7 @@ namespace cbg {
 constexpr unsigned STATUS_NONFINITE = 1u;
 constexpr unsigned STATUS_BAD_LABEL = 2u;
 constexpr unsigned STATUS_TIMEOUT = 4u;
+constexpr unsigned STATUS_BAD_BIN = 8u;     // a bin that does not fit the 4-bit packed layout
 
 cbg_status fail(cbg_ctx* ctx, cbg_status code, const char* fmt, ...);
 

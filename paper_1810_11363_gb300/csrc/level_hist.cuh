@@ -865,7 +865,7 @@ __global__ void pack_bins4_kernel(const uint8_t* __restrict__ bins, int64_t n, i
     reinterpret_cast<uint4*>(bins4)[x] = make_uint4(lo.x | (hi.x << 4), lo.y | (hi.y << 4), lo.z | (hi.z << 4),
                                                     lo.w | (hi.w << 4));
   }
-  if (bad) atomicOr(status, ::cbg::STATUS_NONFINITE);
+  if (bad) atomicOr(status, ::cbg::STATUS_BAD_BIN);
 }
 
 // ---------------------------------------- lane-per-feature, one statistic per warp

@@ -29,6 +29,7 @@ __all__ = [
     "dense_400k",
     "precision_10m",
     "batched_256",
+    "interaction_xor",
     "WORKLOADS",
     "random_level_case",
 ]
@@ -216,6 +217,20 @@ def batched_256(n_problems: int = 256, n_max: int = 200_000, trees: int = 200) -
         out.append(Workload(f"batched_{i}", x, cat, y.astype(np.float32), loss,
                             max_borders=128, depth=6, trees=trees, lr=0.1, seed=i))
     return out
+
+
+def interaction_xor(n: int = 24_000, seed: int = 0, depth: int = 4, trees: int = 3) -> Workload:
+    """A label that only a feature combination carries (Section 2 "Feature combinations"):
+    2 N(0,1) floats and 3 categoricals of 4 categories each; y ~ Bernoulli(0.85) when the
+    parities of c0 and c1 differ, else Bernoulli(0.15). No single column says anything
+    about y. 15 borders, Logloss."""
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(2, n)).astype(np.float32)
+    k = rng.integers(0, 4, size=(3, n))
+    cat = (k * 1000003 + 5).astype(np.uint32)
+    z = (k[0] % 2) ^ (k[1] % 2)
+    y = (rng.random(n) < np.where(z == 1, 0.85, 0.15)).astype(np.float32)
+    return Workload("interaction_xor", x, cat, y, "logloss", 15, depth, trees, 0.2, 1.0, 1.0, seed)
 
 
 WORKLOADS = {

@@ -60,15 +60,7 @@ def _compare(got, res, F, depth, trees, near=1e-5):
 
 
 def _interaction_workload(n, seed=0):
-    """Three categorical columns (4 categories, Zipf-free) and two floats; the label
-    depends on the parity of c0 XOR the parity of c1, which no single column carries."""
-    rng = np.random.default_rng(seed)
-    x = rng.normal(size=(2, n)).astype(np.float32)
-    k = rng.integers(0, 4, size=(3, n))
-    cat = (k * 1000003 + 5).astype(np.uint32)
-    z = (k[0] % 2) ^ (k[1] % 2)
-    y = (rng.random(n) < np.where(z == 1, 0.85, 0.15)).astype(np.float32)
-    return synth.Workload("interaction", x, cat, y, "logloss", 15, 4, 3, 0.2, 1.0, 1.0, seed)
+    return synth.interaction_xor(n=n, seed=seed)
 
 
 @pytest.mark.parametrize("n", [3000, 20001])

@@ -133,3 +133,41 @@ def test_precision_10m_full_size(ctx):
     _check_sampled_features(w, prep, col, feats[:6], gpu_hist, g64, h64, rows)
     del x, catd, prep
     torch.cuda.empty_cache()
+
+
+def test_ordered_boosting_logloss_1m_full_size(ctx):
+    """Ordered boosting at the benchmark's full size (10^6 rows x 110 features, s = 4,
+    depth 6, 2 trees) against the oracle on every output: the permutations and
+    per-permutation bins, the structures (a split may differ only at an oracle near-tie),
+    leaf values, predictions and every supporting value."""
+    w = synth.logloss_1m(trees=2)
+    s = 4
+    op = train.preprocess_ordered(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, s, a=w.a,
+                                  seed=w.seed)
+    model = train.fit_ordered(ctx, op, to_dev(w.y), w.loss, w.depth, 2, w.lr, w.l2, use_graph=True)
+    cbg.cbg_sync(ctx)
+    ref = oracle.preprocess_ordered(w, op.base.F_pad, s)
+    perms = to_host(op.perms, np.uint32)
+    assert np.array_equal(perms, ref["perms"])
+    rows = np.sort(np.random.default_rng(5).choice(w.n, 20000, replace=False))
+    bins_pos = to_host(op.bins_pos)
+    for q in range(s):
+        rm = train.rowmajor_from_grouped(bins_pos[q], w.n, op.base.F_pad)
+        inv = np.empty(w.n, np.int64)
+        inv[perms[q]] = np.arange(w.n)
+        assert np.array_equal(rm[inv[rows]], ref["bins_all"][q][rows]), q
+    res = oracle.fit_ordered(ref["bins_all"], w.n_features, ref["n_borders"], w.y, w.loss, w.depth, 2, w.lr, w.l2,
+                             ref["perms"])
+    sp = model.host_splits()
+    for t in range(2):
+        for d in range(w.depth):
+            if (sp[t, d]["feature"], sp[t, d]["border"]) != (res["split_f"][t, d], res["split_k"][t, d]):
+                assert res["score"][t, d] - res["second"][t, d] <= 1e-5 * abs(res["score"][t, d]), (t, d)
+                return
+        assert np.allclose(to_host(model.leaf_values[t]), res["leaf_values"][t], rtol=1e-4, atol=1e-6), t
+    assert np.all(np.abs(to_host(model.pred) - res["pred"]) <= 1e-4)
+    off = oracle.ordered_sup_offsets(w.n)
+    sup = to_host(model.sup).astype(np.float64)
+    for i in range(len(off) - 1):
+        held = off[i + 1] - off[i]
+        assert np.all(np.abs(sup[:, (2 << i):(2 << i) + held] - res["sup"][:, off[i]:off[i + 1]]) <= 1e-4), i

@@ -459,3 +459,16 @@ def test_packed_kernel_trains_like_the_oracle(ctx):
     assert compared >= w.depth
     tiles, ms = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2)
     assert tiles["kernel"] in (1, 2, 4, 5, 6) and ms > 0
+
+
+def test_pack_bins4_flags_bins_of_16_and_more(ctx):
+    """A bin that does not fit 4 bits makes the next cbg_sync report CBG_EDATA."""
+    import torch
+    rm = np.zeros((100, 32), np.uint8)
+    rm[7, 3] = 16
+    out = torch.empty(32 * 100, dtype=torch.uint8, device="cuda")
+    cbg.cbg_pack_bins4(ctx, to_dev(train.grouped_from_rowmajor(rm)), 100, 32, out)
+    with pytest.raises(cbg.CbgError) as e:
+        cbg.cbg_sync(ctx)
+    assert e.value.status == cbg.CBG_EDATA
+    cbg.cbg_sync(ctx)     # the flag is cleared once reported
