@@ -433,6 +433,11 @@ def combos_bench(ctx, dev, x, cat, y, w, trees, max_borders, max_complexity, til
 
 
 # ------------------------------------------------------------------ arms
+def workload_desc(trees: int) -> str:
+    return ("logloss_1m: n=1,000,000, 100 float (40 N(0,1), 30 U(0,1), 30 lognormal) + 10 categorical "
+            f"(K 2..100k, Zipf 1.1), 254 borders (255 bins), depth 6, {trees} trees, lr 0.05, L2 3, Logloss")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -459,8 +464,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "logloss_1m: n=1,000,000, 100 float + 10 categorical features, 254 borders, "
-                                   f"depth 6, {args.trees} trees, lr 0.05, L2 3", "trees": args.trees},
+            "config": {"workload": workload_desc(args.trees), "trees_per_step": args.trees},
             "cpu_baseline": {"value": value, "unit": "trees/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -640,9 +644,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.gh, "data": "synthetic",
-                "config": {"workload": "logloss_1m: n=1,000,000, 100 float (40 N(0,1), 30 U(0,1), 30 lognormal) + "
-                                       "10 categorical (K 2..100k, Zipf 1.1), 254 borders (255 bins), depth 6, "
-                                       f"{T} trees, lr 0.05, L2 3, Logloss", "trees_per_step": T,
+                "config": {"workload": workload_desc(T), "trees_per_step": T,
                            "parallelism": f"replicas x{ws}", "l2_flush": "256 MB write between steps; inputs "
                                                                              "(x 400 MB) larger than L2",
                            "gh_storage": args.gh, "graph_replay": use_graph, "hist_tiles": tiles},
