@@ -566,6 +566,21 @@ def run_ours(args):
                 "alg_bytes_per_launch": alg_bytes / max(hist_launches, 1),
                 "launches": hist_launches, "avg_launch_us": hist_ms * 1e3 / max(hist_launches, 1),
                 "timing": hist_timing}
+    # The same kernel against its own bottleneck: every (row, feature) is one read-modify-
+    # write of a float2 (G, H) cell in shared memory, 16 bytes through a 128-byte-per-clock
+    # shared-memory data path, so an SM can retire at most 8 updates per clock.
+    clk_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    upd = rows_hist * F
+    upd_rate = upd / (hist_ms / 1e3) if hist_ms > 0 else None
+    per_sm_clk = upd_rate / (n_sms * clk_mhz * 1e6) if upd_rate else None
+    roofline_smem = {"bound": "shared-memory updates", "kernel": roofline["kernel"],
+                     "achieved": per_sm_clk, "peak": 8.0, "unit": "float2 updates per SM per clock",
+                     "frac": per_sm_clk / 8.0 if per_sm_clk else None,
+                     "derivation": "128 B/clock/SM shared-memory bandwidth / 16 B per float2 read + write",
+                     "clock_mhz": clk_mhz, "sms": n_sms,
+                     "hbm_frac_at_this_peak": (8.0 * n_sms * clk_mhz * 1e6 * (F + 2 * gh_bytes) / F / 1e9) / peak
+                     if peak else None}
 
     # end to end through the public API from pinned host memory
     e2e = None
@@ -649,7 +664,8 @@ def run_ours(args):
                                                                              "(x 400 MB) larger than L2",
                            "gh_storage": args.gh, "graph_replay": use_graph, "hist_tiles": tiles},
                 "row_feature_bins_per_s": rfb, "gpu_launches": launches_per_step * args.steps,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "roofline": roofline, "roofline_smem": roofline_smem, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk,
                 "forms": forms, "batched_vs_plain": batched, "scorer": scorer, "paper_setting": paper_setting,
                 "ordered_boosting": ordered, "feature_combinations": combos,
                 "breakdown": {"step_ms": step_ms}}
