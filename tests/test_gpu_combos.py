@@ -157,3 +157,20 @@ def test_bad_arguments_are_rejected(ctx):
     assert torch.all(ids == ids[0])                  # constant columns: one value
     with pytest.raises(cbg.CbgError):
         cbg.cbg_combo_work_bytes(10, 2, 6, 255, 4)    # at most 254 borders
+
+
+def test_combinations_with_real_labels(ctx):
+    """RMSE with real labels: the TS (single columns and candidates) are FP64 prefix sums
+    in another order on the GPU, so a border may land one ulp away and a later split may
+    differ; the first split must agree and the final training losses agree closely."""
+    w = synth.rmse_10k(n=8000)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "real", w.max_borders, a=w.a, seed=w.seed)
+    got = train.fit_combos(ctx, prep, to_dev(w.cat), to_dev(w.y), "real", "rmse", 4, 6, 0.1, 3.0, 15, 3, a=w.a)
+    cbg.cbg_sync(ctx)
+    rp = oracle.preprocess(w, prep.F_pad)
+    res = oracle.fit_combos(rp["bins"], w.n_features, w.n_float, rp["n_borders"], w.cat, w.y, "rmse", 4, 6, 0.1, 3.0,
+                            rp["perm"], rp["prior"], w.a, 15, 3)
+    gpu_loss = oracle.loss("rmse", w.y, to_host(got.model.pred).astype(np.float64))
+    assert abs(gpu_loss - res["losses"][-1]) <= 1e-3 * res["losses"][-1]
+    sp = got.model.host_splits()
+    assert (sp[0, 0]["feature"], sp[0, 0]["border"]) == (res["split_f"][0, 0], res["split_k"][0, 0])
