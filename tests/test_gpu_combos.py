@@ -174,3 +174,17 @@ def test_combinations_with_real_labels(ctx):
     assert abs(gpu_loss - res["losses"][-1]) <= 1e-3 * res["losses"][-1]
     sp = got.model.host_splits()
     assert (sp[0, 0]["feature"], sp[0, 0]["border"]) == (res["split_f"][0, 0], res["split_k"][0, 0])
+
+
+def test_bf16_gradients_with_combinations_train_close_to_f32(ctx):
+    w = _interaction_workload(20000, seed=7)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    losses = {}
+    for dt in ("f32", "bf16"):
+        m = train.fit_combos(ctx, prep, to_dev(w.cat), to_dev(w.y), "binary", "logloss", 4, 4, 0.2, 1.0, 15, 3,
+                             a=w.a, gh_dtype=dt)
+        cbg.cbg_sync(ctx)
+        losses[dt] = oracle.loss("logloss", w.y, to_host(m.model.pred).astype(np.float64))
+        assert (m.model.host_splits()["feature"] >= w.n_features).any(), dt
+    assert abs(losses["bf16"] - losses["f32"]) <= 5e-3 * losses["f32"]
