@@ -642,11 +642,13 @@ def run_ours(args):
     if args.combo_trees > 0 and rank == 0:
         combos = combos_bench(ctx, dev, x, cat, y, w, args.combo_trees, args.combo_borders, 4, tiles)
 
-    # kernels of ours per step: the preprocessing launches of logloss_1m (359, counted in
-    # its ncu launch list), the first gradients, and per tree: tree_begin, 5 kernels per
-    # level (histogram, reduction, scoring, partition flags, scatter; no scatter at the
-    # last level), apply, and the record kernel of a graph replay
-    launches_per_step = 359 + 1 + T * (1 + 5 * D - 1 + 1 + (1 if use_graph else 0))
+    # kernels of ours per step: the preprocessing launches of logloss_1m (133, counted in
+    # its ncu launch list: permutation sort, one sort for the ordered TS of the 10
+    # categorical columns, the border sort, quantisation), the first gradients, and per
+    # tree: tree_begin, 5 kernels per level (histogram, reduction, scoring, partition
+    # flags, scatter; no scatter at the last level), apply, and the record kernel of a
+    # graph replay
+    launches_per_step = 133 + 1 + T * (1 + 5 * D - 1 + 1 + (1 if use_graph else 0))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
