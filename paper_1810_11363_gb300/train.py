@@ -6,6 +6,12 @@ fit(): classic boosting of oblivious trees through cbg_boost (Sections 3-5).
 ts_tables() / preprocess_new() / predict(): the inference path: full-data statistics of
 new rows, quantisation with the training borders, and the model value (Section 4,
 "Fast scorer").
+preprocess_ordered() / fit_ordered(): ordered boosting with s permutations and the
+log-scale supporting models (Section 3, Algorithm 1).
+fit_combos() / predict_combos(): classic boosting with greedy feature combinations, and
+their application to new rows (Section 2, "Feature combinations").
+fit_batched() / autotune() / autotune_batch(): many independent problems at once, and the
+histogram tilings picked by timing.
 All arithmetic runs in libcbg's kernels; this module only allocates and marshals.
 """
 from __future__ import annotations
