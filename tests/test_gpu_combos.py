@@ -188,3 +188,33 @@ def test_bf16_gradients_with_combinations_train_close_to_f32(ctx):
         losses[dt] = oracle.loss("logloss", w.y, to_host(m.model.pred).astype(np.float64))
         assert (m.model.host_splits()["feature"] >= w.n_features).any(), dt
     assert abs(losses["bf16"] - losses["f32"]) <= 5e-3 * losses["f32"]
+
+
+def test_depth_one_takes_no_combination(ctx):
+    """A depth-1 tree has only the first level, which takes no combination: the run is the
+    classic one."""
+    w = synth.interaction_xor(5000, seed=2)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    got = train.fit_combos(ctx, prep, to_dev(w.cat), to_dev(w.y), "binary", "logloss", 1, 4, 0.2, 1.0, 15, 4, a=w.a)
+    plain = train.fit(ctx, prep, to_dev(w.y), "logloss", 1, 4, 0.2, 1.0)
+    cbg.cbg_sync(ctx)
+    a, b = got.model.host_splits(), plain.host_splits()
+    assert np.array_equal(a["feature"], b["feature"]) and np.array_equal(a["border"], b["border"])
+    assert np.array_equal(to_host(got.model.pred).view(np.uint32), to_host(plain.pred).view(np.uint32))
+
+
+@pytest.mark.parametrize("n", [50, 1001])
+def test_one_categorical_joins_only_splits(ctx, n):
+    """With one categorical column every candidate is that column joined with float splits
+    of the tree (kind-1 items); small and ragged n against the oracle."""
+    import dataclasses
+    w = synth.interaction_xor(n, seed=4)
+    w = dataclasses.replace(w, cat=np.ascontiguousarray(w.cat[:1]))
+    got, res = _run_both(ctx, w, depth=3, trees=3, max_borders=7, mc=3)
+    compared, n_combo = _compare(got, res, w.n_features, 3, 3)
+    assert compared >= 1
+    items = res["combo_items"][res["split_f"] >= w.n_features]
+    for it in items:
+        used = it[it[:, 0] >= 0]
+        assert used[0, 0] == 0 and np.all(used[1:, 0] == 1)
