@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <set>
+#include <type_traits>
 #include <vector>
 
 #include "cbg_internal.cuh"
@@ -66,9 +67,12 @@ __global__ void combo_ids_kernel(const int* __restrict__ items, const int* __res
 }
 
 // hist[j][l][b][2] += (g, h) of the rows of leaf l with bin b of the level's candidate j,
-// whose column is slot slots[j] of the tree's candidate cache. SHARED: the block's rows
-// are summed in FP32 shared cells first (level_leaves * cmb float2 cells).
-template <typename GH, bool SHARED>
+// whose column is slot slots[j] of the tree's candidate cache. COPIES > 0: the block's rows
+// are summed in FP32 shared cells first, COPIES copies of the level_leaves * cmb float2
+// cells (one per group of 256 / COPIES threads, so that fewer threads contend for a cell;
+// with few cells and skewed bins the contention, not the row count, sets the time), added
+// in copy order; COPIES = 0: FP64 global atomics per row.
+template <typename GH, int COPIES>
 __global__ void cand_hist_kernel(const uint8_t* __restrict__ cbins_t, const int* __restrict__ slots, int64_t n,
                                  const uint16_t* __restrict__ leaf, int level_leaves, const GH* __restrict__ g,
                                  const GH* __restrict__ h, int cmb, double* __restrict__ hist) {
@@ -79,25 +83,31 @@ __global__ void cand_hist_kernel(const uint8_t* __restrict__ cbins_t, const int*
   double* hj = hist + static_cast<int64_t>(j) * cells * 2;
   const int64_t r0 = blockIdx.x * CB_HIST_ROWS;
   const int64_t r1 = min(r0 + CB_HIST_ROWS, n);
-  if (SHARED) {
-    for (int c = threadIdx.x; c < cells; c += blockDim.x) s_h[c] = make_float2(0.f, 0.f);
+  float2* mine = s_h;
+  if (COPIES > 0) {
+    for (int c = threadIdx.x; c < COPIES * cells; c += blockDim.x) s_h[c] = make_float2(0.f, 0.f);
+    mine = s_h + (threadIdx.x * COPIES / blockDim.x) * cells;
     __syncthreads();
   }
   for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     const int c = (leaf[r] & (level_leaves - 1)) * cmb + col[r];
     const float gv = cbgd::load_gh(g, r), hv = cbgd::load_gh(h, r);
-    if (SHARED) {
-      atomicAdd(&s_h[c].x, gv);
-      atomicAdd(&s_h[c].y, hv);
+    if (COPIES > 0) {
+      atomicAdd(&mine[c].x, gv);
+      atomicAdd(&mine[c].y, hv);
     } else {
       atomicAdd(&hj[2 * c], static_cast<double>(gv));
       atomicAdd(&hj[2 * c + 1], static_cast<double>(hv));
     }
   }
-  if (SHARED) {
+  if (COPIES > 0) {
     __syncthreads();
     for (int c = threadIdx.x; c < cells; c += blockDim.x) {
-      const float2 v = s_h[c];
+      float2 v = s_h[c];
+      for (int k = 1; k < COPIES; ++k) {
+        v.x += s_h[k * cells + c].x;
+        v.y += s_h[k * cells + c].y;
+      }
       if (v.x != 0.f) atomicAdd(&hj[2 * c], static_cast<double>(v.x));
       if (v.y != 0.f) atomicAdd(&hj[2 * c + 1], static_cast<double>(v.y));
     }
@@ -327,27 +337,23 @@ cbg_status challenger_for_level(cbg_ctx* ctx, const cbg_combo_args* a, const Com
   const int64_t hist_elems = static_cast<int64_t>(level_leaves) * cmb * 2;
   CBG_CUDA(ctx, cudaMemsetAsync(w.hist, 0, sizeof(double) * hist_elems * nc, ctx->stream));
   const dim3 hgrid(static_cast<unsigned>(ceil_div(n, CB_HIST_ROWS)), nc);
-  const int smem = static_cast<int>(sizeof(float2)) * level_leaves * cmb;
+  const int cell_bytes = static_cast<int>(sizeof(float2)) * level_leaves * cmb;
   const bool f32 = a->gh_dtype == CBG_F32;
-  if (smem <= CB_HIST_SMEM) {
+  auto launch = [&](auto copies) {
+    constexpr int K = decltype(copies)::value;
+    const int smem = K > 0 ? K * cell_bytes : 0;
     if (f32)
-      cand_hist_kernel<float, true><<<hgrid, CB_THREADS, smem, ctx->stream>>>(
+      cand_hist_kernel<float, K><<<hgrid, CB_THREADS, smem, ctx->stream>>>(
           w.cbins_t, w.slots, n, a->leaf, level_leaves, static_cast<const float*>(a->g),
           static_cast<const float*>(a->h), cmb, w.hist);
     else
-      cand_hist_kernel<__nv_bfloat16, true><<<hgrid, CB_THREADS, smem, ctx->stream>>>(
+      cand_hist_kernel<__nv_bfloat16, K><<<hgrid, CB_THREADS, smem, ctx->stream>>>(
           w.cbins_t, w.slots, n, a->leaf, level_leaves, static_cast<const __nv_bfloat16*>(a->g),
           static_cast<const __nv_bfloat16*>(a->h), cmb, w.hist);
-  } else {
-    if (f32)
-      cand_hist_kernel<float, false><<<hgrid, CB_THREADS, 0, ctx->stream>>>(
-          w.cbins_t, w.slots, n, a->leaf, level_leaves, static_cast<const float*>(a->g),
-          static_cast<const float*>(a->h), cmb, w.hist);
-    else
-      cand_hist_kernel<__nv_bfloat16, false><<<hgrid, CB_THREADS, 0, ctx->stream>>>(
-          w.cbins_t, w.slots, n, a->leaf, level_leaves, static_cast<const __nv_bfloat16*>(a->g),
-          static_cast<const __nv_bfloat16*>(a->h), cmb, w.hist);
-  }
+  };
+  if (8 * cell_bytes <= CB_HIST_SMEM) launch(std::integral_constant<int, 8>{});
+  else if (cell_bytes <= CB_HIST_SMEM) launch(std::integral_constant<int, 1>{});
+  else launch(std::integral_constant<int, 0>{});
   CBG_CHECK_LAUNCH(ctx);
   cand_score_kernel<<<nc, CB_THREADS, 0, ctx->stream>>>(w.hist, w.nb, w.slots, level_leaves, cmb, a->l2, w.best);
   CBG_CHECK_LAUNCH(ctx);
@@ -436,9 +442,13 @@ cbg_status cbg_boost_combos(cbg_ctx* ctx, const cbg_combo_args* a) {
   DeviceGuard guard(ctx->device);
   const int cmb = a->max_borders + 1;
   if (static_cast<int>(sizeof(float2)) * (1 << (D - 1)) * cmb <= CB_HIST_SMEM) {
-    CBG_CUDA(ctx, cudaFuncSetAttribute(cand_hist_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CBG_CUDA(ctx, cudaFuncSetAttribute(cand_hist_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        CB_HIST_SMEM));
-    CBG_CUDA(ctx, cudaFuncSetAttribute(cand_hist_kernel<__nv_bfloat16, true>,
+    CBG_CUDA(ctx, cudaFuncSetAttribute(cand_hist_kernel<__nv_bfloat16, 1>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, CB_HIST_SMEM));
+    CBG_CUDA(ctx, cudaFuncSetAttribute(cand_hist_kernel<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       CB_HIST_SMEM));
+    CBG_CUDA(ctx, cudaFuncSetAttribute(cand_hist_kernel<__nv_bfloat16, 8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, CB_HIST_SMEM));
   }
   const int L = 1 << D;
