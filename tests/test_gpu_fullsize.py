@@ -171,3 +171,14 @@ def test_ordered_boosting_logloss_1m_full_size(ctx):
     for i in range(len(off) - 1):
         held = off[i + 1] - off[i]
         assert np.all(np.abs(sup[:, (2 << i):(2 << i) + held] - res["sup"][:, off[i]:off[i + 1]]) <= 1e-4), i
+
+
+def test_combinations_interaction_1m(ctx):
+    """Feature combinations at 10^6 rows (the XOR interaction workload, depth 4, 3 trees,
+    up to 3 items, 15 borders) against the oracle: structures, combinations and their
+    borders, leaf values and predictions."""
+    from test_gpu_combos import _compare, _run_both
+    w = synth.interaction_xor(1_000_000, seed=7)
+    got, res = _run_both(ctx, w, depth=4, trees=3, max_borders=15, mc=3)
+    compared, n_combo = _compare(got, res, w.n_features, 4, 3)
+    assert compared >= 1 and n_combo >= 1
