@@ -45,8 +45,9 @@ def parse_args():
     p.add_argument("--ref-sample-trees", type=int, default=2)
     p.add_argument("--no-graph", action="store_true", help="launch every kernel from the host instead of "
                                                            "replaying one captured tree")
-    p.add_argument("--hist-kernel", choices=["pair", "lane", "wp", "red", "cas64"], default="red",
-                   help="warp-private atomic-free histograms (wp) or shared-memory float reductions (red)")
+    p.add_argument("--hist-kernel", choices=["pair", "lane", "wp", "red", "int", "cas64"], default="int",
+                   help="warp-private atomic-free histograms (wp), shared-memory float reductions (red) or "
+                        "shared-memory integer reductions of fixed-point values (int)")
     p.add_argument("--cluster", type=int, default=0, help="CTAs per histogram cluster (0 = library default)")
     p.add_argument("--rows-per-item", type=int, default=0, help="rows per CTA of a histogram work unit")
     p.add_argument("--hist-threads", type=int, default=0, help="threads per histogram CTA (0 = library default)")
@@ -170,13 +171,15 @@ def hist_source_hash():
     return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
 
 
-def recorded_traffic_per_row():
+def recorded_traffic_per_row(variant):
     """DRAM bytes per histogrammed row from the committed ncu summary, if it was taken on
-    the current histogram source; else None."""
+    the current histogram source and the given kernel variant; else None."""
     try:
         with open(TRAFFIC_FILE) as fh:
             kv = dict(line.split(None, 1) for line in fh if line.strip() and not line.startswith("#"))
         if kv.get("source_sha256_16", "").strip() != hist_source_hash():
+            return None
+        if kv.get("kernel_variant", "red").strip() != variant:
             return None
         return float(kv["dram_bytes_per_row"])
     except (OSError, KeyError, ValueError):
@@ -503,7 +506,8 @@ def run_ours(args):
         return prep, model
 
     prep0 = train.preprocess(ctx, x, cat, y, "binary", w.max_borders, a=w.a, seed=w.seed)
-    tiles = {"kernel": {"wp": 2, "red": 1, "cas64": 3, "lane": 4, "pair": 5}[args.hist_kernel], "cluster": args.cluster,
+    tiles = {"kernel": {"wp": 2, "red": 1, "cas64": 3, "lane": 4, "pair": 5, "int": 7}[args.hist_kernel],
+             "cluster": args.cluster,
              "rows_per_item": args.rows_per_item, "threads": args.hist_threads}
     bufs = train.alloc_fit(prep0, D, T, args.gh, tiles=tiles)
     for _ in range(args.warmup):
@@ -554,7 +558,7 @@ def run_ours(args):
     alg_bytes = rows_hist * (F + 2 * gh_bytes)
     achieved = alg_bytes / (hist_ms / 1e3) / 1e9 if hist_ms > 0 else None
     peak, peak_kind = measured_peak_hbm()
-    per_row = recorded_traffic_per_row()
+    per_row = recorded_traffic_per_row(args.hist_kernel)
     rows_per_launch = rows_hist / max(hist_launches, 1)
     roofline = {"bound": "hbm", "kernel": {"wp": "level_hist_wp_kernel", "lane": "level_hist_lane_kernel", "pair": "level_hist_pair_kernel"}.get(
                     args.hist_kernel, "level_hist_kernel"),
@@ -562,7 +566,7 @@ def run_ours(args):
                 "achieved": achieved, "peak": peak,
                 "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": per_row * rows_per_launch if (per_row and args.hist_kernel == "red") else None,
+                "traffic": per_row * rows_per_launch if per_row else None,
                 "alg_bytes_per_launch": alg_bytes / max(hist_launches, 1),
                 "launches": hist_launches, "avg_launch_us": hist_ms * 1e3 / max(hist_launches, 1),
                 "timing": hist_timing}

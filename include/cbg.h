@@ -72,13 +72,24 @@ typedef struct cbg_split {
  * thread-block cluster that share one partial histogram through distributed
  * shared memory (1..16; a smaller power of two is used if that many cannot be
  * co-resident); kernel: 1 = one shared histogram per CTA updated with
- * shared-memory float reductions (the default, 0), 2 = warp-private
- * histograms of 16 features updated without atomics, 3 = one shared histogram
- * per CTA with (G, H) updated by one 64-bit compare-and-swap, 4 = lane-per-
- * feature warp-private histograms with store forwarding (bins must be 16-byte
- * aligned), 5 = the same with G and H in separate warps, 6 = lane-per-feature
- * over the 4-bit packed bins of cbg_pack_bins4 (max_bins <= 16; the level
- * arguments carry bins4). Zero fields take library defaults. */
+ * shared-memory float reductions, 2 = warp-private histograms of 16 features
+ * updated without atomics, 3 = one shared histogram per CTA with (G, H)
+ * updated by one 64-bit compare-and-swap, 4 = lane-per-feature warp-private
+ * histograms with store forwarding (bins must be 16-byte aligned), 5 = the
+ * same with G and H in separate warps, 6 = lane-per-feature over the 4-bit
+ * packed bins of cbg_pack_bins4 (max_bins <= 16; the level arguments carry
+ * bins4), 7 = one shared histogram per CTA of int32 fixed-point cells updated
+ * with shared-memory integer reductions (the default, 0; 4096 rows per CTA and
+ * clusters of 4 by default). Kernel 7 rounds each (g, h) of a CTA's rows to a
+ * multiple of 2^-e, e the largest exponent with 2^e * 1.001 * S < 2^30 for S the
+ * sum of |g| (of |h| for H) over those rows, with a dither hashed from the row's
+ * position (floor(v 2^e + u), u in [0, 1)): the rounding error of a row is below
+ * 2.002 * S * 2^-30 with mean zero (integer values are exact), the sums are exact
+ * and do not depend on the order of the updates, and each cluster's cells are
+ * rounded once to the FP32 partial.
+ * cbg_boost_batched has no batched fixed-point histogram: problems on the default
+ * kernel there take kernel 1 with the default tiling's rows and cluster.
+ * Zero fields take library defaults. */
 typedef struct cbg_tiles {
   int32_t slab_chunks;
   int32_t rows_per_item;
@@ -433,10 +444,10 @@ cbg_status cbg_predict(cbg_ctx* ctx, const cbg_predict_args* args);
  * `depth` levels of one tree per timing (cbg_tree_begin + cbg_build_level on the
  * ctx stream, CUDA events), and writes the fastest to *best and its mean device
  * time per tree (ms) to *best_ms. The candidates vary:
- *  - the histogram kernel: shared-memory reductions (1), lane-per-feature warp
- *    histograms (4) and their one-statistic-per-warp form (5), 16-feature
- *    warp-private histograms (2), and with bins4 and max_bins <= 16 the packed
- *    lane-per-feature kernel (6);
+ *  - the histogram kernel: shared-memory reductions (1) and their fixed-point
+ *    form (7), lane-per-feature warp histograms (4) and their one-statistic-per-
+ *    warp form (5), 16-feature warp-private histograms (2), and with bins4 and
+ *    max_bins <= 16 the packed lane-per-feature kernel (6);
  *  - CTAs per cluster;
  *  - rows per CTA of a work unit.
  * Ownership and layout follow cbg_build_level. args->shape->tiles is ignored.

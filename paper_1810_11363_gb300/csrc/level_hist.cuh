@@ -40,7 +40,9 @@ size_t hist_smem_bytes(int nb_alloc) { return static_cast<size_t>(2) * nb_alloc 
 // histograms of 16 features per warp; kind 1: one shared histogram per CTA updated with
 // shared-memory float reductions; kind 3: the same with 64-bit compare-and-swap; kind 4:
 // lane-per-feature warp histograms with store forwarding; kind 5: the same with G and H
-// in separate warps. Kinds 4 and 5 read (g, h) by position, the others by row.
+// in separate warps; kind 6: kind 4 over 4-bit packed bins; kind 7: kind 1 with int32
+// fixed-point cells and integer reductions. Kinds 4-7 read (g, h) by position, the
+// others by row.
 struct HistConfig {
   int64_t n;
   int G, F, max_bins, nb_alloc, threads, cluster, kind = 0;
@@ -66,6 +68,45 @@ inline size_t wp_smem_bytes(int max_bins, int warps) {
 __device__ __forceinline__ void red_add(uint32_t addr, float v) {
   asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
+__device__ __forceinline__ void red_add_s32(uint32_t addr, int v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Fixed-point scale of the integer histogram: the largest e with 2^e * bound < 2^30, where
+// bound >= the sum of |v| over a CTA's rows (the float sum, inflated by 0.1% to cover its
+// rounding). Then every cell's sum of the rounded v * 2^e stays below 2^30 + rows < 2^31 in
+// magnitude. e is clamped to [-120, 120]; an all-zero chunk takes e = 0.
+__device__ __forceinline__ int fixed_scale_exp(float abs_sum) {
+  const float b = abs_sum * 1.001f;
+  if (!(b > 0.f)) return 0;
+  if (!(b < 1e30f)) return -120;
+  int k;
+  frexpf(b, &k);   // b < 2^k
+  const int e = 30 - k;
+  return e < -120 ? -120 : (e > 120 ? 120 : e);
+}
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }          // |e| <= 126
+
+// The 32-bit finaliser of MurmurHash3 (Appleby): a bijection that mixes every input bit.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// floor(x + u) for u in [0, 1): dithered rounding of a fixed-point value. Values that
+// repeat across rows (after a few trees g takes one value per leaf and label) would all
+// round the same way under round-to-nearest, and their errors would add up linearly; a
+// dither drawn per row makes the errors independent with mean zero. x - floor(x) is exact
+// in FP32, so only the comparison with 1 - u rounds. The error is below one unit.
+__device__ __forceinline__ int dither_round(float x, float u) {
+  const float xi = floorf(x);
+  return __float2int_rz(xi) + ((x - xi) + u >= 1.f ? 1 : 0);
+}
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double(static_cast<long long>(1023 + e) << 52); }
 
 // Persistent kernel over work units (leaf chunk x feature group), launched as thread-block
 // clusters of cs CTAs. Each CTA of a cluster accumulates the (G, H) histogram of its
@@ -80,6 +121,16 @@ __device__ __forceinline__ void red_add(uint32_t addr, float v) {
 // MODE 1: (G, H) interleaved as float2 [NB][32], updated with one 64-bit compare-and-swap
 // loop per (row, feature); on sm_103a the FP32 shared reduction is itself a
 // compare-and-swap loop, so this halves the atomic operations.
+// MODE 2: G and H in two int32 planes, updated with the native integer reduction
+// red.shared.add.u32 of fixed-point values floor(g * 2^eg + u), floor(h * 2^eh + u'), u
+// and u' dithers hashed from the position, with (g, h) read by position (the copies the
+// partition moves along with the rows). A pre-pass over the CTA's rows sums |g| and |h|,
+// and each scale is the largest power of two that keeps every cell below 2^31
+// (fixed_scale_exp). Integer sums are exact, so the CTA's histogram does not depend on
+// the order of its updates. The cluster step converts each CTA's cells with its own scale
+// (exact in FP64), sums them in rank order and rounds once to the FP32 partial. Per row
+// the error is below 2^-e <= 2.002 * (sum of |g| over the CTA's rows) * 2^-30, with mean
+// zero; integer-valued g with e >= 0 is exact.
 __device__ __forceinline__ void cas_add2(float2* p, float gx, float hy) {
   unsigned long long* a = reinterpret_cast<unsigned long long*>(p);
   unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(a);
@@ -116,11 +167,10 @@ __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs
                                           const float* const* peer, uint32_t sbase) {
   namespace cgr = cooperative_groups;
   constexpr int PLANE = NB * GROUP;
+  __shared__ int s_exp[2];   // MODE 2: this CTA's fixed-point exponents of G and H
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int j = lane >> 1, c = lane & 1;
-  uint32_t off[16];   // lane (j, c) updates feature 16c + (l + j) % 16 at iteration l
-#pragma unroll
-  for (int l = 0; l < 16; ++l) off[l] = sbase + 4u * static_cast<uint32_t>(c * 16 + ((l + j) & 15));
+  const uint32_t cbase = sbase + 64u * static_cast<uint32_t>(c);   // lane (j, c) updates feature 16c + (l + j) % 16 at step l
   const Plan* plan = P.plan;
   const int G = P.G;
   const int unit = item / G, grp = item - unit * G;
@@ -137,7 +187,7 @@ __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs
   const int p0 = seg_s + (chunk * cs + rank) * cr;
   const int p1 = min(seg_s + seg_c, p0 + cr);
   // zero the rows the problem's bins use (rows at or above max_bins are never read)
-  if (MODE == 0) {   // two planes [NB][32]
+  if (MODE != 1) {   // two planes [NB][32] (float, or int32 for MODE 2)
     const int rows4 = P.max_bins * GROUP / 4;   // float4 per plane
     for (int i = threadIdx.x; i < 2 * rows4; i += blockDim.x) {
       const int st = i / rows4;
@@ -147,17 +197,80 @@ __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs
     for (int i = threadIdx.x; i < P.max_bins * GROUP / 2; i += blockDim.x)
       reinterpret_cast<float4*>(hsh)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  __syncthreads();
-  const bool active = grp * GROUP + c * 16 < P.F;
-  const uint8_t* gbase = P.bins + static_cast<int64_t>(grp) * P.n * GROUP + c * 16;
   const GH* g = static_cast<const GH*>(P.g);
   const GH* h = static_cast<const GH*>(P.h);
   const uint32_t* order = P.order;
+  float scale_g = 1.f, scale_h = 1.f;
+  if constexpr (MODE == 2) {
+    // pre-pass: sums of |g| and |h| over this CTA's rows, reduced in a fixed order
+    __shared__ float s_abs[2][32];
+    float ag = 0.f, ah = 0.f;
+#pragma unroll 4
+    for (int pos = p0 + static_cast<int>(threadIdx.x); pos < p1; pos += blockDim.x) {
+      ag += fabsf(cbgd::load_gh(g, pos));   // (g, h) by position
+      ah += fabsf(cbgd::load_gh(h, pos));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ag += __shfl_down_sync(0xffffffffu, ag, o);
+      ah += __shfl_down_sync(0xffffffffu, ah, o);
+    }
+    if (lane == 0) {
+      s_abs[0][warp] = ag;
+      s_abs[1][warp] = ah;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float tg = 0.f, th = 0.f;
+      for (int w = 0; w < nw; ++w) {
+        tg += s_abs[0][w];
+        th += s_abs[1][w];
+      }
+      s_exp[0] = fixed_scale_exp(tg);
+      s_exp[1] = fixed_scale_exp(th);
+    }
+    __syncthreads();
+    scale_g = pow2f(s_exp[0]);
+    scale_h = pow2f(s_exp[1]);
+  }
+  __syncthreads();
+  const bool active = grp * GROUP + c * 16 < P.F;
+  const uint8_t* gbase = P.bins + static_cast<int64_t>(grp) * P.n * GROUP + c * 16;
   if (active) {
-    for (int pos = p0 + warp * 16 + j; pos < p1; pos += nw * 16) {
+    // software-pipelined over rows: the row id two rows ahead, and the next row's bin record
+    // and (g, h), are loaded before this row's 32 reductions issue, so their latency
+    // overlaps the shared-memory work. MODE 2 reads (g, h) by position.
+    const int stride = nw * 16;
+    int pos = p0 + warp * 16 + j;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    float gv = 0.f, hv = 0.f;
+    uint32_t rn = 0;   // row id at pos + stride
+    if (pos < p1) {
       const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(gbase + static_cast<int64_t>(row) * GROUP));
-      const float gv = cbgd::load_gh(g, row), hv = cbgd::load_gh(h, row);
+      v = __ldg(reinterpret_cast<const uint4*>(gbase + static_cast<int64_t>(row) * GROUP));
+      gv = cbgd::load_gh(g, MODE == 2 ? static_cast<uint32_t>(pos) : row);
+      hv = cbgd::load_gh(h, MODE == 2 ? static_cast<uint32_t>(pos) : row);
+      if (pos + stride < p1) rn = order ? order[pos + stride] : static_cast<uint32_t>(pos + stride);
+    }
+    for (; pos < p1; pos += stride) {
+      const int nxt = pos + stride, nn = nxt + stride;
+      uint32_t rnn = 0;
+      if (nn < p1) rnn = order ? order[nn] : static_cast<uint32_t>(nn);
+      uint4 vn = make_uint4(0u, 0u, 0u, 0u);
+      float gn = 0.f, hn = 0.f;
+      if (nxt < p1) {
+        vn = __ldg(reinterpret_cast<const uint4*>(gbase + static_cast<int64_t>(rn) * GROUP));
+        gn = cbgd::load_gh(g, MODE == 2 ? static_cast<uint32_t>(nxt) : rn);
+        hn = cbgd::load_gh(h, MODE == 2 ? static_cast<uint32_t>(nxt) : rn);
+      }
+      int qg = 0, qh = 0;
+      if (MODE == 2) {
+        // dithers of this position (the same for every feature group of the level)
+        const uint32_t d1 = fmix32(static_cast<uint32_t>(pos) * 0x9e3779b9u + 0x7f4a7c15u);
+        const uint32_t d2 = fmix32(d1);
+        qg = dither_round(gv * scale_g, static_cast<float>(d1 >> 8) * 0x1p-24f);   // gv * 2^e is exact
+        qh = dither_round(hv * scale_h, static_cast<float>(d2 >> 8) * 0x1p-24f);
+      }
       // rotate the 16 bytes so that byte l of R is byte (l + j) % 16 of v
       uint32_t w0 = v.x, w1 = v.y, w2 = v.z, w3 = v.w;
       const int q = (j >> 2) & 3, r = j & 3;
@@ -176,16 +289,24 @@ __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs
 #pragma unroll
       for (int l = 0; l < 16; ++l) {
         const uint32_t b = (R[l >> 2] >> (8 * (l & 3))) & (NB - 1);
+        const uint32_t fo = 4u * static_cast<uint32_t>((l + j) & 15);   // 4 x feature within the chunk
         if (MODE == 0) {
-          const uint32_t a = off[l] + b * (GROUP * 4);
+          const uint32_t a = cbase + fo + b * (GROUP * 4);
           red_add(a, gv);
           red_add(a + PLANE * 4, hv);
+        } else if (MODE == 2) {
+          const uint32_t a = cbase + fo + b * (GROUP * 4);
+          red_add_s32(a, qg);
+          red_add_s32(a + PLANE * 4, qh);
         } else {
-          // off[l] - sbase is 4 x (feature within the group)
-          const uint32_t f = (off[l] - sbase) >> 2;
+          const uint32_t f = static_cast<uint32_t>(c * 16) + (fo >> 2);
           cas_add2(reinterpret_cast<float2*>(hsh) + b * GROUP + f, gv, hv);
         }
       }
+      v = vn;
+      gv = gn;
+      hv = hn;
+      rn = rnn;
     }
   }
   cgr::this_cluster().sync();
@@ -195,12 +316,32 @@ __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs
   const int b0 = rank * bs;
   const int nbs = max(0, min(max_bins, b0 + bs) - b0);
   float* dst = P.partials + static_cast<int64_t>(item) * (2 * max_bins * GROUP);
-  for (int i = threadIdx.x; i < 2 * nbs * GROUP; i += blockDim.x) {
-    const int st = i / (nbs * GROUP), rem = i - st * (nbs * GROUP);
-    const int e = MODE == 0 ? st * PLANE + b0 * GROUP + rem : (b0 * GROUP + rem) * 2 + st;
-    float v = 0.f;
-    for (int r = 0; r < cs; ++r) v += peer[r][e];
-    dst[st * (max_bins * GROUP) + b0 * GROUP + rem] = v;
+  if constexpr (MODE == 2) {
+    // each peer's cells back to real units with that peer's scales (exact in FP64)
+    __shared__ double s_inv[2][16];
+    if (static_cast<int>(threadIdx.x) < cs) {
+      const int* e = cgr::this_cluster().map_shared_rank(s_exp, static_cast<int>(threadIdx.x));
+      s_inv[0][threadIdx.x] = pow2d(-e[0]);
+      s_inv[1][threadIdx.x] = pow2d(-e[1]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * nbs * GROUP; i += blockDim.x) {
+      const int st = i / (nbs * GROUP), rem = i - st * (nbs * GROUP);
+      const int e = st * PLANE + b0 * GROUP + rem;
+      double v = 0.0;
+#pragma unroll 4
+      for (int r = 0; r < cs; ++r) v += static_cast<double>(reinterpret_cast<const int*>(peer[r])[e]) * s_inv[st][r];
+      dst[st * (max_bins * GROUP) + b0 * GROUP + rem] = static_cast<float>(v);
+    }
+  } else {
+    for (int i = threadIdx.x; i < 2 * nbs * GROUP; i += blockDim.x) {
+      const int st = i / (nbs * GROUP), rem = i - st * (nbs * GROUP);
+      const int e = MODE == 0 ? st * PLANE + b0 * GROUP + rem : (b0 * GROUP + rem) * 2 + st;
+      float v = 0.f;
+#pragma unroll 4
+      for (int r = 0; r < cs; ++r) v += peer[r][e];
+      dst[st * (max_bins * GROUP) + b0 * GROUP + rem] = v;
+    }
   }
   cgr::this_cluster().sync();
 }
@@ -1228,7 +1369,9 @@ cbg_status hist_geom_mode(cbg_ctx* ctx, const HistConfig& L, HistGeom* g) {
 
 template <typename GH>
 cbg_status hist_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* g) {
-  return L.kind == 3 ? hist_geom_mode<GH, 1>(ctx, L, g) : hist_geom_mode<GH, 0>(ctx, L, g);
+  return L.kind == 3   ? hist_geom_mode<GH, 1>(ctx, L, g)
+         : L.kind == 7 ? hist_geom_mode<GH, 2>(ctx, L, g)
+                       : hist_geom_mode<GH, 0>(ctx, L, g);
 }
 
 template <typename GH>
@@ -1542,6 +1685,19 @@ cbg_status launch_hist(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins, c
                                               : level_hist_lane_kernel<GH>,
                                      bins, L.n, L.G, L.F, order, gg, hh, plan, L.max_bins, partials));
     return CBG_OK;
+  }
+  if (L.kind == 7) {
+    switch (L.nb_alloc) {
+      case 2: return launch_hist_nb<GH, 2, 2>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 4: return launch_hist_nb<GH, 4, 2>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 8: return launch_hist_nb<GH, 8, 2>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 16: return launch_hist_nb<GH, 16, 2>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 32: return launch_hist_nb<GH, 32, 2>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 64: return launch_hist_nb<GH, 64, 2>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 128: return launch_hist_nb<GH, 128, 2>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      case 256: return launch_hist_nb<GH, 256, 2>(ctx, L, bins, order, gg, hh, plan, partials, cs);
+      default: return ::cbg::fail(ctx, CBG_EINVAL, "unsupported bin allocation %d", L.nb_alloc);
+    }
   }
   if (L.kind == 3) {
     switch (L.nb_alloc) {

@@ -83,14 +83,17 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
   L->nb_alloc = pow2_at_least(L->max_bins);
   L->D = s->max_depth;
   CBG_REQUIRE(ctx, t.cluster >= 0 && t.cluster <= 16, "cluster must be in [0, 16]");
-  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 6, "kernel must be 0 (default), 1 (shared reductions), 2 "
+  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 7, "kernel must be 0 (default), 1 (shared reductions), 2 "
               "(warp-private, 16 features per warp), 3 (64-bit compare-and-swap), 4 (lane per feature), 5 (lane "
-              "per feature, one statistic per warp) or 6 (lane per feature over 4-bit packed bins)");
+              "per feature, one statistic per warp), 6 (lane per feature over 4-bit packed bins) or 7 (shared "
+              "integer reductions of fixed-point values)");
   CBG_REQUIRE(ctx, t.kernel != 6 || s->max_bins <= 16, "the 4-bit packed kernel needs max_bins <= 16");
-  L->kind = t.kernel == 2 ? 0 : (t.kernel >= 3 ? t.kernel : 1);
+  // the default (0) is the fixed-point shared-reduction kernel
+  L->kind = t.kernel == 0 ? 7 : t.kernel == 2 ? 0 : (t.kernel >= 3 ? t.kernel : 1);
   const bool lane_kind = L->kind == 4 || L->kind == 5 || L->kind == 6;
-  L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : (lane_kind ? 8192 : 2048);
-  L->cluster = t.cluster > 0 ? t.cluster : (lane_kind ? 2 : 8);
+  const bool fixed_kind = L->kind == 7;
+  L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : (lane_kind ? 8192 : fixed_kind ? 4096 : 2048);
+  L->cluster = t.cluster > 0 ? t.cluster : (lane_kind ? 2 : fixed_kind ? 4 : 8);
   L->threads = t.threads > 0 ? t.threads : 512;
   const int fit = static_cast<int>((227 * 1024) / hist_smem_bytes(L->nb_alloc));
   L->blocks_per_sm = std::max(1, std::min(t.blocks_per_sm > 0 ? t.blocks_per_sm : 3, fit));
@@ -1125,10 +1128,11 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   CBG_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &capturing));
   if (do_hist && capturing == cudaStreamCaptureStatusNone) st = prof_begin(ctx, &ev0, &ev1);
   if (st != CBG_OK) return st;
-  // the lane-per-feature kernels read (g, h) by position: the caller's arrays at the root
-  // (positions are rows), then the copies the previous level's partition moved along (for
-  // the shared-reduction kernel the copy costs the partition more than it saves)
-  const bool by_pos = L.kind == 4 || L.kind == 5 || L.kind == 6;
+  // the lane-per-feature kernels and the fixed-point kernel read (g, h) by position: the
+  // caller's arrays at the root (positions are rows), then the copies the previous level's
+  // partition moved along (for the FP32 shared-reduction kernel, which is bound by its
+  // compare-and-swap loops, the copy costs the partition more than it saves)
+  const bool by_pos = L.kind == 4 || L.kind == 5 || L.kind == 6 || L.kind == 7;
   const uint8_t* hist_bins = L.kind == 6 ? a->bins4 : a->bins;
   const void* g_pos = d == 0 ? a->g : at<char>(S, d % 2 == 1 ? L.o_gp_a : L.o_gp_b);
   const void* h_pos = d == 0 ? a->h : at<char>(S, d % 2 == 1 ? L.o_hp_a : L.o_hp_b);
@@ -1417,7 +1421,9 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
   if (trees == 0) return CBG_OK;
   // One histogram launch per level for all problems when they all use the shared-reduction
   // kernel with the same tiling (the plans are chunked for one cluster size); the other
-  // kernels of a level run per problem on the graph branches.
+  // kernels of a level run per problem on the graph branches. The batched histogram has
+  // no fixed-point form: problems on the default tiles (kernel 0) take its FP32 form with
+  // the default tiling's rows and cluster size.
   bool batch_hist = n_problems <= HIST_MAX_BATCH;
   Layout L0;
   {
@@ -1429,8 +1435,8 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
     Layout L;
     cbg_status st = make_layout(ctx, &problems[i].shape, &L);
     if (st != CBG_OK) return st;
-    batch_hist = L.kind == 1 && L.cluster == L0.cluster && L.rows_per_item == L0.rows_per_item &&
-                 L.threads == L0.threads;
+    batch_hist = (L.kind == 1 || problems[i].shape.tiles.kernel == 0) && L.cluster == L0.cluster &&
+                 L.rows_per_item == L0.rows_per_item && L.threads == L0.threads;
     nb_alloc = std::max(nb_alloc, L.nb_alloc);
   }
   std::vector<HistProblem*> tables;        // histogram tables, one per level
@@ -1440,7 +1446,9 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
   int begin_blocks = 0, score_blocks = 0, tile_blocks = 0, apply_blocks = 0;
   std::vector<int> reduce_blocks;
   if (batch_hist) {
-    cbg_status st = hist_cluster_size(ctx, hist_config(L0), &cs_plan);
+    HistConfig hc0 = hist_config(L0);
+    hc0.kind = 1;
+    cbg_status st = hist_cluster_size(ctx, hc0, &cs_plan);
     if (st != CBG_OK) return st;
     st = gh_dtype == CBG_F32 ? launch_hist_batched<float>(ctx, nb_alloc, nullptr, n_problems, L0.threads, cs_plan, true)
                              : launch_hist_batched<__nv_bfloat16>(ctx, nb_alloc, nullptr, n_problems, L0.threads,
@@ -1697,7 +1705,8 @@ cbg_status cbg_pack_bins4(cbg_ctx* ctx, const uint8_t* bins, int64_t n, int32_t 
 namespace {
 
 // The tilings the autotuner times: the shared-reduction kernel with clusters of 1, 2, 4
-// or 8 and 2048 or 4096 rows per CTA of a unit; the lane-per-feature kernel with clusters of 2
+// or 8 and 2048 or 4096 rows per CTA of a unit; its fixed-point form with clusters of 4 or 8
+// and 4096 or 8192 rows; the lane-per-feature kernel with clusters of 2
 // and 8192 or 16384 rows; its one-statistic-per-warp form with clusters of 2 or 4 and
 // 8192 or 16384 rows; the 16-feature warp-private kernel once; with 4-bit packed bins
 // (at most 16 bins), the packed lane-per-feature kernel with clusters of 2 and 8192 or
@@ -1713,6 +1722,8 @@ std::vector<cbg_tiles> autotune_candidates(bool packed) {
   };
   for (int cl : {1, 2, 4, 8})
     for (int r : {2048, 4096}) add(1, cl, r);
+  for (int cl : {4, 8})
+    for (int r : {4096, 8192}) add(7, cl, r);
   for (int r : {8192, 16384}) add(4, 2, r);
   for (int cl : {2, 4})
     for (int r : {8192, 16384}) add(5, cl, r);
