@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "trees/s and row·feature·bins/s at 1M×110 depth 6; HBM roofline %; batched vs plain"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "hist_kernel_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "hist_kernel_traffic_{}.txt")   # per --hist-kernel variant
 HIST_SOURCE = os.path.join(ROOT, "paper_1810_11363_gb300", "csrc", "level_hist.cuh")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -45,7 +45,7 @@ def parse_args():
     p.add_argument("--ref-sample-trees", type=int, default=2)
     p.add_argument("--no-graph", action="store_true", help="launch every kernel from the host instead of "
                                                            "replaying one captured tree")
-    p.add_argument("--hist-kernel", choices=["pair", "lane", "wp", "red", "int", "cas64"], default="int",
+    p.add_argument("--hist-kernel", choices=["pair", "lane", "wp", "red", "int", "cas64"], default="red",
                    help="warp-private atomic-free histograms (wp), shared-memory float reductions (red) or "
                         "shared-memory integer reductions of fixed-point values (int)")
     p.add_argument("--cluster", type=int, default=0, help="CTAs per histogram cluster (0 = library default)")
@@ -55,6 +55,8 @@ def parse_args():
                    help="problems of the batched_256 workload for the batched-vs-plain comparison (0 = skip)")
     p.add_argument("--batched-trees", type=int, default=20)
     p.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-storage comparison step")
+    p.add_argument("--no-fixed-point-form", action="store_true",
+                   help="skip the fixed-point histogram comparison step")
     p.add_argument("--scorer-trees", type=int, default=8000,
                    help="trees of the model-prediction measurement (0 = skip)")
     p.add_argument("--ordered-trees", type=int, default=200,
@@ -175,7 +177,7 @@ def recorded_traffic_per_row(variant):
     """DRAM bytes per histogrammed row from the committed ncu summary, if it was taken on
     the current histogram source and the given kernel variant; else None."""
     try:
-        with open(TRAFFIC_FILE) as fh:
+        with open(TRAFFIC_FILE.format(variant)) as fh:
             kv = dict(line.split(None, 1) for line in fh if line.strip() and not line.startswith("#"))
         if kv.get("source_sha256_16", "").strip() != hist_source_hash():
             return None
@@ -331,23 +333,31 @@ def paper_setting_bench(ctx, dev, trees, n=400_000, F=2000, borders=15, depth=6)
     cat = torch.zeros((0, n), dtype=torch.int32, device=dev)
     prep = train.preprocess(ctx, x, cat, y, "binary", borders, seed=0)
     del x
-    tiles, _ = train.autotune(ctx, prep, y, "logloss", depth)
-    bufs = train.alloc_fit(prep, depth, trees, tiles=tiles)
     stream = torch.cuda.current_stream(dev)
-    train.fit(ctx, prep, y, "logloss", depth, min(trees, 5), 0.1, 3.0, bufs=bufs, use_graph=True)   # warm-up
-    bufs.pred.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    train.fit(ctx, prep, y, "logloss", depth, trees, 0.1, 3.0, bufs=bufs, use_graph=True)
-    e1.record(stream)
-    e1.synchronize()
-    cbg.cbg_sync(ctx)
-    ms = e0.elapsed_time(e1)
+
+    def timed(fixed_point):
+        tiles, _ = train.autotune(ctx, prep, y, "logloss", depth, fixed_point=fixed_point)
+        bufs = train.alloc_fit(prep, depth, trees, tiles=tiles)
+        train.fit(ctx, prep, y, "logloss", depth, min(trees, 5), 0.1, 3.0, bufs=bufs, use_graph=True)   # warm-up
+        bufs.pred.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        train.fit(ctx, prep, y, "logloss", depth, trees, 0.1, 3.0, bufs=bufs, use_graph=True)
+        e1.record(stream)
+        e1.synchronize()
+        cbg.cbg_sync(ctx)
+        return e0.elapsed_time(e1), tiles, training_loss("logloss", y, bufs.pred)
+
+    ms, tiles, loss = timed(False)
+    ms_fp, tiles_fp, loss_fp = timed(True)
     return {"workload": f"Epsilon-shaped {n} x {F} dense N(0,1), logistic labels, {borders} borders "
                         f"({prep.max_bins} bins), depth {depth}, {trees} trees, lr 0.1, L2 3",
-            "ms_per_tree": ms / trees, "trees_per_s": trees / (ms / 1e3),
+            "ms_per_tree": ms / trees, "trees_per_s": trees / (ms / 1e3), "final_loss": loss,
             "hist_tiles": {"kernel": tiles["kernel"], "cluster": tiles["cluster"],
                            "rows_per_item": tiles["rows_per_item"]},
+            "fixed_point_allowed": {"ms_per_tree": ms_fp / trees, "final_loss": loss_fp,
+                                    "hist_tiles": {"kernel": tiles_fp["kernel"], "cluster": tiles_fp["cluster"],
+                                                   "rows_per_item": tiles_fp["rows_per_item"]}},
             "paper_context": "CatBoost GPU, Epsilon, 15 bins, depth 6, classic scheme: 17.9 ms/tree on "
                              "an NVIDIA P100 (not the same data or hardware)"}
 
@@ -630,6 +640,43 @@ def run_ours(args):
         forms["bf16"] = {"trees_per_s": T / (e0.elapsed_time(e1) / 1e3), "final_loss": l16,
                          "rel_final_loss_diff_vs_f32": abs(l16 - forms["f32"]["final_loss"]) /
                          abs(forms["f32"]["final_loss"])}
+    # the opt-in fixed-point histogram (int32 cells, native shared integer reductions; its
+    # shared-memory accumulation is not FP32) against FP32 on the same workload
+    if not args.no_fixed_point_form and args.hist_kernel == "red":
+        tiles_fp = {"kernel": 7, "cluster": 4, "rows_per_item": 4096}
+        bufs_fp = train.alloc_fit(prep0, D, T, args.gh, tiles=tiles_fp)
+        step(bufs_fp)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(bufs_fp)
+        e1.record(stream)
+        e1.synchronize()
+        ms_fp = e0.elapsed_time(e1)
+        l_fp = training_loss(w.loss, y, bufs_fp.pred)
+        cbg.cbg_tree_rows_histogrammed(ctx, bufs_fp.shape, bufs_fp.state, reset=True)
+        cbg.cbg_profile_read(ctx, reset=True)
+        cbg.cbg_profile_enable(ctx, True)
+        step(bufs_fp, graph=False)
+        cbg.cbg_profile_enable(ctx, False)
+        fp_hist_ms, fp_launches = cbg.cbg_profile_read(ctx, reset=True)
+        fp_rows = cbg.cbg_tree_rows_histogrammed(ctx, bufs_fp.shape, bufs_fp.state, reset=True)
+        fp_upd = fp_rows * prep0.F / (fp_hist_ms / 1e3) if fp_hist_ms > 0 else None
+        fp_clk = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        fp_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp_peak, _ = measured_peak_hbm()
+        fp_achieved = fp_rows * (prep0.F + 2 * (4 if args.gh == "f32" else 2)) / (fp_hist_ms / 1e3) / 1e9 \
+            if fp_hist_ms > 0 else None
+        forms["fixed_point"] = {
+            "trees_per_s": T / (ms_fp / 1e3), "final_loss": l_fp,
+            "rel_final_loss_diff_vs_f32": abs(l_fp - forms["f32"]["final_loss"]) / abs(forms["f32"]["final_loss"]),
+            "hist_tiles": tiles_fp, "accumulation": "int32 fixed-point cells in shared memory, dithered rounding, "
+                                                    "FP64 cross-cluster (not the FP32 shared-memory accumulation)",
+            "hist_avg_launch_us": fp_hist_ms * 1e3 / max(fp_launches, 1),
+            "hist_hbm_frac": (fp_achieved / fp_peak) if (fp_achieved and fp_peak) else None,
+            "hist_smem_updates_per_sm_clk": fp_upd / (fp_sms * fp_clk * 1e6) if fp_upd else None,
+            "timing": "one step (preprocessing + trees) with CUDA events, after one untimed step; histogram "
+                      "launches timed in one more step with host launches"}
     batched = None
     if args.batched_problems > 0 and rank == 0:
         batched = batched_comparison(ctx, args.batched_problems, args.batched_trees, dev)

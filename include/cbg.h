@@ -79,17 +79,17 @@ typedef struct cbg_split {
  * same with G and H in separate warps, 6 = lane-per-feature over the 4-bit
  * packed bins of cbg_pack_bins4 (max_bins <= 16; the level arguments carry
  * bins4), 7 = one shared histogram per CTA of int32 fixed-point cells updated
- * with shared-memory integer reductions (the default, 0; 4096 rows per CTA and
- * clusters of 4 by default). Kernel 7 rounds each (g, h) of a CTA's rows to a
+ * with shared-memory integer reductions (4096 rows per CTA and clusters of 4 by
+ * default). The default (0) is kernel 1, whose shared-memory accumulation is FP32.
+ * Kernel 7 is an opt-in form that does not accumulate in FP32: it rounds each (g, h) of a CTA's rows to a
  * multiple of 2^-e, e the largest exponent with 2^e * 1.001 * S < 2^30 for S the
  * sum of |g| (of |h| for H) over those rows, with a dither hashed from the row's
  * position (floor(v 2^e + u), u in [0, 1)): the rounding error of a row is below
  * 2.002 * S * 2^-30 with mean zero (integer values are exact), the sums are exact
  * and do not depend on the order of the updates, and each cluster's cells are
- * rounded once to the FP32 partial.
- * cbg_boost_batched has no batched fixed-point histogram: problems on the default
- * kernel there take kernel 1 with the default tiling's rows and cluster.
- * Zero fields take library defaults. */
+ * rounded once to the FP32 partial. Its error per cell is therefore bounded by the
+ * cell's rows times that per-row bound, not by a fraction of the cell's own sum of |g|.
+ * cbg_boost_batched batches only kernel 1. Zero fields take library defaults. */
 typedef struct cbg_tiles {
   int32_t slab_chunks;
   int32_t rows_per_item;
@@ -444,10 +444,11 @@ cbg_status cbg_predict(cbg_ctx* ctx, const cbg_predict_args* args);
  * `depth` levels of one tree per timing (cbg_tree_begin + cbg_build_level on the
  * ctx stream, CUDA events), and writes the fastest to *best and its mean device
  * time per tree (ms) to *best_ms. The candidates vary:
- *  - the histogram kernel: shared-memory reductions (1) and their fixed-point
- *    form (7), lane-per-feature warp histograms (4) and their one-statistic-per-
- *    warp form (5), 16-feature warp-private histograms (2), and with bins4 and
- *    max_bins <= 16 the packed lane-per-feature kernel (6);
+ *  - the histogram kernel: shared-memory reductions (1), lane-per-feature warp
+ *    histograms (4) and their one-statistic-per-warp form (5), 16-feature
+ *    warp-private histograms (2), with bins4 and max_bins <= 16 the packed
+ *    lane-per-feature kernel (6), and with fixed_point != 0 the fixed-point
+ *    shared-reduction kernel (7);
  *  - CTAs per cluster;
  *  - rows per CTA of a work unit.
  * Ownership and layout follow cbg_build_level. args->shape->tiles is ignored.
@@ -474,6 +475,7 @@ typedef struct cbg_autotune_args {
   int32_t reps;
   const uint8_t* bins4;        /* device 4-bit packed bins (cbg_pack_bins4) or NULL; with
                                   max_bins <= 16 the packed kernel is a candidate too */
+  int32_t fixed_point;         /* nonzero: the fixed-point kernel (7) is a candidate too */
 } cbg_autotune_args;
 
 /* 4-bit packed bins (Section 5 "Dense numerical features": features with at most

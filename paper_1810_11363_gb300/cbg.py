@@ -48,7 +48,7 @@ class AutotuneArgs(C.Structure):
     _fields_ = [("shape", C.POINTER(TreeShape)), ("state", c_vp), ("state_bytes", C.c_size_t),
                 ("bins", c_vp), ("bins_t", c_vp), ("n_borders", c_vp), ("g", c_vp), ("h", c_vp),
                 ("gh_dtype", c_i32), ("depth", c_i32), ("l2", c_f64), ("leaf", c_vp), ("splits", c_vp),
-                ("child_totals", c_vp), ("reps", c_i32), ("bins4", c_vp)]
+                ("child_totals", c_vp), ("reps", c_i32), ("bins4", c_vp), ("fixed_point", c_i32)]
 
 
 class PredictArgs(C.Structure):
@@ -352,12 +352,13 @@ def cbg_autotune_state_bytes(shape: TreeShape) -> int:
 
 
 def cbg_autotune_tiles(ctx: Context, shape: TreeShape, state, bins, n_borders, g, h, gh_dtype: str, depth: int,
-                       l2: float, leaf, splits, child_totals, bins_t=None, reps: int = 2, bins4=None):
+                       l2: float, leaf, splits, child_totals, bins_t=None, reps: int = 2, bins4=None,
+                       fixed_point: bool = False):
     """Fastest histogram tiling for this problem (dict of cbg_tiles fields) and its device
-    time per tree in ms."""
+    time per tree in ms. fixed_point: the fixed-point kernel (7) is a candidate too."""
     a = AutotuneArgs(C.pointer(shape), _p(state), state.numel() * state.element_size(), _p(bins), _p(bins_t),
                      _p(n_borders), _p(g), _p(h), DTYPE[gh_dtype], depth, l2, _p(leaf), _p(splits),
-                     _p(child_totals), reps, _p(bins4))
+                     _p(child_totals), reps, _p(bins4), 1 if fixed_point else 0)
     best = Tiles()
     ms = c_f64()
     ctx.check(ctx.lib.cbg_autotune_tiles(ctx.h, C.byref(a), C.byref(best), C.byref(ms)), "cbg_autotune_tiles")

@@ -88,8 +88,7 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
               "per feature, one statistic per warp), 6 (lane per feature over 4-bit packed bins) or 7 (shared "
               "integer reductions of fixed-point values)");
   CBG_REQUIRE(ctx, t.kernel != 6 || s->max_bins <= 16, "the 4-bit packed kernel needs max_bins <= 16");
-  // the default (0) is the fixed-point shared-reduction kernel
-  L->kind = t.kernel == 0 ? 7 : t.kernel == 2 ? 0 : (t.kernel >= 3 ? t.kernel : 1);
+  L->kind = t.kernel == 2 ? 0 : (t.kernel >= 3 ? t.kernel : 1);
   const bool lane_kind = L->kind == 4 || L->kind == 5 || L->kind == 6;
   const bool fixed_kind = L->kind == 7;
   L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : (lane_kind ? 8192 : fixed_kind ? 4096 : 2048);
@@ -1421,9 +1420,7 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
   if (trees == 0) return CBG_OK;
   // One histogram launch per level for all problems when they all use the shared-reduction
   // kernel with the same tiling (the plans are chunked for one cluster size); the other
-  // kernels of a level run per problem on the graph branches. The batched histogram has
-  // no fixed-point form: problems on the default tiles (kernel 0) take its FP32 form with
-  // the default tiling's rows and cluster size.
+  // kernels of a level run per problem on the graph branches.
   bool batch_hist = n_problems <= HIST_MAX_BATCH;
   Layout L0;
   {
@@ -1435,8 +1432,8 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
     Layout L;
     cbg_status st = make_layout(ctx, &problems[i].shape, &L);
     if (st != CBG_OK) return st;
-    batch_hist = (L.kind == 1 || problems[i].shape.tiles.kernel == 0) && L.cluster == L0.cluster &&
-                 L.rows_per_item == L0.rows_per_item && L.threads == L0.threads;
+    batch_hist = L.kind == 1 && L.cluster == L0.cluster && L.rows_per_item == L0.rows_per_item &&
+                 L.threads == L0.threads;
     nb_alloc = std::max(nb_alloc, L.nb_alloc);
   }
   std::vector<HistProblem*> tables;        // histogram tables, one per level
@@ -1446,9 +1443,7 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
   int begin_blocks = 0, score_blocks = 0, tile_blocks = 0, apply_blocks = 0;
   std::vector<int> reduce_blocks;
   if (batch_hist) {
-    HistConfig hc0 = hist_config(L0);
-    hc0.kind = 1;
-    cbg_status st = hist_cluster_size(ctx, hc0, &cs_plan);
+    cbg_status st = hist_cluster_size(ctx, hist_config(L0), &cs_plan);
     if (st != CBG_OK) return st;
     st = gh_dtype == CBG_F32 ? launch_hist_batched<float>(ctx, nb_alloc, nullptr, n_problems, L0.threads, cs_plan, true)
                              : launch_hist_batched<__nv_bfloat16>(ctx, nb_alloc, nullptr, n_problems, L0.threads,
@@ -1705,13 +1700,13 @@ cbg_status cbg_pack_bins4(cbg_ctx* ctx, const uint8_t* bins, int64_t n, int32_t 
 namespace {
 
 // The tilings the autotuner times: the shared-reduction kernel with clusters of 1, 2, 4
-// or 8 and 2048 or 4096 rows per CTA of a unit; its fixed-point form with clusters of 4 or 8
-// and 4096 or 8192 rows; the lane-per-feature kernel with clusters of 2
+// or 8 and 2048 or 4096 rows per CTA of a unit; on request its fixed-point form with
+// clusters of 4 or 8 and 4096 or 8192 rows; the lane-per-feature kernel with clusters of 2
 // and 8192 or 16384 rows; its one-statistic-per-warp form with clusters of 2 or 4 and
 // 8192 or 16384 rows; the 16-feature warp-private kernel once; with 4-bit packed bins
 // (at most 16 bins), the packed lane-per-feature kernel with clusters of 2 and 8192 or
 // 16384 rows.
-std::vector<cbg_tiles> autotune_candidates(bool packed) {
+std::vector<cbg_tiles> autotune_candidates(bool packed, bool fixed_point) {
   std::vector<cbg_tiles> c;
   auto add = [&](int kernel, int cluster, int rows) {
     cbg_tiles t{};
@@ -1722,8 +1717,9 @@ std::vector<cbg_tiles> autotune_candidates(bool packed) {
   };
   for (int cl : {1, 2, 4, 8})
     for (int r : {2048, 4096}) add(1, cl, r);
-  for (int cl : {4, 8})
-    for (int r : {4096, 8192}) add(7, cl, r);
+  if (fixed_point)
+    for (int cl : {4, 8})
+      for (int r : {4096, 8192}) add(7, cl, r);
   for (int r : {8192, 16384}) add(4, 2, r);
   for (int cl : {2, 4})
     for (int r : {8192, 16384}) add(5, cl, r);
@@ -1767,7 +1763,7 @@ cbg_status tune_tree(cbg_ctx* ctx, const cbg_tree_shape* s, const cbg_autotune_a
 cbg_status cbg_autotune_state_bytes(const cbg_tree_shape* shape, size_t* bytes) {
   if (!shape || !bytes) return CBG_EINVAL;
   size_t mx = 0;
-  for (const cbg_tiles& t : autotune_candidates(shape->max_bins <= 16)) {
+  for (const cbg_tiles& t : autotune_candidates(shape->max_bins <= 16, true)) {
     cbg_tree_shape s = *shape;
     s.tiles = t;
     Layout L;
@@ -1798,7 +1794,8 @@ cbg_status cbg_autotune_tiles(cbg_ctx* ctx, const cbg_autotune_args* a, cbg_tile
   double best_t = INFINITY;
   cbg_tiles best_c{};
   cbg_status result = CBG_OK;
-  for (const cbg_tiles& cand : autotune_candidates(a->bins4 != nullptr && a->shape->max_bins <= 16)) {
+  for (const cbg_tiles& cand : autotune_candidates(a->bins4 != nullptr && a->shape->max_bins <= 16,
+                                                   a->fixed_point != 0)) {
     cbg_tree_shape s = *a->shape;
     s.tiles = cand;
     Layout L;

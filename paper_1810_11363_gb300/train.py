@@ -300,9 +300,10 @@ def rowmajor_from_grouped(flat: np.ndarray, n: int, F_pad: int) -> np.ndarray:
 
 
 def autotune(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, l2: float = 3.0, gh_dtype: str = "f32",
-             reps: int = 2):
+             reps: int = 2, fixed_point: bool = False):
     """Fastest histogram tiling for this problem (cbg_autotune_tiles), timed on trees built
-    from its gradients at prediction 0. Returns (tiles dict, ms per tree)."""
+    from its gradients at prediction 0. fixed_point: also time the fixed-point kernel,
+    whose shared-memory accumulation is not FP32. Returns (tiles dict, ms per tree)."""
     import torch
     dev = prep.bins.device
     shape = cbg.make_shape(prep.n, prep.F, prep.F_pad, prep.max_bins, depth)
@@ -315,7 +316,8 @@ def autotune(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, l2: flo
     splits = torch.empty((depth, 2), dtype=torch.float64, device=dev)
     child = torch.empty((1 << depth, 2), dtype=torch.float64, device=dev)
     return cbg.cbg_autotune_tiles(ctx, shape, state, prep.bins, prep.n_borders, g, h, gh_dtype, depth, l2, leaf,
-                                  splits, child, bins_t=prep.bins_t, reps=reps, bins4=prep.bins4)
+                                  splits, child, bins_t=prep.bins_t, reps=reps, bins4=prep.bins4,
+                                  fixed_point=fixed_point)
 
 
 # Tilings timed on a whole batch: the shared-reduction kernel (whose histograms of a level
