@@ -61,3 +61,18 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("LOCAL_RANK", "1")
     args = argparse.Namespace(trees=1000, steps=1, warmup=1, ref_sample_trees=1)
     assert bench.run_reference(args) == 0     # returns before any work
+
+
+def test_recorded_traffic_needs_the_same_kernel_source_and_variant(tmp_path, monkeypatch):
+    """bench.py reports the ncu DRAM traffic of the histogram kernel only from a capture
+    taken on the current kernel source and on the selected --hist-kernel variant."""
+    import bench
+    h = bench.hist_source_hash()
+    (tmp_path / "hist_kernel_traffic_red.txt").write_text(
+        f"# comment\nsource_sha256_16 {h}\nkernel_variant red\ndram_bytes_per_row 321.4\n")
+    (tmp_path / "hist_kernel_traffic_int.txt").write_text(
+        "source_sha256_16 0000000000000000\nkernel_variant int\ndram_bytes_per_row 285.1\n")
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "hist_kernel_traffic_{}.txt"))
+    assert bench.recorded_traffic_per_row("red") == 321.4
+    assert bench.recorded_traffic_per_row("int") is None      # taken on another source
+    assert bench.recorded_traffic_per_row("lane") is None     # no capture for the variant
