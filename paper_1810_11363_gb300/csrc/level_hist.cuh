@@ -68,6 +68,7 @@ inline size_t wp_smem_bytes(int max_bins, int warps) {
 __device__ __forceinline__ void red_add(uint32_t addr, float v) {
   asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
+// Signed int32 reduction: two's-complement addition is the unsigned one.
 __device__ __forceinline__ void red_add_s32(uint32_t addr, int v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
@@ -101,12 +102,15 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
 // repeat across rows (after a few trees g takes one value per leaf and label) would all
 // round the same way under round-to-nearest, and their errors would add up linearly; a
 // dither drawn per row makes the errors independent with mean zero. x - floor(x) is exact
-// in FP32, so only the comparison with 1 - u rounds. The error is below one unit.
+// in FP32; only its sum with u rounds, which moves the result only when that sum lies
+// within an ulp of 1. The error is below one unit.
 __device__ __forceinline__ int dither_round(float x, float u) {
   const float xi = floorf(x);
   return __float2int_rz(xi) + ((x - xi) + u >= 1.f ? 1 : 0);
 }
-__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double(static_cast<long long>(1023 + e) << 52); }
+__device__ __forceinline__ double pow2d(int e) {   // |e| <= 1022
+  return __longlong_as_double(static_cast<long long>(1023 + e) << 52);
+}
 
 // Persistent kernel over work units (leaf chunk x feature group), launched as thread-block
 // clusters of cs CTAs. Each CTA of a cluster accumulates the (G, H) histogram of its
