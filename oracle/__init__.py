@@ -76,7 +76,7 @@ def lib():
                 "or_apply_leaf_values": (None, [u16p, i64, f64p, f64, f64p]),
                 "or_loss": (f64, [i32, f32p, f64p, i64]),
                 "or_fit": (None, [u8p, i64, i32, i32, i32p, i32, f32p, i32, i32, i32, i32, f64, f64,
-                                  f64p, i32p, i32p, f64p, f64p, f64p, f64p]),
+                                  f64p, i32p, i32p, f64p, f64p, f64p, f64p, i32p, i32p, f64, i32p]),
                 "or_ts_full": (None, [u32p, f32p, i64, f64, f64, u32p, i64, f32p]),
                 "or_predict": (None, [u8p, i64, i32, i32p, i32p, f64p, i32, i32, f64, f64p]),
                 "or_ordered_sup_size": (i64, [i64]),
@@ -85,7 +85,8 @@ def lib():
                                          u32p, f64, f64, i32, i32, f64p, i32p, i32p, f64p, f64p, f64p, f64p, i32p,
                                          i32p, f32p]),
                 "or_fit_ordered": (None, [u8p, i64, i32, i32, i32p, i32, f32p, i32, i32, i32, f64, f64, u32p, i32,
-                                          f64p, i32p, i32p, f64p, f64p, f64p, f64p, f64p]),
+                                          f64p, i32p, i32p, f64p, f64p, f64p, f64p, f64p, i32p, i32p, f64,
+                                          i32p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -253,10 +254,33 @@ def loss(loss_name: str, y, pred) -> float:
     return float(lib().or_loss(LOSS[loss_name], _p(y, _f32), _p(pred, _f64), y.shape[0]))
 
 
+FOLLOW_TOL = 1e-6   # relative score margin of a near-tie (the split-identity tolerance)
+
+
+def _follow_args(follow, T, D):
+    """follow: None, or another implementation's splits as (split_f [T][D], split_k [T][D])
+    or a structured array with fields feature/border. -> (ff, fk, followed) arrays."""
+    if follow is None:
+        return None, None, None
+    if isinstance(follow, np.ndarray) and follow.dtype.names:
+        ff, fk = follow["feature"], follow["border"]
+    else:
+        ff, fk = follow
+    ff = _c(np.asarray(ff)[:T, :D], np.int32)
+    fk = _c(np.asarray(fk)[:T, :D], np.int32)
+    assert ff.shape == (T, D) and fk.shape == (T, D)
+    return ff, fk, np.zeros((T, D), np.int32)
+
+
 def fit(bins, F: int, n_borders, y, loss_name: str, depth: int, trees: int, lr: float, l2: float,
-        dtype: str = "f32", pred=None):
+        dtype: str = "f32", pred=None, follow=None, follow_tol: float = FOLLOW_TOL):
     """Classic boosting of `trees` oblivious trees. Returns a dict with pred (FP64),
-    split_f/split_k/score/second [T][D], leaf_values [T][2^D], losses [T]."""
+    split_f/split_k/score/second [T][D], leaf_values [T][2^D], losses [T].
+    follow: another implementation's splits [T][D]; at a level where that split scores
+    within follow_tol x |best| of the oracle's best, the oracle takes it (lock step
+    through near-ties). "followed" [T][D] then holds 0 (same split), 1 (near-tie,
+    followed) or -1 (the followed split scores lower by more than the margin; the oracle
+    kept its own)."""
     bins = _c(bins, np.uint8)
     n, F_pad = bins.shape
     nb = _c(n_borders, np.int32)
@@ -270,11 +294,13 @@ def fit(bins, F: int, n_borders, y, loss_name: str, depth: int, trees: int, lr: 
     s2 = np.empty((T, D), np.float64)
     lv = np.empty((T, 1 << D), np.float64)
     losses = np.empty(T, np.float64)
+    ff, fk, fl = _follow_args(follow, T, D)
     lib().or_fit(_p(bins, _u8), n, F_pad, F, _p(nb, _i32), max_bins, _p(y, _f32), LOSS[loss_name],
                  DTYPE[dtype], D, T, lr, l2, _p(pred, _f64), _p(sf, _i32), _p(sk, _i32),
-                 _p(ss, _f64), _p(s2, _f64), _p(lv, _f64), _p(losses, _f64))
+                 _p(ss, _f64), _p(s2, _f64), _p(lv, _f64), _p(losses, _f64), _p(ff, _i32), _p(fk, _i32),
+                 follow_tol, _p(fl, _i32))
     return {"pred": pred, "split_f": sf, "split_k": sk, "score": ss, "second": s2,
-            "leaf_values": lv, "losses": losses, "max_bins": max_bins}
+            "leaf_values": lv, "losses": losses, "max_bins": max_bins, "followed": fl}
 
 
 def ordered_sup_size(n: int) -> int:
@@ -292,10 +318,11 @@ def ordered_sup_offsets(n: int) -> np.ndarray:
 
 
 def fit_ordered(bins, F: int, n_borders, y, loss_name: str, depth: int, trees: int, lr: float, l2: float,
-                perms, pred=None):
+                perms, pred=None, follow=None, follow_tol: float = FOLLOW_TOL):
     """Ordered boosting (Section 3, Algorithm 1 with the log-scale supporting models).
     bins: [s][n][F_pad], permutation q's bins (row order); perms: [s][n] (position -> row).
-    Returns the dict of fit() plus sup [s][n_sup], the supporting models' values."""
+    Returns the dict of fit() plus sup [s][n_sup], the supporting models' values.
+    follow / follow_tol: the lock step of fit()."""
     bins = _c(bins, np.uint8)
     s, n, F_pad = bins.shape
     perms = _c(perms, np.uint32)
@@ -312,11 +339,13 @@ def fit_ordered(bins, F: int, n_borders, y, loss_name: str, depth: int, trees: i
     lv = np.empty((T, 1 << D), np.float64)
     losses = np.empty(T, np.float64)
     sup = np.empty((s, ordered_sup_size(n)), np.float64)
+    ff, fk, fl = _follow_args(follow, T, D)
     lib().or_fit_ordered(_p(bins, _u8), n, F_pad, F, _p(nb, _i32), max_bins, _p(y, _f32), LOSS[loss_name], D, T,
                          lr, l2, _p(perms, _u32), s, _p(pred, _f64), _p(sf, _i32), _p(sk, _i32), _p(ss, _f64),
-                         _p(s2, _f64), _p(lv, _f64), _p(losses, _f64), _p(sup, _f64))
+                         _p(s2, _f64), _p(lv, _f64), _p(losses, _f64), _p(sup, _f64), _p(ff, _i32), _p(fk, _i32),
+                         follow_tol, _p(fl, _i32))
     return {"pred": pred, "split_f": sf, "split_k": sk, "score": ss, "second": s2,
-            "leaf_values": lv, "losses": losses, "max_bins": max_bins, "sup": sup}
+            "leaf_values": lv, "losses": losses, "max_bins": max_bins, "sup": sup, "followed": fl}
 
 
 def combo_ids(items, cat, bins):

@@ -357,6 +357,27 @@ double or_loss(int loss, const float* y, const double* pred, int64_t n) {
   return loss == LOSS_RMSE ? std::sqrt(s) : s;
 }
 
+// ------------------------------------------------------------------ lock step
+// Where the best and the runner-up split differ by at most a rounding-sized margin, the
+// paper's greedy search (Section 3, one split per level, Section 4 "Fast scorer") does not
+// fix the choice: an implementation that accumulates in another order may take either.
+// To follow such an implementation through a whole run, the oracle can be given its
+// split for every level ("follow"). At a level where the followed split (ff, fk) is not
+// the oracle's own best, the oracle takes it if its score here is within
+// tol * |best| of the best (a near-tie: flag 1) and keeps its own otherwise (flag -1:
+// a genuine disagreement, which a test reports). Flag 0: the two agree. Only the choice
+// changes; every score, total and leaf value is computed exactly as without a follow.
+static int follow_split(const double* scores, int F, int K, const int* n_borders, int ff, int fk, double tol,
+                        int* bf, int* bk, double bs) {
+  if (ff == *bf && fk == *bk) return 0;
+  if (ff < 0 || ff >= F || fk < 0 || fk >= n_borders[ff] || fk >= K) return -1;
+  const double sf = scores[static_cast<int64_t>(ff) * K + fk];
+  if (!(bs - sf <= tol * std::fabs(bs))) return -1;
+  *bf = ff;
+  *bk = fk;
+  return 1;
+}
+
 // ------------------------------------------------------------------- boosting
 // Classic (non-ordered) boosting of T oblivious trees of depth D on quantised
 // features, starting from pred = 0 (pred is in/out, FP64). Per tree: gradients
@@ -365,10 +386,13 @@ double or_loss(int loss, const float* y, const double* pred, int64_t n) {
 // Outputs per tree t and level d (arrays [T][D]): chosen feature and border,
 // best and second-best score; per tree: leaf values v [T][2^D] (before lr) and
 // the training loss after the tree [T].
+// follow_f / follow_k (optional, [T][D]): another implementation's splits, taken at
+// near-ties within follow_tol (see follow_split); followed [T][D] receives the flags.
 void or_fit(const uint8_t* bins, int64_t n, int F_pad, int F, const int* n_borders, int max_bins,
             const float* y, int loss, int dtype, int depth, int trees, double lr, double l2,
             double* pred, int* split_f, int* split_k, double* split_score, double* split_second,
-            double* leaf_values, double* losses) {
+            double* leaf_values, double* losses, const int* follow_f, const int* follow_k, double follow_tol,
+            int* followed) {
   const int L = 1 << depth;
   std::vector<double> g(n), h(n);
   std::vector<uint16_t> leaf(n);
@@ -385,6 +409,12 @@ void or_fit(const uint8_t* bins, int64_t n, int F_pad, int F, const int* n_borde
       double bs, ss;
       or_split_scores(hist.data(), nl, F, n_borders, max_bins, l2, scores.data(), &bf, &bk, &bs,
                       &ss);
+      if (follow_f && bf >= 0)
+        followed[t * depth + d] = follow_split(scores.data(), F, max_bins > 1 ? max_bins - 1 : 1, n_borders,
+                                               follow_f[t * depth + d], follow_k[t * depth + d], follow_tol, &bf,
+                                               &bk, bs);
+      else if (follow_f)
+        followed[t * depth + d] = follow_f[t * depth + d] == bf ? 0 : -1;
       split_f[t * depth + d] = bf;
       split_k[t * depth + d] = bk;
       split_score[t * depth + d] = bs;
@@ -466,7 +496,8 @@ void or_predict(const uint8_t* bins, int64_t n, int F_pad, const int* split_f, c
 //    values on its first 2^i positions, added (times lr) at all positions it holds.
 // Gradients are rounded to FP32 storage as in or_fit. sup_out (optional) receives the
 // supporting values [s][n_sup], n_sup = sum_i min(2^(i+1), n), models in order of i,
-// each model's values by position.
+// each model's values by position. follow_f / follow_k / follow_tol / followed: the lock
+// step of or_fit (follow_split).
 static int floor_log2(int64_t k) {
   int r = 0;
   while ((int64_t(1) << (r + 1)) <= k) ++r;
@@ -484,7 +515,8 @@ int64_t or_ordered_sup_size(int64_t n) {
 void or_fit_ordered(const uint8_t* bins, int64_t n, int F_pad, int F, const int* n_borders, int max_bins,
                     const float* y, int loss, int depth, int trees, double lr, double l2, const uint32_t* perms,
                     int s, double* pred, int* split_f, int* split_k, double* split_score, double* split_second,
-                    double* leaf_values, double* losses, double* sup_out) {
+                    double* leaf_values, double* losses, double* sup_out, const int* follow_f,
+                    const int* follow_k, double follow_tol, int* followed) {
   const int L = 1 << depth;
   const int I = n > 1 ? floor_log2(n - 1) : 0;
   std::vector<int64_t> off(I + 2, 0);
@@ -514,6 +546,12 @@ void or_fit_ordered(const uint8_t* bins, int64_t n, int F_pad, int F, const int*
       double bs, ss;
       or_histogram(bins_r, n, F_pad, F, go.data(), ho.data(), leaf.data(), 1 << d, max_bins, hist.data());
       or_split_scores(hist.data(), 1 << d, F, n_borders, max_bins, l2, scores.data(), &bf, &bk, &bs, &ss);
+      if (follow_f && bf >= 0)
+        followed[t * depth + d] = follow_split(scores.data(), F, max_bins > 1 ? max_bins - 1 : 1, n_borders,
+                                               follow_f[t * depth + d], follow_k[t * depth + d], follow_tol, &bf,
+                                               &bk, bs);
+      else if (follow_f)
+        followed[t * depth + d] = follow_f[t * depth + d] == bf ? 0 : -1;
       split_f[t * depth + d] = bf;
       split_k[t * depth + d] = bk;
       split_score[t * depth + d] = bs;

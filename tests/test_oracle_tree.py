@@ -202,3 +202,71 @@ def test_split_score_ties_go_to_smallest_feature_then_border():
     res = oracle.fit(bins, 2, np.array([3, 3], np.int32), y, "rmse", 1, 1, 1.0, 3.0)
     assert res["split_f"][0, 0] == 0
     assert res["second"][0, 0] == res["score"][0, 0]
+
+
+def _fit_case(seed=4, n=3000, F=5, max_bins=17, depth=3, trees=4):
+    rng = np.random.default_rng(seed)
+    bins = rng.integers(0, max_bins, size=(n, 16)).astype(np.uint8)
+    bins[:, F:] = 0
+    nb = np.full(F, max_bins - 1, np.int32)
+    y = (rng.random(n) < 1 / (1 + np.exp(-(bins[:, 0] / 8.0 - 1 + (bins[:, 2] > 9))))).astype(np.float32)
+    return bins, nb, y, depth, trees
+
+
+def test_following_its_own_splits_changes_nothing():
+    bins, nb, y, D, T = _fit_case()
+    a = oracle.fit(bins, nb.size, nb, y, "logloss", D, T, 0.1, 3.0)
+    b = oracle.fit(bins, nb.size, nb, y, "logloss", D, T, 0.1, 3.0, follow=(a["split_f"], a["split_k"]))
+    assert np.all(b["followed"] == 0)
+    assert np.array_equal(a["pred"], b["pred"])
+    assert np.array_equal(a["leaf_values"], b["leaf_values"])
+
+
+def test_a_duplicate_column_is_an_exact_tie_that_the_lock_step_follows():
+    """Feature 5 is a copy of feature 0, so every split on one scores exactly like the
+    same split on the other: the oracle takes the smaller feature, and told to follow the
+    copy it does so (flag 1) and reaches the same predictions (the rows go the same way)."""
+    bins, nb, y, D, T = _fit_case()
+    bins[:, 5] = bins[:, 0]
+    nb = np.append(nb, nb[0]).astype(np.int32)
+    a = oracle.fit(bins, 6, nb, y, "logloss", D, T, 0.1, 3.0)
+    assert np.any(a["split_f"] == 0)
+    ff = np.where(a["split_f"] == 0, 5, a["split_f"])
+    b = oracle.fit(bins, 6, nb, y, "logloss", D, T, 0.1, 3.0, follow=(ff, a["split_k"]))
+    assert np.array_equal(b["split_f"], ff)
+    assert np.array_equal(b["followed"], (a["split_f"] == 0).astype(np.int32))
+    assert np.array_equal(a["score"], b["score"])
+    assert np.array_equal(a["pred"], b["pred"])
+
+
+def test_a_clearly_worse_split_is_flagged_and_not_followed():
+    bins, nb, y, D, T = _fit_case()
+    a = oracle.fit(bins, nb.size, nb, y, "logloss", D, T, 0.1, 3.0)
+    ff = a["split_f"].copy()
+    fk = a["split_k"].copy()
+    fk[1, 0] = 0 if fk[1, 0] != 0 else 1            # the root split of tree 1 moved to another border
+    b = oracle.fit(bins, nb.size, nb, y, "logloss", D, T, 0.1, 3.0, follow=(ff, fk))
+    assert b["followed"][1, 0] == -1
+    assert np.all(np.delete(b["followed"].ravel(), D) == 0)
+    assert np.array_equal(a["pred"], b["pred"])
+
+
+def test_a_followed_split_drives_the_leaves_and_values():
+    """With a margin that admits any split, the followed structure is taken at every
+    level, and the predictions equal the leaf values of that structure computed from
+    the definitions (leaf index, FP64 totals, Newton step) tree by tree."""
+    bins, nb, y, D, T = _fit_case(trees=3)
+    rng = np.random.default_rng(7)
+    ff = rng.integers(0, nb.size, size=(T, D)).astype(np.int32)
+    fk = rng.integers(0, nb[0], size=(T, D)).astype(np.int32)
+    b = oracle.fit(bins, nb.size, nb, y, "logloss", D, T, 0.1, 3.0, follow=(ff, fk), follow_tol=1e9)
+    assert np.array_equal(b["split_f"], ff) and np.array_equal(b["split_k"], fk)
+    assert np.all(b["followed"] >= 0)
+    pred = np.zeros(y.size)
+    for t in range(T):
+        g, h = oracle.gradients("logloss", y, pred)
+        leaf = oracle.tree_leaf_index(bins, ff[t], fk[t])
+        v = oracle.leaf_values(oracle.leaf_totals(g, h, leaf, 1 << D), 3.0)
+        assert np.allclose(b["leaf_values"][t], v, rtol=1e-13, atol=0)
+        pred = pred + 0.1 * v[leaf]
+    assert np.allclose(b["pred"], pred, rtol=1e-13, atol=1e-15)
