@@ -356,10 +356,15 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
  * Scratch: a file-scope device array of 16 MiB (the work plan and the FP32
  * partial histograms), held by every GPU that loads the library until the
  * process exits. One work unit needs F_pad/32 * max_bins * 256 bytes, so
- * F_pad * max_bins beyond about 2 million is rejected with CBG_EINVAL; larger n
- * only makes each unit longer. The first call on a device looks up the array's
- * device address (once per device, with that device current): make that first
- * call before any stream capture. Every call shares the array and overwrites
+ * F_pad * max_bins beyond about 2 million is rejected with CBG_EINVAL. Rows are
+ * split over as many units as the array holds; a CTA of a unit then sums up to
+ * 16384 rows into its FP32 histogram (the accuracy of the other paths: within
+ * 1e-5 of each bin's sum of |g|), and an n that would need more rows per CTA
+ * is rejected with CBG_EINVAL (for example F_pad 2048 at 128 bins holds about
+ * 9e5 rows, F_pad 96 at 255 bins about 1.1e7). n must be at most 2^31 - 2^20.
+ * The first call through a context looks up the array's device address (once
+ * per device and context, with that device current): make that first call
+ * before any stream capture. Every call shares the array and overwrites
  * what the previous call left there, so calls that can overlap on the GPU (on
  * different streams, or from different contexts on the same device) race: order
  * them on one stream or serialise them. */

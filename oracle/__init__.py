@@ -416,19 +416,37 @@ def predict(bins, split_f, split_k, leaf_values, lr: float):
     return pred
 
 
-def preprocess(workload, F_pad: int):
+def pmap(fn, items, workers: int = 1):
+    """[fn(i) for i in items], optionally on `workers` threads. Each oracle call is
+    single-threaded C code that releases the interpreter lock, so independent calls (one
+    column, one run) can proceed side by side; nothing in any call changes."""
+    items = list(items)
+    if workers <= 1 or len(items) <= 1:
+        return [fn(i) for i in items]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(fn, items))
+
+
+def preprocess(workload, F_pad: int, workers: int = 1):
     """The one-off steps of the path on the oracle: permutation, prior, ordered TS
     per categorical column, borders over floats then TS columns, quantisation.
-    Returns dict(perm, prior, ts [C][n], borders [F][B], n_borders [F], bins [n][F_pad])."""
+    Returns dict(perm, prior, ts [C][n], borders [F][B], n_borders [F], bins [n][F_pad]).
+    workers > 1 runs the per-column steps of different columns on that many threads."""
     w = workload
     perm = make_permutation(w.seed, w.n)
     P = prior(w.y, w.label_kind)
     ts = np.empty((w.n_cat, w.n), np.float32)
-    for c in range(w.n_cat):
-        ts[c] = ordered_ts(w.cat[c], w.y, perm, P, w.a)[0]
+    for c, col in enumerate(pmap(lambda c: ordered_ts(w.cat[c], w.y, perm, P, w.a)[0], range(w.n_cat), workers)):
+        ts[c] = col
     cols = np.concatenate([w.x, ts], axis=0) if w.n_cat else w.x
-    borders, nb = select_borders(cols, w.max_borders)
-    bins = quantize(cols, borders, nb, F_pad)
+    F = cols.shape[0]
+    per = pmap(lambda f: select_borders(cols[f:f + 1], w.max_borders), range(F), workers)
+    borders = np.concatenate([b for b, _ in per], axis=0) if F else np.empty((0, w.max_borders), np.float32)
+    nb = np.concatenate([c for _, c in per]).astype(np.int32) if F else np.empty(0, np.int32)
+    bins = np.zeros((w.n, F_pad), np.uint8)
+    pmap(lambda f: quantize(cols[f:f + 1], borders[f:f + 1], nb[f:f + 1], F_pad, f_offset=f, bins=bins),
+         range(F), workers)
     return {"perm": perm, "prior": P, "ts": ts, "borders": borders, "n_borders": nb, "bins": bins}
 
 

@@ -30,6 +30,7 @@ struct cbg_ctx {
   cudaStream_t capture_stream = nullptr;   // non-blocking stream used to capture graphs
   std::vector<cudaStream_t> branch_streams;  // branches of a captured batched round
   std::vector<cudaEvent_t> branch_events;
+  void* noalloc_scratch = nullptr;   // device address of cbg_histogram_noalloc's array (looked up once)
 };
 
 namespace cbg {

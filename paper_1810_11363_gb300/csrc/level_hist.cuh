@@ -102,8 +102,10 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
 // repeat across rows (after a few trees g takes one value per leaf and label) would all
 // round the same way under round-to-nearest, and their errors would add up linearly; a
 // dither drawn per row makes the errors independent with mean zero. x - floor(x) is exact
-// in FP32; only its sum with u rounds, which moves the result only when that sum lies
-// within an ulp of 1. The error is below one unit.
+// in FP32 for x >= 0 and for negative x with |x| not below 2^-24 |floor(x)|; a tinier
+// negative x gives 1 + x = 1 after rounding and so always rounds to 0 (no dither there).
+// The sum with u rounds too, which moves the result only when that sum lies within an
+// ulp of 1. In every case the error is below one unit.
 __device__ __forceinline__ int dither_round(float x, float u) {
   const float xi = floorf(x);
   return __float2int_rz(xi) + ((x - xi) + u >= 1.f ? 1 : 0);

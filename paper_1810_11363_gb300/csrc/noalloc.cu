@@ -10,36 +10,30 @@
 #include "cbg_internal.cuh"
 #include "level_hist.cuh"
 
-#include <mutex>
-
 using namespace cbg;
 
 namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = static_cast<size_t>(16) << 20;   // 16 MiB per device
-constexpr int NOALLOC_MAX_DEVICES = 64;
-constexpr int NOALLOC_ROWS_PER_CTA = 4096;
+constexpr int NOALLOC_ROWS_PER_CTA = 4096;        // rows per CTA while the scratch has room for the units
+constexpr int NOALLOC_MAX_ROWS_PER_CTA = 16384;   // beyond this one FP32 cell would sum too many rows
+constexpr int64_t NOALLOC_MAX_N = (int64_t(1) << 31) - (int64_t(1) << 20);   // slack for the last chunk's end
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_scratch_mu;
-void* g_scratch_addr[NOALLOC_MAX_DEVICES] = {};
-
-// Device address of the scratch array on ctx's device (current while this runs).
-// Looked up once per device; in host code the array's name is only a stand-in.
+// Device address of the scratch array on ctx's device (current while this runs). In host
+// code the array's name is only a stand-in. The address is looked up by the first call
+// through a context and kept in it; a new context (for example after cudaDeviceReset,
+// which may reload the module at another address) looks it up again.
 cbg_status scratch_address(cbg_ctx* ctx, void** out) {
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (ctx->device < 0 || ctx->device >= NOALLOC_MAX_DEVICES)
-    return fail(ctx, CBG_EUNSUPPORTED, "device %d is beyond the %d devices the scratch table covers", ctx->device,
-                NOALLOC_MAX_DEVICES);
-  if (!g_scratch_addr[ctx->device]) {
+  if (!ctx->noalloc_scratch) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr)
       return fail(ctx, CBG_ECUDA, "cudaGetSymbolAddress of the histogram scratch failed: %s", cudaGetErrorString(e));
-    g_scratch_addr[ctx->device] = p;
+    ctx->noalloc_scratch = p;
   }
-  *out = g_scratch_addr[ctx->device];
+  *out = ctx->noalloc_scratch;
   return CBG_OK;
 }
 
@@ -66,7 +60,7 @@ extern "C" cbg_status cbg_histogram_noalloc(cbg_ctx* ctx, const uint8_t* bins, i
                                             int32_t max_bins, const void* g, const void* h, int32_t gh_dtype,
                                             double* hist_out) {
   if (!ctx) return CBG_EINVAL;
-  CBG_REQUIRE(ctx, n >= 1 && n <= INT32_MAX, "n must be in [1, 2^31-1]");
+  CBG_REQUIRE(ctx, n >= 1 && n <= NOALLOC_MAX_N, "n must be in [1, 2^31 - 2^20]");
   CBG_REQUIRE(ctx, F >= 1 && F_pad >= F && F_pad % GROUP == 0, "F_pad must be a multiple of 32 and >= F >= 1");
   CBG_REQUIRE(ctx, max_bins >= 2 && max_bins <= 256, "max_bins must be in [2, 256]");
   CBG_REQUIRE(ctx, gh_dtype == CBG_F32 || gh_dtype == CBG_BF16, "bad gh_dtype");
@@ -99,6 +93,12 @@ extern "C" cbg_status cbg_histogram_noalloc(cbg_ctx* ctx, const uint8_t* bins, i
   int64_t units = ceil_div(n, static_cast<int64_t>(cs) * NOALLOC_ROWS_PER_CTA);
   if (units > max_units) units = max_units;
   if (units < 1) units = 1;
+  if (ceil_div(n, units * cs) > NOALLOC_MAX_ROWS_PER_CTA)
+    return fail(ctx, CBG_EINVAL,
+                "n = %lld rows at F_pad %d x %d bins: the scratch holds %lld work units of %d CTAs, which would "
+                "put more than %d rows into one CTA's FP32 histogram; at most %lld rows fit",
+                static_cast<long long>(n), F_pad, max_bins, static_cast<long long>(max_units), cs,
+                NOALLOC_MAX_ROWS_PER_CTA, static_cast<long long>(max_units * cs * NOALLOC_MAX_ROWS_PER_CTA));
   const int chunk_rows = static_cast<int>(ceil_div(n, units * cs));
   Plan* plan = static_cast<Plan*>(scratch);
   float* partials = reinterpret_cast<float*>(static_cast<char*>(scratch) + plan_bytes);

@@ -34,3 +34,20 @@ def golden_directives(name, tag):
             if line.startswith("#" + tag + " "):
                 rows.append(line[len(tag) + 1:].split())
     return rows
+
+
+# Numbers the parity tests measure (error against the FP64 oracle per result, near-ties
+# followed in lock step), printed at the end of the run.
+PARITY_REPORT = {}
+
+
+def report(key, value):
+    PARITY_REPORT[key] = value
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    if not PARITY_REPORT:
+        return
+    terminalreporter.section("parity report (error against the FP64 oracle)")
+    for k in sorted(PARITY_REPORT):
+        terminalreporter.write_line(f"{k}: {PARITY_REPORT[k]}")

@@ -4,8 +4,10 @@ builder (cbg_build_level at depth 0, which needs a caller-allocated tree state).
 cbg_histogram_noalloc serves callers that cannot allocate device memory (an application
 that owns the whole device memory budget, or plugin code that may not call cudaMalloc):
 its scratch is a fixed device array inside the library. Two calls in a row must both
-agree with the regular path within the histogram tolerance of the other tests: 1e-5 of
-the per-bin sum of |g| (|h|). This file is collected last on purpose."""
+agree with the regular path, and with the FP64 oracle directly, within the histogram
+tolerance of the other tests: 1e-5 of the per-bin sum of |g| (|h|). Two shapes fill the
+scratch, so that each CTA sums more rows than the regular tiling gives it. This file is
+collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -46,7 +48,11 @@ def _regular_root_hist(ctx, bins_rm, nb, g, h, dtype):
 
 
 @pytest.mark.parametrize("n,F,F_pad,max_bins,dtype", [(200003, 70, 96, 255, "f32"), (4097, 33, 64, 129, "bf16"),
-                                                       (1, 3, 32, 5, "f32")])
+                                                       (1, 3, 32, 5, "f32"),
+                                                       # the scratch's unit count binds: ~7k rows per CTA
+                                                       (400000, 2000, 2048, 129, "f32"),
+                                                       # ~4.4k rows per CTA, 255 bins
+                                                       (3000007, 90, 96, 255, "bf16")])
 def test_noalloc_root_histogram_matches_build_level_twice(ctx, n, F, F_pad, max_bins, dtype):
     import torch
     bins_rm, nb, g, h, _ = synth.random_level_case(n + F, n, F, F_pad, max_bins, 1)
@@ -56,6 +62,7 @@ def test_noalloc_root_histogram_matches_build_level_twice(ctx, n, F, F_pad, max_
     bins, ref = _regular_root_hist(ctx, bins_rm, nb, gd, hd, dtype)
     g64, h64 = gd.double().cpu().numpy(), hd.double().cpu().numpy()
     bound = oracle.histogram(bins_rm, F, np.abs(g64), np.abs(h64), None, 1, ref.shape[1])[0]
+    exact = oracle.histogram(bins_rm, F, g64, h64, None, 1, ref.shape[1])[0]
     mb = int(nb.max()) + 1
     for _ in range(2):
         out = torch.full((F, mb, 2), float("nan"), dtype=torch.float64, device="cuda")
@@ -64,6 +71,7 @@ def test_noalloc_root_histogram_matches_build_level_twice(ctx, n, F, F_pad, max_
         got = to_host(out)
         assert not np.isnan(got).any()
         assert hist_tolerance_ok(got, ref, bound), np.abs(got - ref).max()
+        assert hist_tolerance_ok(got, exact, bound), np.max(np.abs(got - exact) / np.maximum(bound, 1e-300))
 
 
 def test_noalloc_rejects_what_does_not_fit_its_scratch(ctx):
@@ -76,3 +84,17 @@ def test_noalloc_rejects_what_does_not_fit_its_scratch(ctx):
     with pytest.raises(cbg.CbgError) as e:
         cbg.cbg_histogram_noalloc(ctx, bins, n, F_pad, F_pad, 255, g, g, "f32", out)
     assert e.value.status == cbg.CBG_EINVAL
+
+
+def test_noalloc_rejects_more_rows_per_cta_than_its_bound(ctx):
+    """F_pad 2048 at 128 bins leaves room for 7 work units: 10^6 rows would put more
+    than 16384 rows into one CTA's FP32 histogram, which the call refuses."""
+    import torch
+    n, F_pad = 1_000_000, 2048
+    bins = torch.zeros(F_pad * n, dtype=torch.uint8, device="cuda")
+    g = torch.zeros(n, dtype=torch.float32, device="cuda")
+    out = torch.empty((F_pad, 129, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(cbg.CbgError) as e:
+        cbg.cbg_histogram_noalloc(ctx, bins, n, F_pad, F_pad, 129, g, g, "f32", out)
+    assert e.value.status == cbg.CBG_EINVAL
+    assert "rows" in str(e.value)
