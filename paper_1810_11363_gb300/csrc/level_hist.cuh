@@ -17,14 +17,22 @@
 namespace {
 
 constexpr int GROUP = 32;          // features per group / histogram slab
+// Shared memory a CTA may take: the 227 KB opt-in limit less 1 KB kept for the kernels'
+// static shared variables (the work-queue slot, cluster bookkeeping).
+constexpr int SMEM_DYN_BUDGET = 227 * 1024 - 1024;
 constexpr int MAX_DEPTH = 10;
 constexpr int MAX_HLEAVES = 1 << (MAX_DEPTH - 1);  // leaves histogrammed at the last level
 
+// Work of one level's histogram launch. The directly computed leaves are listed by
+// decreasing rows per CTA (largest work items first), each split into chunk units; work
+// item u * G + g is unit u of feature group g. Every cluster of a launch takes its next
+// item from `queue` (reset to 0 by whoever writes the plan and by the reduction that
+// follows the launch), so the items spread over the clusters as they finish.
 struct Plan {
   int n_small;                      // leaves histogrammed directly at this level
   int total_units;                  // sum of chunks over those leaves
   int level_leaves;                 // 2^d
-  int pad;
+  int queue;                        // next work item of the running histogram launch
   int small_leaf[MAX_HLEAVES];
   int large_leaf[MAX_HLEAVES];      // sibling obtained by subtraction (-1: none)
   int parent[MAX_HLEAVES];          // index of the parent in the previous histogram
@@ -39,7 +47,7 @@ size_t hist_smem_bytes(int nb_alloc) { return static_cast<size_t>(2) * nb_alloc 
 // What the histogram launch needs to know about a problem. kind 0: warp-private
 // histograms of 16 features per warp; kind 1: one shared histogram per CTA updated with
 // shared-memory float reductions; kind 3: the same with 64-bit compare-and-swap; kind 4:
-// lane-per-feature warp histograms with store forwarding; kind 5: the same with G and H
+// lane-per-feature warp histograms with batched updates; kind 5: the same with G and H
 // in separate warps; kind 6: kind 4 over 4-bit packed bins; kind 7: kind 1 with int32
 // fixed-point cells and integer reductions. Kinds 4-7 read (g, h) by position, the
 // others by row.
@@ -54,7 +62,7 @@ struct HistConfig {
 // max_bins; warps come in pairs (the two halves of a 32-feature group).
 constexpr int WP_FEATS = 16;
 inline int wp_warps(int max_bins, int requested_threads) {
-  const int fit = static_cast<int>((227 * 1024) / (static_cast<size_t>(max_bins) * WP_FEATS * sizeof(float2)));
+  const int fit = static_cast<int>(SMEM_DYN_BUDGET / (static_cast<size_t>(max_bins) * WP_FEATS * sizeof(float2)));
   int w = fit < 16 ? fit : 16;
   if (requested_threads > 0 && requested_threads / 32 < w) w = requested_threads / 32;
   w &= ~1;
@@ -168,9 +176,23 @@ struct HistProblem {
 // One work item (unit x group) of one problem, for this CTA of the cluster: accumulate
 // the item's rows into the CTA's shared histogram, then sum this CTA's slice of bins over
 // the cluster (distributed shared memory) into the item's FP32 partial.
+// Work-item queue of a single-problem launch: thread 0 of cluster rank 0 takes the next
+// item and writes it into the same shared slot of every CTA of the cluster (distributed
+// shared memory); each CTA then reads only its own slot. The writes happen between the
+// two cluster barriers of an item (every CTA has read the current item before the first
+// and reads the next one after the second), and no CTA touches another CTA's shared
+// memory after the last barrier, so a CTA may exit as soon as it finds the queue empty.
+// Before the first take the cluster synchronises once, so that every CTA has started.
+__device__ __forceinline__ void queue_take(const Plan* plan, int* slot, int cs) {
+  const int v = atomicAdd(&const_cast<Plan*>(plan)->queue, 1);
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  for (int r = 0; r < cs; ++r) *cl.map_shared_rank(slot, r) = v;
+}
+__device__ __forceinline__ int queue_read(const int* slot) { return *reinterpret_cast<const volatile int*>(slot); }
+
 template <typename GH, int NB, int MODE>
 __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs, int rank, float* hsh,
-                                          const float* const* peer, uint32_t sbase) {
+                                          const float* const* peer, uint32_t sbase, int* next_slot = nullptr) {
   namespace cgr = cooperative_groups;
   constexpr int PLANE = NB * GROUP;
   __shared__ int s_exp[2];   // MODE 2: this CTA's fixed-point exponents of G and H
@@ -316,6 +338,7 @@ __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs
     }
   }
   cgr::this_cluster().sync();
+  if (next_slot != nullptr && rank == 0 && threadIdx.x == 0) queue_take(P.plan, next_slot, cs);
   // this CTA's slice of bins, summed over the cluster's CTAs in rank order
   const int max_bins = P.max_bins;
   const int bs = (max_bins + cs - 1) / cs;
@@ -377,11 +400,15 @@ __global__ void __launch_bounds__(512, 3) level_hist_kernel(const uint8_t* __res
                                                          const Plan* __restrict__ plan, int max_bins,
                                                          float* __restrict__ partials) {
   extern __shared__ __align__(16) float hsh[];   // [2][NB][32]
+  __shared__ int s_next;
   HistCta k(hsh);
   const HistProblem P{bins, n, G, F, order, g, h, plan, max_bins, partials};
   const int total_items = plan->total_units * G;
-  for (int item = k.cid; item < total_items; item += k.ncl)
-    hist_item<GH, NB, MODE>(P, item, k.cs, k.rank, hsh, k.peer, k.sbase);
+  cooperative_groups::this_cluster().sync();
+  if (k.rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, k.cs);
+  cooperative_groups::this_cluster().sync();
+  for (int item = queue_read(&s_next); item < total_items; item = queue_read(&s_next))
+    hist_item<GH, NB, MODE>(P, item, k.cs, k.rank, hsh, k.peer, k.sbase, &s_next);
 }
 
 // The batched form: one launch for a level of many problems. The work items of all
@@ -469,7 +496,11 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
   for (int c = 0; c < cs && c < MAX_CS; ++c) peer[c] = cl.map_shared_rank(wsh, c);
   const int total_items = plan->total_units * G;
   const int n_small = plan->n_small;
-  for (int item = cid; item < total_items; item += ncl) {
+  __shared__ int s_next;   // this cluster's next work item (rank 0's slot)
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
+  cl.sync();
+  for (int item = queue_read(&s_next); item < total_items; item = queue_read(&s_next)) {
     const int unit = item / G, grp = item - unit * G;
     int lo = 0, hi = n_small - 1;
     while (lo < hi) {
@@ -548,6 +579,7 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
       }
     }
     cl.sync();
+    if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
     const int bs = (max_bins + cs - 1) / cs;
     const int b0 = rank * bs;
     const int nbs = max(0, min(max_bins, b0 + bs) - b0);
@@ -576,12 +608,12 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
 // column f for every row, so the 32 addresses of an update are always distinct and no
 // atomics are needed. Rows come in blocks of 32 staged in shared memory: lane i fetches
 // the row id and the position-ordered (g, h) of row i four blocks ahead and copies the
-// row's 32-byte bin record with cp.async two blocks ahead. Within a block the histogram
-// load of row i + 2 is issued before the stores of rows i and i + 1; if its bin equals
-// one of theirs, the value just stored replaces the stale load (store-to-load forwarding
-// in registers), so the 30-cycle shared-memory round trip is off the critical path.
-// A 255-bin warp histogram is 64 KB, so an SM holds 3 such warps; the unrolled block
-// and the forwarding give each warp the instruction-level parallelism it needs.
+// row's 32-byte bin record with cp.async two blocks ahead. Within a block the rows are
+// updated in batches of LH_BATCH: the histogram loads of a batch are issued before its
+// stores, and a row whose cell repeats an earlier row of the batch takes that row's new
+// value (forwarding in registers), so one shared-memory round trip serves a whole batch
+// (lane_batched_updates). A 255-bin warp histogram is 64 KB, so an SM holds 3 such
+// warps; the batches give each warp the instruction-level parallelism it needs.
 // At the end of a work unit the warps of a CTA are summed into warp 0's histogram, and
 // CTA r of the cluster sums its slice of bins over the cluster (distributed shared
 // memory) into the unit's FP32 partial.
@@ -589,7 +621,7 @@ constexpr int LH_ROWS = 32;       // rows per block: one per lane for row ids an
 constexpr int LH_STAGES = 3;      // bin-record buffers per warp: blocks j, j + 1, j + 2
 constexpr int LH_AHEAD = 4;       // blocks of lookahead for row ids and (g, h)
 constexpr int LH_MAX_WARPS = 16;
-constexpr int LH_FWD = 3;         // rows between a histogram load and its use
+constexpr int LH_BATCH = 4;       // rows whose histogram loads are issued before their stores
 
 // Histogram accesses of the lane kernel. Volatile keeps them in program order among
 // themselves (a load issued ahead of a store to the same cell must stay ahead of it, the
@@ -604,12 +636,53 @@ __device__ __forceinline__ void sts_f2(uint32_t addr, float2 v) {
   asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y));
 }
 
+// Histogram updates of N consecutive staged rows of one lane, for C update chains whose
+// cells are disjoint (chain c: cell addresses a[c][i]; rows row0 + i take their (g, h)
+// from the staged pairs gh4, two rows per float4; row0 is even). A warp's shared load
+// waits for that warp's own earlier shared stores, so an update loop that loads a row's
+// cell after the previous row's store pays one full shared-memory round trip per row.
+// Here the loads of LH_BATCH rows (of every chain) are issued before any of their stores;
+// a row whose cell repeats an earlier row of the same batch and chain takes that row's new
+// value instead of its own, stale, load. Every cell still adds its rows in row order.
+template <int N, int C>
+__device__ __forceinline__ void lane_batched_updates(const uint32_t (&a)[C][N], const float4* __restrict__ gh4, int row0,
+                                                     const bool (&act)[C]) {
+  static_assert(N % LH_BATCH == 0, "rows must fill whole batches");
+#pragma unroll
+  for (int i0 = 0; i0 < N; i0 += LH_BATCH) {
+    float2 v[C][LH_BATCH];
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int j = 0; j < LH_BATCH; ++j) v[c][j] = act[c] ? lds_f2(a[c][i0 + j]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < LH_BATCH; ++j) {
+      const float4 gq = gh4[(row0 + i0 + j) >> 1];
+      const float gx = ((i0 + j) & 1) ? gq.z : gq.x;
+      const float hy = ((i0 + j) & 1) ? gq.w : gq.y;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int q = 0; q < j; ++q)
+          if (a[c][i0 + q] == a[c][i0 + j]) v[c][j] = v[c][q];
+        v[c][j].x += gx;
+        v[c][j].y += hy;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int j = 0; j < LH_BATCH; ++j)
+        if (act[c]) sts_f2(a[c][i0 + j], v[c][j]);
+  }
+}
+
 inline size_t lh_warp_bytes(int max_bins) {
   return static_cast<size_t>(max_bins) * GROUP * sizeof(float2) + static_cast<size_t>(LH_STAGES) * LH_ROWS * GROUP +
          LH_ROWS * sizeof(float2);
 }
 inline int lh_warps(int max_bins, int requested_threads) {
-  int w = static_cast<int>((227 * 1024) / lh_warp_bytes(max_bins));
+  int w = static_cast<int>(SMEM_DYN_BUDGET / lh_warp_bytes(max_bins));
   if (w > LH_MAX_WARPS) w = LH_MAX_WARPS;
   if (requested_threads > 0 && requested_threads / 32 < w) w = requested_threads / 32;
   return w < 1 ? 1 : w;
@@ -653,7 +726,11 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
   for (int r = 0; r < cs && r < MAX_CS; ++r) peer0[r] = cl.map_shared_rank(hist_all, r);
   const int total_items = plan->total_units * G;
   const int n_small = plan->n_small;
-  for (int item = cid; item < total_items; item += ncl) {
+  __shared__ int s_next;   // this cluster's next work item (rank 0's slot)
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
+  cl.sync();
+  for (int item = queue_read(&s_next); item < total_items; item = queue_read(&s_next)) {
     const int unit = item / G, grp = item - unit * G;
     int lo = 0, hi = n_small - 1;
     while (lo < hi) {
@@ -720,31 +797,12 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
           const float4* gh4 = reinterpret_cast<const float4*>(my_gh);
           // shared-memory offsets (bytes) of the 32 rows' cells, loaded up front so that
           // only the histogram loads remain on the chain
-          uint32_t a[LH_ROWS];
+          uint32_t a[1][LH_ROWS];
 #pragma unroll
           for (int i = 0; i < LH_ROWS; ++i)
-            a[i] = hbase + static_cast<uint32_t>(min(static_cast<int>(sb[i * GROUP]), maxb1)) * (GROUP * 8u);
-          float2 v[LH_FWD];
-#pragma unroll
-          for (int i = 0; i < LH_FWD; ++i) v[i] = lds_f2(a[i]);
-          float2 nw[LH_FWD];   // values stored for the previous LH_FWD rows (most recent last)
-#pragma unroll
-          for (int i = 0; i < LH_ROWS; ++i) {
-            float2 nxt = make_float2(0.f, 0.f);
-            if (i + LH_FWD < LH_ROWS) nxt = lds_f2(a[i + LH_FWD]);   // before the stores of rows i .. i+LH_FWD-1
-            float2 cur = v[i % LH_FWD];
-            // the loaded value misses the stores of the previous LH_FWD rows: take the most
-            // recent one to the same cell instead
-#pragma unroll
-            for (int q = LH_FWD; q >= 1; --q)
-              if (i - q >= 0 && a[i] == a[i - q]) cur = nw[(i - q) % LH_FWD];
-            const float4 gq = gh4[i >> 1];
-            cur.x += (i & 1) ? gq.z : gq.x;
-            cur.y += (i & 1) ? gq.w : gq.y;
-            sts_f2(a[i], cur);
-            nw[i % LH_FWD] = cur;
-            v[i % LH_FWD] = nxt;
-          }
+            a[0][i] = hbase + static_cast<uint32_t>(min(static_cast<int>(sb[i * GROUP]), maxb1)) * (GROUP * 8u);
+          const bool on[1] = {true};
+          lane_batched_updates<LH_ROWS, 1>(a, gh4, 0, on);
         }
         __syncwarp();
 #pragma unroll
@@ -770,6 +828,7 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
       }
     }
     cl.sync();
+    if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
     // this CTA's slice of bins, summed over the cluster's CTAs in rank order
     const int bs = (max_bins + cs - 1) / cs;
     const int b0 = rank * bs;
@@ -806,7 +865,7 @@ inline size_t l4_warp_bytes(int max_bins) {
          LH_ROWS * sizeof(float2);
 }
 inline int l4_warps(int max_bins, int requested_threads) {
-  int w = static_cast<int>((227 * 1024) / l4_warp_bytes(max_bins));
+  int w = static_cast<int>(SMEM_DYN_BUDGET / l4_warp_bytes(max_bins));
   if (w > LH_MAX_WARPS) w = LH_MAX_WARPS;
   if (requested_threads > 0 && requested_threads / 32 < w) w = requested_threads / 32;
   return w < 1 ? 1 : w;
@@ -845,7 +904,11 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
   for (int r = 0; r < cs && r < MAX_CS; ++r) peer0[r] = cl.map_shared_rank(hist_all, r);
   const int total_items = plan->total_units * G4;
   const int n_small = plan->n_small;
-  for (int item = cid; item < total_items; item += ncl) {
+  __shared__ int s_next;   // this cluster's next work item (rank 0's slot)
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
+  cl.sync();
+  for (int item = queue_read(&s_next); item < total_items; item = queue_read(&s_next)) {
     const int unit = item / G4, q4 = item - unit * G4;
     int lo = 0, hi = n_small - 1;
     while (lo < hi) {
@@ -912,38 +975,16 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
         const float4* gh4 = reinterpret_cast<const float4*>(my_gh);
 #pragma unroll
         for (int s0 = 0; s0 < LH_ROWS; s0 += L4_SUB) {
-          uint32_t alo[L4_SUB], ahi[L4_SUB];
+          uint32_t a[2][L4_SUB];
 #pragma unroll
           for (int i = 0; i < L4_SUB; ++i) {
             const unsigned byte = sb[(s0 + i) * GROUP];
-            alo[i] = hbase_lo + static_cast<uint32_t>(min(static_cast<int>(byte & 15u), maxb1)) * bin_stride;
-            ahi[i] = hbase_hi + static_cast<uint32_t>(min(static_cast<int>(byte >> 4), maxb1)) * bin_stride;
+            a[0][i] = hbase_lo + static_cast<uint32_t>(min(static_cast<int>(byte & 15u), maxb1)) * bin_stride;
+            a[1][i] = hbase_hi + static_cast<uint32_t>(min(static_cast<int>(byte >> 4), maxb1)) * bin_stride;
           }
-          // one update chain per nibble, each with the lane kernel's store forwarding
-          auto chain = [&](const uint32_t* a) {
-            float2 v[LH_FWD];
-#pragma unroll
-            for (int i = 0; i < LH_FWD; ++i) v[i] = lds_f2(a[i]);
-            float2 nw[LH_FWD];
-#pragma unroll
-            for (int i = 0; i < L4_SUB; ++i) {
-              float2 nxt = make_float2(0.f, 0.f);
-              if (i + LH_FWD < L4_SUB) nxt = lds_f2(a[i + LH_FWD]);
-              float2 cur = v[i % LH_FWD];
-#pragma unroll
-              for (int q = LH_FWD; q >= 1; --q)
-                if (i - q >= 0 && a[i] == a[i - q]) cur = nw[(i - q) % LH_FWD];
-              const int row = s0 + i;
-              const float4 gq = gh4[row >> 1];
-              cur.x += (row & 1) ? gq.z : gq.x;
-              cur.y += (row & 1) ? gq.w : gq.y;
-              sts_f2(a[i], cur);
-              nw[i % LH_FWD] = cur;
-              v[i % LH_FWD] = nxt;
-            }
-          };
-          if (act_lo) chain(alo);
-          if (act_hi) chain(ahi);
+          // the two nibbles' chains (disjoint halves of the warp histogram) in one batch
+          const bool on[2] = {act_lo, act_hi};
+          lane_batched_updates<L4_SUB, 2>(a, gh4, s0, on);
         }
         __syncwarp();
 #pragma unroll
@@ -969,6 +1010,7 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
       }
     }
     cl.sync();
+    if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
     // this CTA's slice of bins, summed over the cluster's CTAs in rank order, written as
     // the partials of uint8 groups 2 q4 and 2 q4 + 1
     const int bs = (max_bins + cs - 1) / cs;
@@ -1021,7 +1063,7 @@ __global__ void pack_bins4_kernel(const uint8_t* __restrict__ bins, int64_t n, i
 // (32 KB at 255 bins instead of 64 KB), so twice as many warps fit on an SM to hide the
 // shared-memory latency that bounds the one-warp-per-scheduler lane kernel. Both warps of a
 // pair stage the same 32-row blocks (the second copy comes from L2); each loads only its
-// own statistic. Store forwarding and the per-unit reduction are as in the lane kernel:
+// own statistic. The batched updates and the per-unit reduction are as in the lane kernel:
 // the G warps are summed in order into warp 0, the H warps into warp 1.
 __device__ __forceinline__ float lds_f(uint32_t addr) {
   float v;
@@ -1037,7 +1079,7 @@ inline size_t lp_warp_bytes(int max_bins) {
          LH_ROWS * sizeof(float);
 }
 inline int lp_warps(int max_bins, int requested_threads) {
-  int w = static_cast<int>((227 * 1024) / lp_warp_bytes(max_bins));
+  int w = static_cast<int>(SMEM_DYN_BUDGET / lp_warp_bytes(max_bins));
   if (w > LH_MAX_WARPS) w = LH_MAX_WARPS;
   if (requested_threads > 0 && requested_threads / 32 < w) w = requested_threads / 32;
   w &= ~1;
@@ -1075,7 +1117,11 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
   for (int r = 0; r < cs && r < MAX_CS; ++r) peer0[r] = cl.map_shared_rank(hist_all, r);
   const int total_items = plan->total_units * G;
   const int n_small = plan->n_small;
-  for (int item = cid; item < total_items; item += ncl) {
+  __shared__ int s_next;   // this cluster's next work item (rank 0's slot)
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
+  cl.sync();
+  for (int item = queue_read(&s_next); item < total_items; item = queue_read(&s_next)) {
     const int unit = item / G, grp = item - unit * G;
     int lo = 0, hi = n_small - 1;
     while (lo < hi) {
@@ -1142,23 +1188,23 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
 #pragma unroll
           for (int i = 0; i < LH_ROWS; ++i)
             a[i] = hbase + static_cast<uint32_t>(min(static_cast<int>(sb[i * GROUP]), maxb1)) * (GROUP * 4u);
-          float v[LH_FWD];
+          // batches of LH_BATCH rows: loads before stores, repeats take the batch's new value
 #pragma unroll
-          for (int i = 0; i < LH_FWD; ++i) v[i] = lds_f(a[i]);
-          float nw[LH_FWD];
+          for (int i0 = 0; i0 < LH_ROWS; i0 += LH_BATCH) {
+            float v[LH_BATCH];
 #pragma unroll
-          for (int i = 0; i < LH_ROWS; ++i) {
-            float nxt = 0.f;
-            if (i + LH_FWD < LH_ROWS) nxt = lds_f(a[i + LH_FWD]);   // before the stores of rows i .. i+LH_FWD-1
-            float cur = v[i % LH_FWD];
+            for (int q = 0; q < LH_BATCH; ++q) v[q] = lds_f(a[i0 + q]);
 #pragma unroll
-            for (int q = LH_FWD; q >= 1; --q)
-              if (i - q >= 0 && a[i] == a[i - q]) cur = nw[(i - q) % LH_FWD];
-            const float4 sq = s4[i >> 2];
-            cur += (i & 3) == 0 ? sq.x : (i & 3) == 1 ? sq.y : (i & 3) == 2 ? sq.z : sq.w;
-            sts_f(a[i], cur);
-            nw[i % LH_FWD] = cur;
-            v[i % LH_FWD] = nxt;
+            for (int q = 0; q < LH_BATCH; ++q) {
+              const int i = i0 + q;
+#pragma unroll
+              for (int e = 0; e < q; ++e)
+                if (a[i0 + e] == a[i]) v[q] = v[e];
+              const float4 sq = s4[i >> 2];
+              v[q] += (i & 3) == 0 ? sq.x : (i & 3) == 1 ? sq.y : (i & 3) == 2 ? sq.z : sq.w;
+            }
+#pragma unroll
+            for (int q = 0; q < LH_BATCH; ++q) sts_f(a[i0 + q], v[q]);
           }
         }
         __syncwarp();
@@ -1181,6 +1227,7 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
       }
     }
     cl.sync();
+    if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
     // this CTA's slice of bins, summed over the cluster's CTAs in rank order
     const int bs = (max_bins + cs - 1) / cs;
     const int b0 = rank * bs;
@@ -1293,6 +1340,8 @@ __global__ void __launch_bounds__(RD_THREADS)
     reduce_kernel(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
                   const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
                   const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df) {
+  // the histogram launch that filled the partials has ended: rearm its work queue
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) const_cast<Plan*>(plan)->queue = 0;
   reduce_body(plan, partials, G, F, max_bins, hist_prev, hist_cur, splits, depth, hist_df, blockIdx.x, blockIdx.y);
 }
 
@@ -1397,7 +1446,7 @@ cbg_status wp_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   auto kern = level_hist_wp_kernel<GH>;
   const size_t smem = wp_smem_bytes(L.max_bins, warps);
   // one attribute for every histogram size this kernel is launched with
-  CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN_BUDGET));
   HistGeom geom;
   // the cluster size (<= the requested one) that keeps the most CTAs co-resident
   for (int cs = L.cluster; cs >= 1; cs >>= 1) {
@@ -1455,7 +1504,7 @@ cbg_status lane_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   const size_t smem = V == 1   ? lp_smem_bytes(L.max_bins, warps)
                       : V == 2 ? l4_smem_bytes(L.max_bins, warps)
                                : lh_smem_bytes(L.max_bins, warps);
-  CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN_BUDGET));
   HistGeom geom;
   for (int cs = L.cluster; cs >= 1; cs >>= 1) {
     if (cs > 8) CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -1488,8 +1537,9 @@ cbg_status lane_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   return CBG_OK;
 }
 
-// The cluster size the plan must chunk for (identical for FP32 and BF16 gradients).
-cbg_status hist_cluster_size(cbg_ctx* ctx, const HistConfig& L, int* cs) {
+// The cluster size the plan must chunk for, and the clusters of a launch (identical for
+// FP32 and BF16 gradients).
+cbg_status hist_cluster_geom(cbg_ctx* ctx, const HistConfig& L, int* cs, int* clusters) {
   HistGeom g;
   cbg_status st = L.kind == 0   ? wp_geom<float>(ctx, L, &g)
                   : L.kind == 4 ? lane_geom<float, 0>(ctx, L, &g)
@@ -1498,7 +1548,16 @@ cbg_status hist_cluster_size(cbg_ctx* ctx, const HistConfig& L, int* cs) {
                                 : hist_geom<float>(ctx, L, &g);
   if (st != CBG_OK) return st;
   *cs = g.cs;
+  if (clusters) *clusters = g.clusters;
   return CBG_OK;
+}
+cbg_status hist_cluster_size(cbg_ctx* ctx, const HistConfig& L, int* cs) { return hist_cluster_geom(ctx, L, cs, nullptr); }
+
+// Work items a level's histogram launch is cut into, per cluster of the launch: enough
+// that the clusters, taking items from the queue as they finish, end close together.
+constexpr int HIST_ITEMS_PER_CLUSTER = 4;
+inline int hist_target_units(int clusters, int G) {
+  return (HIST_ITEMS_PER_CLUSTER * clusters + G - 1) / G;
 }
 
 // Every occupancy query and function attribute that a launch of this configuration

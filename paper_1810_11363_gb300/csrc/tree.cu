@@ -94,7 +94,7 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
   L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : (lane_kind ? 8192 : fixed_kind ? 4096 : 2048);
   L->cluster = t.cluster > 0 ? t.cluster : (lane_kind ? 2 : fixed_kind ? 4 : 8);
   L->threads = t.threads > 0 ? t.threads : 512;
-  const int fit = static_cast<int>((227 * 1024) / hist_smem_bytes(L->nb_alloc));
+  const int fit = static_cast<int>(SMEM_DYN_BUDGET / hist_smem_bytes(L->nb_alloc));
   L->blocks_per_sm = std::max(1, std::min(t.blocks_per_sm > 0 ? t.blocks_per_sm : 3, fit));
   const int hleaves = 1 << (L->D - 1);
   L->max_items = static_cast<int64_t>(L->G) * (ceil_div(L->n, L->rows_per_item) + hleaves + 1);
@@ -186,12 +186,25 @@ unsigned grid_stride_blocks(int64_t n, int block) {
 
 // ------------------------------------------------------------------ tree begin
 // The root's plan and segment (one thread): every row in leaf 0, chunked into units.
-__device__ void tree_begin_body(Plan* plan, Segs* seg, int n, int rows_per_item, int cs,
+// Rows of one work unit (its cs CTAs together) for a level whose directly computed
+// leaves hold `rows` rows: rows_per_item per CTA of the unit, or more when the level has
+// so many rows that this would give more than target_units units (larger units then
+// write fewer partials, and the launch's queue still has several items per cluster).
+// target_units = 0 keeps rows_per_item x cs.
+__device__ __forceinline__ int unit_rows(long long rows, int rows_per_item, int cs, int target_units) {
+  const long long floor_rows = static_cast<long long>(rows_per_item) * cs;
+  if (target_units <= 0) return static_cast<int>(floor_rows);
+  const long long r = (rows + target_units - 1) / target_units;
+  return static_cast<int>(r > floor_rows ? r : floor_rows);
+}
+
+__device__ void tree_begin_body(Plan* plan, Segs* seg, int n, int rows_per_item, int cs, int target_units,
                                 unsigned long long* rows_hist) {
   *rows_hist += static_cast<unsigned long long>(n);
-  const int per_unit = rows_per_item * cs;
+  const int per_unit = unit_rows(n, rows_per_item, cs, target_units);
   int chunks = (n + per_unit - 1) / per_unit;
   if (chunks < 1) chunks = 1;
+  plan->queue = 0;
   plan->n_small = 1;
   plan->total_units = chunks;
   plan->level_leaves = 1;
@@ -208,9 +221,9 @@ __device__ void tree_begin_body(Plan* plan, Segs* seg, int n, int rows_per_item,
   seg->order[0] = 0;
 }
 
-__global__ void tree_begin_kernel(Plan* plan, Segs* seg, int n, int rows_per_item, int cs,
+__global__ void tree_begin_kernel(Plan* plan, Segs* seg, int n, int rows_per_item, int cs, int target_units,
                                   unsigned long long* rows_hist) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) tree_begin_body(plan, seg, n, rows_per_item, cs, rows_hist);
+  if (threadIdx.x == 0 && blockIdx.x == 0) tree_begin_body(plan, seg, n, rows_per_item, cs, target_units, rows_hist);
 }
 
 // ----------------------------------------------------------------- scoring
@@ -467,7 +480,7 @@ __device__ __forceinline__ int split_bit(const uint8_t* bins, const uint8_t* bin
 // child of each pair is histogrammed directly, the other by subtraction).
 __device__ void plan_next_level(uint32_t* __restrict__ tile_cnt, int64_t n_ptiles, Segs* __restrict__ cur,
                                 Segs* __restrict__ nxt, Plan* __restrict__ plan, int depth, int rows_per_item,
-                                int cs, unsigned long long* __restrict__ rows_hist) {
+                                int cs, int target_units, unsigned long long* __restrict__ rows_hist) {
   __shared__ uint32_t sh[PT_THREADS / 32];
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -565,55 +578,75 @@ __device__ void plan_next_level(uint32_t* __restrict__ tile_cnt, int64_t n_ptile
       nxt->ones[l + L] = 0;
     }
   }
-  // pair p = children p and p + L of parent p; the smaller one is histogrammed directly
+  // pair p = children p and p + L of parent p; the smaller one is histogrammed directly.
+  // Its rows are cut into units of about the same size over the whole level; the pairs
+  // are listed by decreasing rows per CTA, so that a launch hands out its largest work
+  // items first.
   {
-    const int per_unit = rows_per_item * cs;
-    uint32_t v[PER_T];
-    int m_of[PER_T];
+    __shared__ int s_cr[1 << (MAX_DEPTH - 1)];         // rows per CTA of pair p
+    __shared__ int s_chunks_by_rank[1 << (MAX_DEPTH - 1)];
+    __shared__ int s_pair_by_rank[1 << (MAX_DEPTH - 1)];
+    __shared__ unsigned long long s_rows;
+    if (threadIdx.x == 0) s_rows = 0;
+    __syncthreads();
     unsigned long long rows = 0;
+    for (int p = threadIdx.x; p < L; p += blockDim.x) {
+      const int c1 = static_cast<int>(s_ones_by_leaf[p]);
+      rows += static_cast<unsigned long long>(min(cur->cnt[p] - c1, c1));
+    }
+    if (rows) atomicAdd(&s_rows, rows);
+    __syncthreads();
+    const int per_unit = unit_rows(static_cast<long long>(s_rows), rows_per_item, cs, target_units);
+    for (int p = threadIdx.x; p < L; p += blockDim.x) {
+      const int c1 = static_cast<int>(s_ones_by_leaf[p]);
+      const int m = min(cur->cnt[p] - c1, c1);
+      const int chunks = m > per_unit ? (m + per_unit - 1) / per_unit : 1;
+      s_cr[p] = m > 0 ? (m + chunks * cs - 1) / (chunks * cs) : 0;
+    }
+    __syncthreads();
+    // rank of pair p: pairs with more rows per CTA first, then by index
+    for (int p = threadIdx.x; p < L; p += blockDim.x) {
+      const int cr = s_cr[p];
+      int rank = 0;
+      for (int q = 0; q < L; ++q) rank += (s_cr[q] > cr || (s_cr[q] == cr && q < p)) ? 1 : 0;
+      const int c1 = static_cast<int>(s_ones_by_leaf[p]);
+      const int m = min(cur->cnt[p] - c1, c1);
+      s_chunks_by_rank[rank] = m > per_unit ? (m + per_unit - 1) / per_unit : 1;
+      s_pair_by_rank[rank] = p;
+    }
+    __syncthreads();
+    uint32_t v[PER_T];
 #pragma unroll
     for (int q = 0; q < PER_T; ++q) {
-      const int p = threadIdx.x * PER_T + q;
-      v[q] = 0;
-      m_of[q] = 0;
-      if (p < L) {
-        const int c = cur->cnt[p];
-        const int c1 = static_cast<int>(s_ones_by_leaf[p]);
-        const int m = min(c - c1, c1);
-        int chunks = (m + per_unit - 1) / per_unit;
-        if (chunks < 1) chunks = 1;
-        v[q] = static_cast<uint32_t>(chunks);
-        m_of[q] = m;
-        rows += static_cast<unsigned long long>(m);
-      }
+      const int r = threadIdx.x * PER_T + q;
+      v[q] = r < L ? static_cast<uint32_t>(s_chunks_by_rank[r]) : 0u;
     }
     uint32_t units;
     block_scan(v, units);
 #pragma unroll
     for (int q = 0; q < PER_T; ++q) {
-      const int p = threadIdx.x * PER_T + q;
-      if (p >= L) continue;
+      const int r = threadIdx.x * PER_T + q;
+      if (r >= L) continue;
+      const int p = s_pair_by_rank[r];
       const int c = cur->cnt[p];
       const int c1 = static_cast<int>(s_ones_by_leaf[p]);
       const int c0 = c - c1;
       const bool small_is_a = c0 <= c1;   // ties go to child p
-      const int small = small_is_a ? p : p + L;
-      const int m = m_of[q];
-      const int chunks = (m + per_unit - 1) / per_unit < 1 ? 1 : (m + per_unit - 1) / per_unit;
-      plan->small_leaf[p] = small;
-      plan->large_leaf[p] = small_is_a ? p + L : p;
-      plan->parent[p] = p;
-      plan->unit_begin[p] = static_cast<int>(v[q]);
-      plan->chunk_rows[p] = m > 0 ? (m + chunks * cs - 1) / (chunks * cs) : 1;
-      plan->seg_start[p] = small_is_a ? cur->start[p] : cur->start[p] + c0;
-      plan->seg_cnt[p] = m;
+      plan->small_leaf[r] = small_is_a ? p : p + L;
+      plan->large_leaf[r] = small_is_a ? p + L : p;
+      plan->parent[r] = p;
+      plan->unit_begin[r] = static_cast<int>(v[q]);
+      plan->chunk_rows[r] = s_cr[p] > 0 ? s_cr[p] : 1;
+      plan->seg_start[r] = small_is_a ? cur->start[p] : cur->start[p] + c0;
+      plan->seg_cnt[r] = min(c0, c1);
     }
-    if (rows) atomicAdd(rows_hist, rows);
     if (threadIdx.x == 0) {
+      atomicAdd(rows_hist, s_rows);
       plan->unit_begin[L] = static_cast<int>(units);
       plan->n_small = L;
       plan->total_units = static_cast<int>(units);
       plan->level_leaves = 2 * L;
+      plan->queue = 0;
     }
   }
 }
@@ -649,6 +682,7 @@ __device__ __forceinline__ void part_flags_body(const uint8_t* __restrict__ bins
                                   uint16_t* __restrict__ leaf, uint8_t* __restrict__ flags,
                                   uint32_t* __restrict__ tile_cnt, Segs* seg, int write_flags, int64_t n_ptiles,
                                   Segs* __restrict__ nxt, Plan* __restrict__ plan, int rows_per_item, int cs,
+                                  int target_units,
                                   unsigned long long* __restrict__ rows_hist, Misc* misc,
                                   const double* __restrict__ hist, int F, int max_bins,
                                   double* __restrict__ child_totals, int bid, int nblk,
@@ -717,7 +751,7 @@ __device__ __forceinline__ void part_flags_body(const uint8_t* __restrict__ bins
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  plan_next_level(tile_cnt, n_ptiles, seg, nxt, plan, depth, rows_per_item, cs, rows_hist);
+  plan_next_level(tile_cnt, n_ptiles, seg, nxt, plan, depth, rows_per_item, cs, target_units, rows_hist);
   if (threadIdx.x == 0) misc->done_part = 0;
 }
 
@@ -726,11 +760,14 @@ __global__ void part_flags_kernel(const uint8_t* __restrict__ bins, const uint8_
                                   uint16_t* __restrict__ leaf, uint8_t* __restrict__ flags,
                                   uint32_t* __restrict__ tile_cnt, Segs* seg, int write_flags, int64_t n_ptiles,
                                   Segs* __restrict__ nxt, Plan* __restrict__ plan, int rows_per_item, int cs,
+                                  int target_units,
                                   unsigned long long* __restrict__ rows_hist, Misc* misc,
                                   const double* __restrict__ hist, int F, int max_bins,
                                   double* __restrict__ child_totals, const uint8_t* __restrict__ chal_bins,
                                   const double* __restrict__ chal_hist, int chal_max_bins) {
-  part_flags_body(bins, bins_t, n, order, splits, depth, leaf, flags, tile_cnt, seg, write_flags, n_ptiles, nxt, plan, rows_per_item, cs, rows_hist, misc, hist, F, max_bins, child_totals, blockIdx.x, gridDim.x, chal_bins, chal_hist, chal_max_bins);
+  part_flags_body(bins, bins_t, n, order, splits, depth, leaf, flags, tile_cnt, seg, write_flags, n_ptiles, nxt, plan,
+                  rows_per_item, cs, target_units, rows_hist, misc, hist, F, max_bins, child_totals, blockIdx.x,
+                  gridDim.x, chal_bins, chal_hist, chal_max_bins);
 }
 
 // C: stable partition of every segment: the row at position i moves to
@@ -911,6 +948,7 @@ struct LevelProblem {
   const uint8_t* bins_t;
   int64_t n;
   int F, G, max_bins, rows_per_item, cs;
+  int target_units;           // work units per level of a histogram launch (0: rows_per_item x cs each)
   int64_t n_ptiles;
   int apply_blocks;
   const int32_t* n_borders;
@@ -959,7 +997,7 @@ __global__ void begin_batched_kernel(const LevelProblem* __restrict__ tab, const
     P.misc->done = 0;
     P.misc->done_part = 0;
     P.misc->forced_score = 0.0;
-    tree_begin_body(P.plan, P.seg_root, static_cast<int>(P.n), P.rows_per_item, P.cs, P.rows_hist);
+    tree_begin_body(P.plan, P.seg_root, static_cast<int>(P.n), P.rows_per_item, P.cs, P.target_units, P.rows_hist);
   }
 }
 
@@ -987,7 +1025,8 @@ __global__ void flags_batched_kernel(const LevelProblem* __restrict__ tab, const
   const int2 m = map[blockIdx.x];
   const LevelProblem& P = tab[m.x];
   part_flags_body(P.bins, P.bins_t, P.n, P.order_cur, P.sp, depth, P.leaf, P.flags, P.tcnt, P.seg_cur, write_flags,
-                  P.n_ptiles, P.seg_nxt, P.plan, P.rows_per_item, P.cs, P.rows_hist, P.misc, P.hist_cur, P.F,
+                  P.n_ptiles, P.seg_nxt, P.plan, P.rows_per_item, P.cs, P.target_units, P.rows_hist, P.misc,
+                  P.hist_cur, P.F,
                   P.max_bins, P.child_totals, m.y, static_cast<int>(P.n_ptiles), nullptr, nullptr, 0);
 }
 
@@ -1062,11 +1101,12 @@ cbg_status cbg_tree_begin(cbg_ctx* ctx, const cbg_tree_shape* shape, void* state
   CBG_CUDA(ctx, cudaMemsetAsync(leaf, 0, L.n * sizeof(uint16_t), ctx->stream));
   CBG_CUDA(ctx, cudaMemsetAsync(at<char>(state, L.o_seg_a), 0, sizeof(Segs), ctx->stream));
   CBG_CUDA(ctx, cudaMemsetAsync(at<char>(state, L.o_misc), 0, sizeof(Misc), ctx->stream));
-  int cs = 1;
-  st = hist_cluster_size(ctx, hist_config(L), &cs);
+  int cs = 1, clusters = 1;
+  st = hist_cluster_geom(ctx, hist_config(L), &cs, &clusters);
   if (st != CBG_OK) return st;
   tree_begin_kernel<<<1, 32, 0, ctx->stream>>>(at<Plan>(state, L.o_plan), at<Segs>(state, L.o_seg_a),
                                                static_cast<int>(L.n), L.rows_per_item, cs,
+                                               hist_target_units(clusters, L.G),
                                                at<unsigned long long>(state, L.o_count));
   CBG_CHECK_LAUNCH(ctx);
   return CBG_OK;
@@ -1175,14 +1215,15 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
                                   cudaMemcpyDeviceToDevice, ctx->stream));
   // 4. leaf update and (unless this is the last level) the row partition of the next level
   const bool last = a->last_level || d == L.D - 1;
-  int cs = 1;
+  int cs = 1, clusters = 1;
   if (!last) {
-    st = hist_cluster_size(ctx, hist_config(L), &cs);
+    st = hist_cluster_geom(ctx, hist_config(L), &cs, &clusters);
     if (st != CBG_OK) return st;
   }
   part_flags_kernel<<<static_cast<unsigned>(L.n_ptiles), PT_THREADS, 0, ctx->stream>>>(
       a->bins, a->bins_t, L.n, order_cur, a->splits, d, a->leaf, flags, tcnt, seg_cur, last ? 0 : 1, L.n_ptiles,
-      seg_nxt, plan, L.rows_per_item, cs, at<unsigned long long>(S, L.o_count), misc, hist_cur, L.F, L.max_bins,
+      seg_nxt, plan, L.rows_per_item, cs, hist_target_units(clusters, L.G), at<unsigned long long>(S, L.o_count),
+      misc, hist_cur, L.F, L.max_bins,
       a->child_totals, a->challenger ? a->challenger_bins : nullptr, a->challenger_hist, a->challenger_max_bins);
   CBG_CHECK_LAUNCH(ctx);
   if (!last) {
@@ -1816,7 +1857,10 @@ cbg_status cbg_autotune_tiles(cbg_ctx* ctx, const cbg_autotune_args* a, cbg_tile
       result = fail(ctx, CBG_ECUDA, "autotuner timing: %s", cudaGetErrorString(ce));
       break;
     }
-    if (!ok) continue;   // a candidate this device or these inputs cannot run
+    if (!ok) {           // a candidate this device or these inputs cannot run
+      cudaGetLastError();  // its API error must not surface in the caller's next launch check
+      continue;
+    }
     const double t = total / a->reps;
     if (t < best_t) {
       best_t = t;
