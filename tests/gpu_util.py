@@ -80,10 +80,13 @@ def hist_cell_report(hist, ref, ref_abs, direct_leaves, copied_feature=-1, rel=1
     direct_leaves; at every level except the root the feature of the parent's split is
     copied from the parent instead) must meet rel; the others (siblings obtained by
     subtraction, copied cells) carry their ancestors' rounding and are only reported.
-    Returns (worst direct ratio, worst other ratio), ratio = |gpu - fp64| / own sum."""
+    Returns (worst direct ratio, worst other ratio), ratio = |gpu - fp64| / own sum, over
+    cells that have rows."""
     err = np.abs(hist - ref)
     denom = np.maximum(ref_abs, 1e-300)
-    ratio = np.where(err <= atol, 0.0, err / denom)
+    # cells without rows of their own (own sum 0) have no relative error to report; a
+    # subtracted one may hold rounding residue, which the caller bounds by the root's rows
+    ratio = np.where((err <= atol) | (ref_abs == 0), 0.0, err / denom)
     direct = np.zeros(hist.shape[:2], bool)
     direct[list(direct_leaves)] = True
     if copied_feature >= 0:
