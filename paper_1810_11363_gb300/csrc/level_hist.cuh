@@ -1269,7 +1269,8 @@ constexpr int RD_THREADS = 256;   // 2 x RD_BINS x 32 = 256 cells, one per threa
 
 __device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
                   const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
-                  const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df, int bx, int by) {
+                  const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df, int bx, int by,
+                  const int32_t* __restrict__ n_borders = nullptr) {
   constexpr int CELLS = 2 * RD_BINS * GROUP;
   __shared__ double tile[GROUP][RD_BINS][2];
   const int jj = by;
@@ -1283,8 +1284,11 @@ __device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const
     const int fl = c % GROUP, rest = c / GROUP;
     const int st = rest / RD_BINS, bl = rest - st * RD_BINS;
     const int b = b0 + bl;
+    const int f = grp * GROUP + fl;
     double s = 0.0;
-    if (b < max_bins) {
+    // padding features and the bins above a feature's last border hold no rows: their
+    // partials are zero, and FP64 additions are scarce on this GPU
+    if (b < max_bins && f < F && (n_borders == nullptr || b <= n_borders[f])) {
       const float* src = partials + (static_cast<int64_t>(u0) * G + grp) * item_elems +
                          static_cast<int64_t>(st) * max_bins * GROUP + b * GROUP + fl;
       const int64_t step = G * item_elems;
@@ -1339,10 +1343,12 @@ __device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const
 __global__ void __launch_bounds__(RD_THREADS)
     reduce_kernel(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
                   const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
-                  const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df) {
+                  const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df,
+                  const int32_t* __restrict__ n_borders) {
   // the histogram launch that filled the partials has ended: rearm its work queue
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) const_cast<Plan*>(plan)->queue = 0;
-  reduce_body(plan, partials, G, F, max_bins, hist_prev, hist_cur, splits, depth, hist_df, blockIdx.x, blockIdx.y);
+  reduce_body(plan, partials, G, F, max_bins, hist_prev, hist_cur, splits, depth, hist_df, blockIdx.x, blockIdx.y,
+              n_borders);
 }
 
 // Grid of reduce_kernel for one level: (bin tiles x groups, directly computed leaves).

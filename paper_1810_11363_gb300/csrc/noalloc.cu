@@ -109,7 +109,7 @@ extern "C" cbg_status cbg_histogram_noalloc(cbg_ctx* ctx, const uint8_t* bins, i
                            : launch_hist<__nv_bfloat16>(ctx, hc, bins, nullptr, g, h, plan, partials);
   if (st != CBG_OK) return st;
   reduce_kernel<<<reduce_grid(hc.G, max_bins, 1), RD_THREADS, 0, ctx->stream>>>(plan, partials, hc.G, F, max_bins,
-                                                                               nullptr, hist_out, nullptr, 0, nullptr);
+                                                                               nullptr, hist_out, nullptr, 0, nullptr, nullptr);
   CBG_CHECK_LAUNCH(ctx);
   return CBG_OK;
 }

@@ -1007,7 +1007,7 @@ __global__ void __launch_bounds__(RD_THREADS) reduce_batched_kernel(const LevelP
   const LevelProblem& P = tab[m.x];
   const int gx = P.G * ((P.max_bins + RD_BINS - 1) / RD_BINS);
   reduce_body(P.plan, P.partials, P.G, P.F, P.max_bins, P.hist_prev, P.hist_cur, P.sp, depth, P.hist_df, m.y % gx,
-              m.y / gx);
+              m.y / gx, P.n_borders);
 }
 
 template <int SC_WARPS>
@@ -1190,7 +1190,7 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   // 2. FP64 reduction of the partials + sibling subtraction
   {
     reduce_kernel<<<reduce_grid(L.G, L.max_bins, d == 0 ? 1 : (1 << (d - 1))), RD_THREADS, 0, ctx->stream>>>(
-        plan, partials, L.G, L.F, L.max_bins, hist_prev, hist_cur, a->splits, d, hist_df);
+        plan, partials, L.G, L.F, L.max_bins, hist_prev, hist_cur, a->splits, d, hist_df, a->n_borders);
     CBG_CHECK_LAUNCH(ctx);
   }
   // 3. split scores and argmax
