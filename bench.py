@@ -45,15 +45,21 @@ def parse_args():
     p.add_argument("--ref-sample-trees", type=int, default=2)
     p.add_argument("--no-graph", action="store_true", help="launch every kernel from the host instead of "
                                                            "replaying one captured tree")
-    p.add_argument("--hist-kernel", choices=["pair", "lane", "wp", "red", "int", "cas64"], default="red",
-                   help="warp-private atomic-free histograms (wp), shared-memory float reductions (red) or "
-                        "shared-memory integer reductions of fixed-point values (int)")
+    p.add_argument("--hist-kernel", choices=["auto", "pair", "lane", "wp", "red", "int", "cas64"], default="auto",
+                   help="histogram kernel: the autotuner's pick among the FP32 kernels (auto), lane per feature "
+                        "(lane), the same with G and H in separate warps (pair), warp-private 16-feature "
+                        "histograms (wp), shared-memory float reductions (red) or shared-memory integer "
+                        "reductions of fixed-point values (int)")
     p.add_argument("--cluster", type=int, default=0, help="CTAs per histogram cluster (0 = library default)")
     p.add_argument("--rows-per-item", type=int, default=0, help="rows per CTA of a histogram work unit")
     p.add_argument("--hist-threads", type=int, default=0, help="threads per histogram CTA (0 = library default)")
-    p.add_argument("--batched-problems", type=int, default=64,
+    p.add_argument("--batched-problems", type=int, default=256,
                    help="problems of the batched_256 workload for the batched-vs-plain comparison (0 = skip)")
-    p.add_argument("--batched-trees", type=int, default=20)
+    p.add_argument("--batched-trees", type=int, default=200)
+    p.add_argument("--dense-trees", type=int, default=500,
+                   help="trees of the dense_400k workload (4e5 x 2000, 128 borders, depth 8; 0 = skip)")
+    p.add_argument("--precision-trees", type=int, default=300,
+                   help="trees of the precision_10m workload (1e7 rows, depth 10, FP32 and BF16; 0 = skip)")
     p.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-storage comparison step")
     p.add_argument("--no-fixed-point-form", action="store_true",
                    help="skip the fixed-point histogram comparison step")
@@ -159,15 +165,19 @@ def measured_peak_hbm():
 HIST_ITEM_START = "template <typename GH, int NB, int MODE>\n__device__ __forceinline__ void hist_item("
 HIST_KERNEL_START = ("template <typename GH, int NB, int MODE>\n__global__ void __launch_bounds__(512, 3) "
                      "level_hist_kernel(")
+LANE_UPDATE_START = "template <int N, int C>\n__device__ __forceinline__ void lane_batched_updates("
+LANE_KERNEL_START = "template <typename GH>\n__global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)\n    level_hist_lane_kernel("
+SOURCE_MARKERS = {"lane": (LANE_UPDATE_START, LANE_KERNEL_START)}
 
 
-def hist_source_hash():
-    """sha256 (first 16 hex digits) of the default histogram kernel's source text: its
-    per-item routine and the kernel, each from its template line to its closing brace."""
+def hist_source_hash(variant="red"):
+    """sha256 (first 16 hex digits) of a histogram kernel's source text: the shared-
+    reduction kernels' per-item routine and kernel, or the lane kernel's update routine
+    and kernel, each from its template line to its closing brace."""
     with open(HIST_SOURCE) as fh:
         src = fh.read()
     parts = []
-    for marker in (HIST_ITEM_START, HIST_KERNEL_START):
+    for marker in SOURCE_MARKERS.get(variant, (HIST_ITEM_START, HIST_KERNEL_START)):
         start = src.index(marker)
         parts.append(src[start:src.index("\n}\n", start) + 3])
     return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
@@ -179,7 +189,7 @@ def recorded_traffic_per_row(variant):
     try:
         with open(TRAFFIC_FILE.format(variant)) as fh:
             kv = dict(line.split(None, 1) for line in fh if line.strip() and not line.startswith("#"))
-        if kv.get("source_sha256_16", "").strip() != hist_source_hash():
+        if kv.get("source_sha256_16", "").strip() != hist_source_hash(variant):
             return None
         if kv.get("kernel_variant", "red").strip() != variant:
             return None
@@ -314,6 +324,106 @@ def scorer_bench(ctx, dev, trees, rows=100_000, F=2000, depth=6, reps=5):
             "timing": f"CUDA events, median of {reps} calls after 2 untimed",
             "paper_table3_context": "CatBoost CPU scorer on Epsilon, 8000 trees: 2.4 s (1 thread), 231 ms "
                                     "(32 threads), Intel Xeon E5-2660"}
+
+
+def hist_profile(ctx, prep, y, loss, depth, trees, lr, l2, gh, tiles, bufs):
+    """Histogram launches of `trees` trees run with host launches and CUDA events around
+    every histogram launch: (summed ms, launches, rows histogrammed)."""
+    from paper_1810_11363_gb300 import cbg, train
+    cbg.cbg_tree_rows_histogrammed(ctx, bufs.shape, bufs.state, reset=True)
+    cbg.cbg_profile_read(ctx, reset=True)
+    cbg.cbg_profile_enable(ctx, True)
+    bufs.pred.zero_()
+    train.fit(ctx, prep, y, loss, depth, trees, lr, l2, gh_dtype=gh, bufs=bufs, use_graph=False)
+    cbg.cbg_profile_enable(ctx, False)
+    ms, launches = cbg.cbg_profile_read(ctx, reset=True)
+    rows = cbg.cbg_tree_rows_histogrammed(ctx, bufs.shape, bufs.state, reset=True)
+    return ms, launches, rows
+
+
+def config_bench(ctx, dev, w, label_kind, forms, cpu_rows=0, prior=None):
+    """One of the stated workloads at its full size (inputs resident on the device,
+    histogram tiles from the autotuner, set up outside the timing): preprocessing once,
+    then `w.trees` trees with graph replay, timed with CUDA events, for each gradient
+    storage form in `forms`. Reports trees/s, row.feature.bins/s, the final training
+    loss, and the histogram kernel against the HBM roofline (algorithmic bytes: rows
+    read x (F bin bytes + g + h)) from one more tree with host launches. cpu_rows > 0
+    also times the oracle on a cpu_rows-row sample of the same generator (preprocessing
+    and one tree), extrapolated to the full rows (its cost grows with the rows)."""
+    import numpy as np
+    import torch
+    from paper_1810_11363_gb300 import cbg, synth, train
+
+    def dev_arr(a):
+        return torch.from_numpy(np.ascontiguousarray(a.view(np.int32) if a.dtype == np.uint32 else a)).to(dev)
+
+    x, y = dev_arr(w.x), dev_arr(w.y)
+    cat = dev_arr(w.cat) if w.n_cat else torch.zeros((0, w.n), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    train.preprocess(ctx, x, cat, y, label_kind, w.max_borders, a=w.a, seed=w.seed, prior=prior)   # warm-up
+    torch.cuda.synchronize()
+    e0.record(stream)
+    prep = train.preprocess(ctx, x, cat, y, label_kind, w.max_borders, a=w.a, seed=w.seed, prior=prior)
+    e1.record(stream)
+    e1.synchronize()
+    prep_ms = e0.elapsed_time(e1)
+    peak, peak_kind = measured_peak_hbm()
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {"workload": f"{w.name}: n={w.n}, {w.n_float} float + {w.n_cat} categorical features, {w.max_borders} "
+                       f"borders ({prep.max_bins} bins), depth {w.depth}, {w.trees} trees, lr {w.lr}, L2 {w.l2}, "
+                       f"{w.loss}", "preprocess_ms": prep_ms, "forms": {}}
+    for gh in forms:
+        tiles, _ = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2, gh_dtype=gh)
+        bufs = train.alloc_fit(prep, w.depth, w.trees, gh, tiles=tiles)
+        train.fit(ctx, prep, y, w.loss, w.depth, min(w.trees, 3), w.lr, w.l2, gh_dtype=gh, bufs=bufs, use_graph=True)
+        bufs.pred.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        train.fit(ctx, prep, y, w.loss, w.depth, w.trees, w.lr, w.l2, gh_dtype=gh, bufs=bufs, use_graph=True)
+        e1.record(stream)
+        e1.synchronize()
+        cbg.cbg_sync(ctx)
+        ms = e0.elapsed_time(e1)
+        loss = training_loss(w.loss, y, bufs.pred)
+        prof_trees = min(w.trees, 5)
+        hms, launches, rows = hist_profile(ctx, prep, y, w.loss, w.depth, prof_trees, w.lr, w.l2, gh, tiles, bufs)
+        gh_bytes = 4 if gh == "f32" else 2
+        achieved = rows * (prep.F + 2 * gh_bytes) / (hms / 1e3) / 1e9 if hms > 0 else None
+        upd = rows * prep.F / (hms / 1e3) if hms > 0 else None
+        out["forms"][gh] = {
+            "trees_per_s": w.trees / (ms / 1e3), "ms_per_tree": ms / w.trees,
+            "row_feature_bins_per_s": w.n * prep.F * prep.max_bins * w.depth * w.trees / (ms / 1e3),
+            "final_loss": loss,
+            "hist_tiles": {"kernel": tiles["kernel"], "cluster": tiles["cluster"],
+                           "rows_per_item": tiles["rows_per_item"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "peak_kind": f"{peak_kind} hbm_gbs",
+                         "avg_launch_us": hms * 1e3 / max(launches, 1), "launches": launches,
+                         "smem_updates_per_sm_clk": upd / (n_sms * 2070e6) if upd else None,
+                         "timing": f"CUDA events around every histogram launch of {prof_trees} trees with host "
+                                   "launches"}}
+        del bufs
+    if len(forms) > 1:
+        base = out["forms"][forms[0]]["final_loss"]
+        for gh in forms[1:]:
+            f = out["forms"][gh]
+            f["rel_final_loss_diff_vs_" + forms[0]] = abs(f["final_loss"] - base) / abs(base)
+            f["speed_vs_" + forms[0]] = f["trees_per_s"] / out["forms"][forms[0]]["trees_per_s"]
+    if cpu_rows > 0:
+        import oracle
+        gen = {"dense_400k": synth.dense_400k, "precision_10m": synth.precision_10m}[w.name]
+        ws = gen(n=cpu_rows, seed=w.seed, trees=1)
+        t_prep, t_tree, _ = oracle_sample(ws, train.f_pad_for(ws.n_features), 1)
+        scale = w.n / cpu_rows
+        t_full = scale * (t_prep + w.trees * t_tree)
+        out["cpu_baseline"] = {"value": w.trees / t_full, "unit": "trees/s", "cores": 1, "kind": "oracle",
+                               "sample": f"oracle on a {cpu_rows}-row sample of the same generator: preprocessing "
+                                         f"{t_prep:.1f} s, one tree {t_tree:.1f} s; extrapolated x{scale:g} rows to "
+                                         f"a {w.trees}-tree run (prep + trees x tree)"}
+    del prep, x, y, cat
+    torch.cuda.empty_cache()
+    return out
 
 
 def paper_setting_bench(ctx, dev, trees, n=400_000, F=2000, borders=15, depth=6):
@@ -516,9 +626,16 @@ def run_ours(args):
         return prep, model
 
     prep0 = train.preprocess(ctx, x, cat, y, "binary", w.max_borders, a=w.a, seed=w.seed)
-    tiles = {"kernel": {"wp": 2, "red": 1, "cas64": 3, "lane": 4, "pair": 5, "int": 7}[args.hist_kernel],
-             "cluster": args.cluster,
-             "rows_per_item": args.rows_per_item, "threads": args.hist_threads}
+    if args.hist_kernel == "auto":
+        # histogram tiles from the autotuner on this workload (setup, outside the timing)
+        tiles, _ = train.autotune(ctx, prep0, y, w.loss, D, w.l2, gh_dtype=args.gh)
+        tiles = {k: tiles[k] for k in ("kernel", "cluster", "rows_per_item")}
+        tiles["threads"] = args.hist_threads
+    else:
+        tiles = {"kernel": {"wp": 2, "red": 1, "cas64": 3, "lane": 4, "pair": 5, "int": 7}[args.hist_kernel],
+                 "cluster": args.cluster,
+                 "rows_per_item": args.rows_per_item, "threads": args.hist_threads}
+    variant = {2: "wp", 1: "red", 3: "cas64", 4: "lane", 5: "pair", 7: "int", 0: "red", 6: "lane4"}[tiles["kernel"]]
     bufs = train.alloc_fit(prep0, D, T, args.gh, tiles=tiles)
     for _ in range(args.warmup):
         step(bufs)
@@ -568,11 +685,12 @@ def run_ours(args):
     alg_bytes = rows_hist * (F + 2 * gh_bytes)
     achieved = alg_bytes / (hist_ms / 1e3) / 1e9 if hist_ms > 0 else None
     peak, peak_kind = measured_peak_hbm()
-    per_row = recorded_traffic_per_row(args.hist_kernel)
+    per_row = recorded_traffic_per_row(variant)
     rows_per_launch = rows_hist / max(hist_launches, 1)
-    roofline = {"bound": "hbm", "kernel": {"wp": "level_hist_wp_kernel", "lane": "level_hist_lane_kernel", "pair": "level_hist_pair_kernel"}.get(
-                    args.hist_kernel, "level_hist_kernel"),
-                "kernel_variant": args.hist_kernel,
+    roofline = {"bound": "hbm", "kernel": {"wp": "level_hist_wp_kernel", "lane": "level_hist_lane_kernel",
+                                           "pair": "level_hist_pair_kernel", "lane4": "level_hist_lane4_kernel"}.get(
+                    variant, "level_hist_kernel"),
+                "kernel_variant": variant,
                 "achieved": achieved, "peak": peak,
                 "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
@@ -642,7 +760,7 @@ def run_ours(args):
                          abs(forms["f32"]["final_loss"])}
     # the opt-in fixed-point histogram (int32 cells, native shared integer reductions; its
     # shared-memory accumulation is not FP32) against FP32 on the same workload
-    if not args.no_fixed_point_form and args.hist_kernel == "red":
+    if not args.no_fixed_point_form and variant != "int":
         tiles_fp = {"kernel": 7, "cluster": 4, "rows_per_item": 4096}
         bufs_fp = train.alloc_fit(prep0, D, T, args.gh, tiles=tiles_fp)
         step(bufs_fp)
@@ -692,6 +810,14 @@ def run_ours(args):
     combos = None
     if args.combo_trees > 0 and rank == 0:
         combos = combos_bench(ctx, dev, x, cat, y, w, args.combo_trees, args.combo_borders, 4, tiles)
+    dense = None
+    if args.dense_trees > 0 and rank == 0:
+        dense = config_bench(ctx, dev, synth.dense_400k(trees=args.dense_trees), "binary", ["f32"],
+                             cpu_rows=0 if args.no_cpu_baseline else 20_000)
+    precision = None
+    if args.precision_trees > 0 and rank == 0:
+        precision = config_bench(ctx, dev, synth.precision_10m(trees=args.precision_trees), "real", ["f32", "bf16"],
+                                 cpu_rows=0 if args.no_cpu_baseline else 500_000)
 
     # kernels of ours per step: the preprocessing launches of logloss_1m (133, counted in
     # its ncu launch list: permutation sort, one sort for the ordered TS of the 10
@@ -721,6 +847,7 @@ def run_ours(args):
                 "clocks": clk,
                 "forms": forms, "batched_vs_plain": batched, "scorer": scorer, "paper_setting": paper_setting,
                 "ordered_boosting": ordered, "feature_combinations": combos,
+                "dense_400k": dense, "precision_10m": precision,
                 "breakdown": {"step_ms": step_ms}}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -76,3 +76,9 @@ def test_recorded_traffic_needs_the_same_kernel_source_and_variant(tmp_path, mon
     assert bench.recorded_traffic_per_row("red") == 321.4
     assert bench.recorded_traffic_per_row("int") is None      # taken on another source
     assert bench.recorded_traffic_per_row("lane") is None     # no capture for the variant
+    (tmp_path / "hist_kernel_traffic_lane.txt").write_text(
+        f"source_sha256_16 {h}\nkernel_variant lane\ndram_bytes_per_row 200.0\n")
+    assert bench.recorded_traffic_per_row("lane") is None     # the red kernel's source hash
+    (tmp_path / "hist_kernel_traffic_lane.txt").write_text(
+        f"source_sha256_16 {bench.hist_source_hash('lane')}\nkernel_variant lane\ndram_bytes_per_row 200.0\n")
+    assert bench.recorded_traffic_per_row("lane") == 200.0
