@@ -122,6 +122,14 @@ const char* cbg_last_error(const cbg_ctx* ctx);
 /* Wait for the context's stream; returns CBG_ECUDA / CBG_EDATA / CBG_ETIMEOUT
  * if an asynchronous failure was recorded, else CBG_OK. */
 cbg_status cbg_sync(cbg_ctx* ctx);
+/* Test hook for the bounded device-side waits (no counterpart in the paper). While
+ * enabled (enable != 0), rounds that cbg_boost_batched captures make each wait of its
+ * persistent per-level kernel look for a count that can never arrive, and give up after
+ * a short limit (about a millisecond per wait) instead of the regular one (about a
+ * second): the kernel records a timeout, skips the work behind the wait and ends, and
+ * the next cbg_sync returns CBG_ETIMEOUT. The results of such rounds are meaningless;
+ * the context stays usable. Off by default; not for production use. */
+cbg_status cbg_test_force_wait_timeout(cbg_ctx* ctx, int enable);
 cbg_status cbg_set_stream(cbg_ctx* ctx, void* cuda_stream);
 /* Number of SMs of the context's device (for tiling decisions). */
 int cbg_num_sms(const cbg_ctx* ctx);
@@ -329,12 +337,19 @@ typedef struct cbg_problem {
 } cbg_problem;
 
 /* Batched boosting of many independent problems (each follows cbg_boost, the
- * classic scheme of Sections 3-4). One round -- one tree of every problem -- is
- * captured once as a single CUDA graph whose `branches` parallel branches
- * (problems assigned round-robin, 0 = min(n_problems, 32)) let the GPU run the
- * small problems' kernels concurrently; the round is replayed `trees` times.
- * Every problem uses the same depth, lr, l2 and gradient storage; problem i's
- * result is the same as cbg_boost on it alone. problems is a host array. */
+ * classic scheme of Sections 3-4); not in the paper. One round -- one tree of every
+ * problem -- is captured once as a CUDA graph and replayed `trees` times.
+ * When every problem uses the shared-reduction histogram kernel (tiles.kernel 0 or 1)
+ * with the same tiling, each step of a round is one launch over all problems: the tree
+ * start, then per level one persistent launch whose clusters take histogram work items
+ * and FP64 reduction blocks of every problem from one device queue (a reduction block
+ * waits, bounded, for its leaf's histogram items: CBG_ETIMEOUT at the next cbg_sync if
+ * a wait runs out), then scoring, partition flags and scatter, and the apply and record
+ * kernels. Otherwise every problem's tree runs on one of `branches` parallel graph
+ * branches (problems round-robin, 0 = min(n_problems, 32)). Every problem uses the same
+ * depth, lr, l2 and gradient storage; problem i's result is the same as cbg_boost on it
+ * alone (bit for bit where the histogram accumulation order allows; within the tests'
+ * tolerances always). problems is a host array. */
 cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t n_problems, int32_t gh_dtype,
                              int32_t depth, int32_t trees, double lr, double l2, int32_t branches);
 

@@ -118,6 +118,7 @@ SIGNATURES = {
     "cbg_ctx_destroy": (None, [c_vp]),
     "cbg_last_error": (C.c_char_p, [c_vp]),
     "cbg_sync": (c_i32, [c_vp]),
+    "cbg_test_force_wait_timeout": (c_i32, [c_vp, c_i32]),
     "cbg_set_stream": (c_i32, [c_vp, c_vp]),
     "cbg_num_sms": (C.c_int, [c_vp]),
     "cbg_make_permutation": (c_i32, [c_vp, c_u64, c_i64, c_vp]),
@@ -225,6 +226,11 @@ def cbg_version() -> str:
 
 def cbg_sync(ctx: Context):
     ctx.check(ctx.lib.cbg_sync(ctx.h), "cbg_sync")
+
+
+def cbg_test_force_wait_timeout(ctx: Context, enable: bool):
+    """Test hook: make the bounded waits of batched rounds captured from now on run out."""
+    ctx.check(ctx.lib.cbg_test_force_wait_timeout(ctx.h, int(enable)), "cbg_test_force_wait_timeout")
 
 
 def cbg_num_sms(ctx: Context) -> int:

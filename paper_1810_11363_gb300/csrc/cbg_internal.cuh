@@ -31,6 +31,7 @@ struct cbg_ctx {
   std::vector<cudaStream_t> branch_streams;  // branches of a captured batched round
   std::vector<cudaEvent_t> branch_events;
   void* noalloc_scratch = nullptr;   // device address of cbg_histogram_noalloc's array (looked up once)
+  bool test_force_wait_timeout = false;   // cbg_test_force_wait_timeout: bounded waits run out
 };
 
 namespace cbg {

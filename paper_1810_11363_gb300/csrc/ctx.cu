@@ -156,6 +156,12 @@ cbg_status cbg_set_stream(cbg_ctx* ctx, void* cuda_stream) {
   return CBG_OK;
 }
 
+cbg_status cbg_test_force_wait_timeout(cbg_ctx* ctx, int enable) {
+  if (!ctx) return CBG_EINVAL;
+  ctx->test_force_wait_timeout = enable != 0;
+  return CBG_OK;
+}
+
 cbg_status cbg_sync(cbg_ctx* ctx) {
   if (!ctx) return CBG_EINVAL;
   DeviceGuard guard(ctx->device);

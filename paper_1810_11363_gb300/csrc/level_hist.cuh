@@ -33,6 +33,8 @@ struct Plan {
   int total_units;                  // sum of chunks over those leaves
   int level_leaves;                 // 2^d
   int queue;                        // next work item of the running histogram launch
+  int rqueue;                       // batched form: next reduction chunk of the running launch
+  int done[MAX_HLEAVES];            // batched form: work items of leaf jj whose partials are written
   int small_leaf[MAX_HLEAVES];
   int large_leaf[MAX_HLEAVES];      // sibling obtained by subtraction (-1: none)
   int parent[MAX_HLEAVES];          // index of the parent in the previous histogram
@@ -171,6 +173,12 @@ struct HistProblem {
   const Plan* plan;
   int max_bins;
   float* partials;
+  // the batched form also reduces the partials into the level's FP64 histogram
+  const double* hist_prev;
+  double* hist_cur;
+  const cbg_split* splits;
+  float2* hist_df;
+  const int32_t* n_borders;
 };
 
 // One work item (unit x group) of one problem, for this CTA of the cluster: accumulate
@@ -184,7 +192,7 @@ struct HistProblem {
 // memory after the last barrier, so a CTA may exit as soon as it finds the queue empty.
 // Before the first take the cluster synchronises once, so that every CTA has started.
 __device__ __forceinline__ void queue_take(const Plan* plan, int* slot, int cs) {
-  const int v = atomicAdd(&const_cast<Plan*>(plan)->queue, 1);
+  const int v = atomicAdd(&const_cast<Plan*>(plan)->queue, 1);   // the launch's counter (see Plan::queue)
   cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
   for (int r = 0; r < cs; ++r) *cl.map_shared_rank(slot, r) = v;
 }
@@ -192,7 +200,8 @@ __device__ __forceinline__ int queue_read(const int* slot) { return *reinterpret
 
 template <typename GH, int NB, int MODE>
 __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs, int rank, float* hsh,
-                                          const float* const* peer, uint32_t sbase, int* next_slot = nullptr) {
+                                          const float* const* peer, uint32_t sbase, int* next_slot = nullptr,
+                                          const Plan* queue_plan = nullptr, bool signal_done = false) {
   namespace cgr = cooperative_groups;
   constexpr int PLANE = NB * GROUP;
   __shared__ int s_exp[2];   // MODE 2: this CTA's fixed-point exponents of G and H
@@ -338,7 +347,8 @@ __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs
     }
   }
   cgr::this_cluster().sync();
-  if (next_slot != nullptr && rank == 0 && threadIdx.x == 0) queue_take(P.plan, next_slot, cs);
+  if (next_slot != nullptr && rank == 0 && threadIdx.x == 0)
+    queue_take(queue_plan != nullptr ? queue_plan : P.plan, next_slot, cs);
   // this CTA's slice of bins, summed over the cluster's CTAs in rank order
   const int max_bins = P.max_bins;
   const int bs = (max_bins + cs - 1) / cs;
@@ -372,7 +382,10 @@ __device__ __forceinline__ void hist_item(const HistProblem& P, int item, int cs
       dst[st * (max_bins * GROUP) + b0 * GROUP + rem] = v;
     }
   }
+  if (signal_done) __threadfence();   // this CTA's partial slice, visible before the count below
   cgr::this_cluster().sync();
+  // every CTA of the cluster has written its slice: one more item of leaf jj is complete
+  if (signal_done && rank == 0 && threadIdx.x == 0) atomicAdd(&const_cast<Plan*>(plan)->done[jj], 1);
 }
 
 // Cluster geometry shared by the single-problem and batched kernels: rank, cluster index,
@@ -409,51 +422,6 @@ __global__ void __launch_bounds__(512, 3) level_hist_kernel(const uint8_t* __res
   cooperative_groups::this_cluster().sync();
   for (int item = queue_read(&s_next); item < total_items; item = queue_read(&s_next))
     hist_item<GH, NB, MODE>(P, item, k.cs, k.rank, hsh, k.peer, k.sbase, &s_next);
-}
-
-// The batched form: one launch for a level of many problems. The work items of all
-// problems are numbered one after the other; every CTA first computes, from the problems'
-// plans, the first item of each problem, then walks the items like the single-problem
-// kernel, looking up an item's problem by binary search.
-constexpr int HIST_MAX_BATCH = 2048;
-
-template <typename GH, int NB>
-__global__ void __launch_bounds__(512, 3) level_hist_batched_kernel(const HistProblem* __restrict__ probs, int n_probs) {
-  extern __shared__ __align__(16) float hsh[];   // [2][NB][32]
-  __shared__ int s_first[HIST_MAX_BATCH + 1];
-  __shared__ int s_carry;
-  HistCta k(hsh);
-  // s_first[p] = items of problems 0..p-1 (block-wide scan in chunks of blockDim)
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  for (int base = 0; base < n_probs; base += blockDim.x) {
-    const int p = base + threadIdx.x;
-    const int cnt = p < n_probs ? probs[p].plan->total_units * probs[p].G : 0;
-    s_first[p < n_probs ? p + 1 : HIST_MAX_BATCH] = cnt;   // counts, scanned below
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int run = s_carry;
-      const int end = min(n_probs, base + static_cast<int>(blockDim.x));
-      for (int q = base; q < end; ++q) {
-        run += s_first[q + 1];
-        s_first[q + 1] = run;
-      }
-      s_carry = run;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) s_first[0] = 0;
-  __syncthreads();
-  const int total_items = s_first[n_probs];
-  for (int item = k.cid; item < total_items; item += k.ncl) {
-    int lo = 0, hi = n_probs - 1;   // last p with s_first[p] <= item
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_first[mid] <= item) lo = mid; else hi = mid - 1;
-    }
-    const HistProblem P = probs[lo];
-    hist_item<GH, NB, 0>(P, item - s_first[lo], k.cs, k.rank, hsh, k.peer, k.sbase);
-  }
 }
 
 // Warp-private histogram, no atomics (the paper's Section 5 scheme: per-warp partial
@@ -1267,12 +1235,13 @@ __device__ __forceinline__ void put_cell(double* hist, float2* hist_df, int64_t 
 constexpr int RD_BINS = 4;
 constexpr int RD_THREADS = 256;   // 2 x RD_BINS x 32 = 256 cells, one per thread
 
-__device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
+template <int BINS>
+__device__ __forceinline__ void reduce_tile(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
                   const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
                   const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df, int bx, int by,
-                  const int32_t* __restrict__ n_borders = nullptr) {
+                  const int32_t* __restrict__ n_borders, double (*tile)[BINS][2]) {   // tile: shared [GROUP][BINS][2]
+  constexpr int RD_BINS = BINS;   // bins of the tile: 2 x BINS x 32 cells
   constexpr int CELLS = 2 * RD_BINS * GROUP;
-  __shared__ double tile[GROUP][RD_BINS][2];
   const int jj = by;
   if (jj >= plan->n_small) return;
   const int nbt = (max_bins + RD_BINS - 1) / RD_BINS;
@@ -1280,7 +1249,7 @@ __device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const
   if (grp >= G) return;
   const int u0 = plan->unit_begin[jj], u1 = plan->unit_begin[jj + 1];
   const int64_t item_elems = static_cast<int64_t>(2) * max_bins * GROUP;
-  for (int c = threadIdx.x; c < CELLS; c += RD_THREADS) {
+  for (int c = threadIdx.x; c < CELLS; c += blockDim.x) {
     const int fl = c % GROUP, rest = c / GROUP;
     const int st = rest / RD_BINS, bl = rest - st * RD_BINS;
     const int b = b0 + bl;
@@ -1312,7 +1281,7 @@ __device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const
   const int par = plan->parent[jj];
   const bool exact = large >= 0 && depth > 0 && splits[depth - 1].feature >= grp * GROUP &&
                      splits[depth - 1].feature < (grp + 1) * GROUP;
-  for (int c = threadIdx.x; c < CELLS; c += RD_THREADS) {
+  for (int c = threadIdx.x; c < CELLS; c += blockDim.x) {
     const int fl = c / (2 * RD_BINS), rem = c - fl * (2 * RD_BINS);
     const int bl = rem >> 1, st = rem & 1;
     const int f = grp * GROUP + fl, b = b0 + bl;
@@ -1340,6 +1309,16 @@ __device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const
   }
 }
 
+// The reduction's block for the regular launch: a tile of RD_BINS bins, one cell a thread.
+__device__ __forceinline__ void reduce_body(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
+                  const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
+                  const cbg_split* __restrict__ splits, int depth, float2* __restrict__ hist_df, int bx, int by,
+                  const int32_t* __restrict__ n_borders = nullptr) {
+  __shared__ double tile[GROUP][RD_BINS][2];
+  reduce_tile<RD_BINS>(plan, partials, G, F, max_bins, hist_prev, hist_cur, splits, depth, hist_df, bx, by, n_borders,
+                       tile);
+}
+
 __global__ void __launch_bounds__(RD_THREADS)
     reduce_kernel(const Plan* __restrict__ plan, const float* __restrict__ partials, int G, int F, int max_bins,
                   const double* __restrict__ hist_prev, double* __restrict__ hist_cur,
@@ -1349,6 +1328,138 @@ __global__ void __launch_bounds__(RD_THREADS)
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) const_cast<Plan*>(plan)->queue = 0;
   reduce_body(plan, partials, G, F, max_bins, hist_prev, hist_cur, splits, depth, hist_df, blockIdx.x, blockIdx.y,
               n_borders);
+}
+
+// The batched form: one persistent launch for a level of many problems, in two phases.
+// 1. Clusters take the histogram work items of every problem (unit x group, as in the
+//    single-problem kernel, numbered problem after problem) from one queue (the first
+//    problem's Plan::queue).
+// 2. A CTA whose cluster finds that queue empty turns to the FP64 reduction: it takes
+//    chunks of reduction tiles (BATCH_RD_CHUNK tiles of BATCH_RD_BINS bins of a group, the
+//    single-problem reduction's blocks made 512 cells wide, of one directly built leaf)
+//    from a second queue
+//    (Plan::rqueue), on its own. A chunk of leaf jj first waits until every histogram
+//    item of jj has written its partials (Plan::done). Those items were all handed out
+//    before any cluster reached phase 2 and are held by clusters still running phase 1,
+//    so the wait ends; it is bounded all the same: after wait_limit polls it sets
+//    STATUS_TIMEOUT in the context's status word (reported by cbg_sync) and skips the
+//    chunk, so the launch ends and the context stays usable. wait_extra > 0 raises the
+//    count waited for past what can arrive (a test hook that makes every wait run out).
+constexpr int HIST_MAX_BATCH = 2048;
+constexpr int BATCH_RD_BINS = 8;      // phase-2 tiles: 2 x 8 x 32 = 512 cells, one per thread of a 512-thread CTA
+constexpr int BATCH_RD_CHUNK = 4;     // tiles of a phase-2 chunk
+constexpr unsigned BATCH_WAIT_LIMIT = 1u << 22;       // polls of about 0.25 us: about 1 s
+// Dynamic shared memory of the batched kernel: the histogram, and at least the phase-2
+// reduction tile that reuses it.
+inline size_t batched_smem_bytes(int nb) {
+  const size_t tile = sizeof(double) * GROUP * BATCH_RD_BINS * 2;
+  return hist_smem_bytes(nb) > tile ? hist_smem_bytes(nb) : tile;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// first[p] = sum over problems q < p of count(q), a block-wide scan in chunks of blockDim
+template <typename Count>
+__device__ void batch_prefix(int n_probs, int* first, int* carry, Count count) {
+  if (threadIdx.x == 0) *carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n_probs; base += blockDim.x) {
+    const int p = base + threadIdx.x;
+    first[p < n_probs ? p + 1 : HIST_MAX_BATCH] = p < n_probs ? count(p) : 0;   // counts, scanned below
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int run = *carry;
+      const int end = min(n_probs, base + static_cast<int>(blockDim.x));
+      for (int q = base; q < end; ++q) {
+        run += first[q + 1];
+        first[q + 1] = run;
+      }
+      *carry = run;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) first[0] = 0;
+  __syncthreads();
+}
+
+__device__ __forceinline__ int batch_find(const int* first, int n_probs, int item) {
+  int lo = 0, hi = n_probs - 1;   // last p with first[p] <= item
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename GH, int NB>
+__global__ void __launch_bounds__(512, 3) level_hist_batched_kernel(const HistProblem* __restrict__ probs, int n_probs,
+                                                                    int depth, unsigned* __restrict__ status,
+                                                                    int wait_extra, unsigned wait_limit) {
+  extern __shared__ __align__(16) float hsh[];   // [2][NB][32]
+  __shared__ int s_first[HIST_MAX_BATCH + 1];
+  __shared__ int s_carry;
+  __shared__ int s_next;
+  __shared__ int s_ok;
+  namespace cgr = cooperative_groups;
+  HistCta k(hsh);
+  const Plan* qplan = probs[0].plan;
+  // phase 1: histogram items
+  batch_prefix(n_probs, s_first, &s_carry, [&](int p) { return probs[p].plan->total_units * probs[p].G; });
+  cgr::this_cluster().sync();
+  if (k.rank == 0 && threadIdx.x == 0) queue_take(qplan, &s_next, k.cs);
+  cgr::this_cluster().sync();
+  const int total_items = s_first[n_probs];
+  for (int item = queue_read(&s_next); item < total_items; item = queue_read(&s_next)) {
+    const int p = batch_find(s_first, n_probs, item);
+    hist_item<GH, NB, 0>(probs[p], item - s_first[p], k.cs, k.rank, hsh, k.peer, k.sbase, &s_next, qplan, true);
+  }
+  // phase 2: reduction chunks, each CTA on its own (no distributed shared memory from here,
+  // so the CTA's histogram buffer serves as the reduction's tile)
+  __syncthreads();
+  auto gx_of = [&](int p) { return probs[p].G * ((probs[p].max_bins + BATCH_RD_BINS - 1) / BATCH_RD_BINS); };
+  auto chunks_per_leaf = [&](int p) { return (gx_of(p) + BATCH_RD_CHUNK - 1) / BATCH_RD_CHUNK; };
+  batch_prefix(n_probs, s_first, &s_carry, [&](int p) { return probs[p].plan->n_small * chunks_per_leaf(p); });
+  const int total_chunks = s_first[n_probs];
+  int* const rq = &const_cast<Plan*>(qplan)->rqueue;
+  while (true) {
+    if (threadIdx.x == 0) s_next = atomicAdd(rq, 1);
+    __syncthreads();
+    const int c = s_next;
+    if (c >= total_chunks) break;
+    const int p = batch_find(s_first, n_probs, c);
+    const HistProblem& P = probs[p];
+    const int cpl = chunks_per_leaf(p), gx = gx_of(p);
+    const int local = c - s_first[p];
+    const int jj = local / cpl;
+    const int b0 = (local - jj * cpl) * BATCH_RD_CHUNK;
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      const int need = (P.plan->unit_begin[jj + 1] - P.plan->unit_begin[jj]) * P.G + wait_extra;
+      unsigned polls = 0;
+      while (ld_acquire_gpu(&P.plan->done[jj]) < need) {
+        if (++polls > wait_limit) {
+          atomicOr(status, ::cbg::STATUS_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok)
+      for (int bx = b0; bx < min(gx, b0 + BATCH_RD_CHUNK); ++bx) {
+        reduce_tile<BATCH_RD_BINS>(P.plan, P.partials, P.G, P.F, P.max_bins, P.hist_prev, P.hist_cur, P.splits, depth,
+                                   P.hist_df, bx, jj, P.n_borders,
+                                   reinterpret_cast<double (*)[BATCH_RD_BINS][2]>(hsh));   // the histogram's buffer
+        __syncthreads();   // every thread has read the shared tile before the next tile overwrites it
+      }
+    __syncthreads();   // s_next and s_ok are rewritten next round
+  }
 }
 
 // Grid of reduce_kernel for one level: (bin tiles x groups, directly computed leaves).
@@ -1622,12 +1733,12 @@ cbg_status batched_clusters(cbg_ctx* ctx, int threads, int cs, int* clusters) {
   }
   auto kern = level_hist_batched_kernel<GH, NB>;
   CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(hist_smem_bytes(NB))));
+                                     static_cast<int>(batched_smem_bytes(NB))));
   if (cs > 8) CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(cs * ctx->num_sms));
   cfg.blockDim = dim3(static_cast<unsigned>(threads));
-  cfg.dynamicSmemBytes = hist_smem_bytes(NB);
+  cfg.dynamicSmemBytes = batched_smem_bytes(NB);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = static_cast<unsigned>(cs);
@@ -1647,7 +1758,8 @@ cbg_status batched_clusters(cbg_ctx* ctx, int threads, int cs, int* clusters) {
 }
 
 template <typename GH, int NB>
-cbg_status launch_hist_batched_nb(cbg_ctx* ctx, const HistProblem* table, int n_probs, int threads, int cs) {
+cbg_status launch_hist_batched_nb(cbg_ctx* ctx, const HistProblem* table, int n_probs, int threads, int cs, int depth,
+                                  int wait_extra, unsigned wait_limit) {
   int clusters = 0;
   cbg_status st = batched_clusters<GH, NB>(ctx, threads, cs, &clusters);
   if (st != CBG_OK) return st;
@@ -1655,7 +1767,7 @@ cbg_status launch_hist_batched_nb(cbg_ctx* ctx, const HistProblem* table, int n_
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(cs * clusters));
   cfg.blockDim = dim3(static_cast<unsigned>(threads));
-  cfg.dynamicSmemBytes = hist_smem_bytes(NB);
+  cfg.dynamicSmemBytes = batched_smem_bytes(NB);
   cfg.stream = ctx->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1664,15 +1776,18 @@ cbg_status launch_hist_batched_nb(cbg_ctx* ctx, const HistProblem* table, int n_
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_batched_kernel<GH, NB>, table, n_probs));
+  CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_batched_kernel<GH, NB>, table, n_probs, depth, ctx->d_status,
+                                   wait_extra, wait_limit));
   return CBG_OK;
 }
 
-// One histogram launch for a level of many problems (shared-reduction kernel): table is a
-// device array of n_probs entries, nb_alloc the largest bin allocation among them.
+// One histogram-and-reduction launch for level `depth` of many problems (shared-reduction
+// kernel): table is a device array of n_probs entries, nb_alloc the largest bin allocation
+// among them; wait_extra / wait_limit as for level_hist_batched_kernel.
 template <typename GH>
 cbg_status launch_hist_batched(cbg_ctx* ctx, int nb_alloc, const HistProblem* table, int n_probs, int threads,
-                               int cs, bool query_only = false) {
+                               int cs, bool query_only = false, int depth = 0, int wait_extra = 0,
+                               unsigned wait_limit = BATCH_WAIT_LIMIT) {
   auto run = [&](auto nbc) -> cbg_status {
     constexpr int NB = decltype(nbc)::value;
     if (query_only) {
@@ -1681,7 +1796,7 @@ cbg_status launch_hist_batched(cbg_ctx* ctx, int nb_alloc, const HistProblem* ta
       if (st != CBG_OK) return st;
       return clusters > 0 ? CBG_OK : CBG_EUNSUPPORTED;
     }
-    return launch_hist_batched_nb<GH, NB>(ctx, table, n_probs, threads, cs);
+    return launch_hist_batched_nb<GH, NB>(ctx, table, n_probs, threads, cs, depth, wait_extra, wait_limit);
   };
   switch (nb_alloc) {
     case 2: return run(std::integral_constant<int, 2>{});

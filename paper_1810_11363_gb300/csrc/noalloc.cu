@@ -42,6 +42,8 @@ cbg_status scratch_address(cbg_ctx* ctx, void** out) {
 __global__ void root_plan_kernel(Plan* plan, int n, int units, int chunk_rows) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   plan->queue = 0;
+  plan->rqueue = 0;
+  plan->done[0] = 0;
   plan->n_small = 1;
   plan->total_units = units;
   plan->level_leaves = 1;

@@ -205,6 +205,8 @@ __device__ void tree_begin_body(Plan* plan, Segs* seg, int n, int rows_per_item,
   int chunks = (n + per_unit - 1) / per_unit;
   if (chunks < 1) chunks = 1;
   plan->queue = 0;
+  plan->rqueue = 0;
+  plan->done[0] = 0;
   plan->n_small = 1;
   plan->total_units = chunks;
   plan->level_leaves = 1;
@@ -632,6 +634,7 @@ __device__ void plan_next_level(uint32_t* __restrict__ tile_cnt, int64_t n_ptile
       const int c1 = static_cast<int>(s_ones_by_leaf[p]);
       const int c0 = c - c1;
       const bool small_is_a = c0 <= c1;   // ties go to child p
+      plan->done[r] = 0;
       plan->small_leaf[r] = small_is_a ? p : p + L;
       plan->large_leaf[r] = small_is_a ? p + L : p;
       plan->parent[r] = p;
@@ -647,6 +650,7 @@ __device__ void plan_next_level(uint32_t* __restrict__ tile_cnt, int64_t n_ptile
       plan->total_units = static_cast<int>(units);
       plan->level_leaves = 2 * L;
       plan->queue = 0;
+      plan->rqueue = 0;
     }
   }
 }
@@ -1001,14 +1005,6 @@ __global__ void begin_batched_kernel(const LevelProblem* __restrict__ tab, const
   }
 }
 
-__global__ void __launch_bounds__(RD_THREADS) reduce_batched_kernel(const LevelProblem* __restrict__ tab,
-                                                                    const int2* __restrict__ map, int depth) {
-  const int2 m = map[blockIdx.x];
-  const LevelProblem& P = tab[m.x];
-  const int gx = P.G * ((P.max_bins + RD_BINS - 1) / RD_BINS);
-  reduce_body(P.plan, P.partials, P.G, P.F, P.max_bins, P.hist_prev, P.hist_cur, P.sp, depth, P.hist_df, m.y % gx,
-              m.y / gx, P.n_borders);
-}
 
 template <int SC_WARPS>
 __global__ void __launch_bounds__(SC_WARPS * 32) score_batched_kernel(const LevelProblem* __restrict__ tab,
@@ -1459,9 +1455,10 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
     CBG_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned), ctx->stream));
   }
   if (trees == 0) return CBG_OK;
-  // One histogram launch per level for all problems when they all use the shared-reduction
-  // kernel with the same tiling (the plans are chunked for one cluster size); the other
-  // kernels of a level run per problem on the graph branches.
+  // When every problem uses the shared-reduction kernel with the same tiling (the plans are
+  // chunked for one cluster size), every kernel of a round is one launch over all problems,
+  // the level's histograms and FP64 reductions in one persistent launch; otherwise each
+  // problem's tree runs on one of the graph's parallel branches.
   bool batch_hist = n_problems <= HIST_MAX_BATCH;
   Layout L0;
   {
@@ -1479,10 +1476,8 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
   }
   std::vector<HistProblem*> tables;        // histogram tables, one per level
   std::vector<LevelProblem*> ltables;      // level tables, one per level
-  std::vector<int2*> reduce_maps;          // block maps of the reduction, one per level
   int2 *begin_map = nullptr, *score_map = nullptr, *tile_map = nullptr, *apply_map = nullptr;
   int begin_blocks = 0, score_blocks = 0, tile_blocks = 0, apply_blocks = 0;
-  std::vector<int> reduce_blocks;
   if (batch_hist) {
     cbg_status st = hist_cluster_size(ctx, hist_config(L0), &cs_plan);
     if (st != CBG_OK) return st;
@@ -1494,11 +1489,16 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
   if (batch_hist) {
     // host copies of every table and block map, then one upload into the workspace
     std::vector<Layout> Ls(n_problems);
-    for (int i = 0; i < n_problems; ++i) make_layout(ctx, &problems[i].shape, &Ls[i]);
+    std::vector<int> target_units(n_problems, 0);
+    for (int i = 0; i < n_problems; ++i) {
+      make_layout(ctx, &problems[i].shape, &Ls[i]);
+      int cs_i = 1, clusters_i = 1;
+      if (hist_cluster_geom(ctx, hist_config(Ls[i]), &cs_i, &clusters_i) == CBG_OK)
+        target_units[i] = hist_target_units(clusters_i, Ls[i].G);
+    }
     std::vector<std::vector<HistProblem>> hts(depth, std::vector<HistProblem>(n_problems));
     std::vector<std::vector<LevelProblem>> lts(depth, std::vector<LevelProblem>(n_problems));
     std::vector<int2> bmap, smap, tmap, amap;
-    std::vector<std::vector<int2>> rmaps(depth);
     for (int i = 0; i < n_problems; ++i) {
       const cbg_problem& p = problems[i];
       const Layout& L = Ls[i];
@@ -1522,6 +1522,7 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
         q.max_bins = L.max_bins;
         q.rows_per_item = L.rows_per_item;
         q.cs = cs_plan;
+        q.target_units = target_units[i];   // the units a single-problem run would cut the level into
         q.n_ptiles = L.n_ptiles;
         q.apply_blocks = apply_grid;
         q.n_borders = p.n_borders;
@@ -1552,9 +1553,12 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
         q.order_nxt = at<uint32_t>(S, (d + 1) % 2 == 1 ? L.o_order_a : L.o_order_b);
         q.hist_cur = at<double>(S, d % 2 == 0 ? L.o_hist_a : L.o_hist_b);
         q.hist_prev = at<double>(S, d % 2 == 0 ? L.o_hist_b : L.o_hist_a);
-        const int n_small = d == 0 ? 1 : (1 << (d - 1));
-        const int rb = L.G * static_cast<int>(ceil_div(L.max_bins, RD_BINS)) * n_small;
-        for (int b = 0; b < rb; ++b) rmaps[d].push_back(make_int2(i, b));
+        // the level's FP64 reduction runs inside the batched histogram launch
+        hts[d][i].hist_prev = q.hist_prev;
+        hts[d][i].hist_cur = q.hist_cur;
+        hts[d][i].splits = q.sp;
+        hts[d][i].hist_df = q.hist_df;
+        hts[d][i].n_borders = q.n_borders;
       }
     }
     size_t need = 4096;
@@ -1562,7 +1566,6 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
     need += depth * (bytes(sizeof(HistProblem) * n_problems) + bytes(sizeof(LevelProblem) * n_problems));
     need += bytes(sizeof(int2) * bmap.size()) + bytes(sizeof(int2) * smap.size()) + bytes(sizeof(int2) * tmap.size()) +
             bytes(sizeof(int2) * amap.size());
-    for (int d = 0; d < depth; ++d) need += bytes(sizeof(int2) * rmaps[d].size());
     cbg_status st = ws_reserve(ctx, need);
     if (st != CBG_OK) return st;
     Carve cv(ctx->ws);
@@ -1577,9 +1580,6 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
       ltables.push_back(cv.take<LevelProblem>(n_problems));
       st = upload(lts[d].data(), sizeof(LevelProblem) * n_problems, ltables.back());
       if (st != CBG_OK) break;
-      reduce_maps.push_back(cv.take<int2>(rmaps[d].size()));
-      reduce_blocks.push_back(static_cast<int>(rmaps[d].size()));
-      st = upload(rmaps[d].data(), sizeof(int2) * rmaps[d].size(), reduce_maps.back());
     }
     begin_map = cv.take<int2>(bmap.size());
     score_map = cv.take<int2>(smap.size());
@@ -1662,12 +1662,15 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
     begin_batched_kernel<<<begin_blocks, 256, 0, origin>>>(ltables[0], begin_map);
     launched("batched tree start");
     for (int d = 0; d < depth && st == CBG_OK; ++d) {
+      // histograms and their FP64 reduction, one persistent launch for every problem
+      const int wait_extra = ctx->test_force_wait_timeout ? 1 : 0;
+      const unsigned wait_limit = ctx->test_force_wait_timeout ? 4096u : BATCH_WAIT_LIMIT;
       st = gh_dtype == CBG_F32
-               ? launch_hist_batched<float>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan)
-               : launch_hist_batched<__nv_bfloat16>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan);
+               ? launch_hist_batched<float>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan, false, d,
+                                            wait_extra, wait_limit)
+               : launch_hist_batched<__nv_bfloat16>(ctx, nb_alloc, tables[d], n_problems, L0.threads, cs_plan,
+                                                    false, d, wait_extra, wait_limit);
       if (st != CBG_OK) break;
-      reduce_batched_kernel<<<reduce_blocks[d], RD_THREADS, 0, origin>>>(ltables[d], reduce_maps[d], d);
-      launched("batched reduction");
       const int level_leaves = 1 << d;
       auto score = [&](auto warps) {
         constexpr int W = decltype(warps)::value;

@@ -526,3 +526,60 @@ def test_pack_bins4_flags_bins_of_16_and_more(ctx):
         cbg.cbg_sync(ctx)
     assert e.value.status == cbg.CBG_EDATA
     cbg.cbg_sync(ctx)     # the flag is cleared once reported
+
+
+def _batched_inputs(ctx, n_problems, n_max, trees):
+    import torch
+    ws = synth.batched_256(n_problems=n_problems, n_max=n_max, trees=trees)
+    preps, ys = [], []
+    for w in ws:
+        cat = to_dev(w.cat) if w.n_cat else torch.zeros((0, w.n), dtype=torch.int32, device="cuda")
+        preps.append(train.preprocess(ctx, to_dev(w.x), cat, to_dev(w.y), w.label_kind, w.max_borders, a=w.a,
+                                      seed=w.seed))
+        ys.append(to_dev(w.y))
+    return ws, preps, ys
+
+
+def test_batched_16_problems_lockstep(ctx):
+    """The batched form's persistent per-level launch (histogram items and FP64 reduction
+    blocks of every problem from one queue) on 16 problems of the batching workload
+    (uneven rows, features, categoricals, both losses), 20 trees each, every problem in
+    lock step with the oracle on its own preprocessing."""
+    depth, trees, lr, l2 = 6, 20, 0.1, 3.0
+    ws, preps, ys = _batched_inputs(ctx, 16, 60000, trees)
+    models, _ = train.fit_batched(ctx, preps, ys, [w.loss for w in ws], depth, trees, lr, l2)
+    cbg.cbg_sync(ctx)
+    ties = 0
+    for i, (w, p) in enumerate(zip(ws, preps)):
+        rp = oracle.preprocess(w, p.F_pad)
+        assert np.array_equal(train.rowmajor_from_grouped(to_host(p.bins), w.n, p.F_pad), rp["bins"]), i
+        sp = models[i].host_splits()
+        res = oracle.fit(rp["bins"], w.n_features, rp["n_borders"], w.y, w.loss, depth, trees, lr, l2, follow=sp)
+        rep = lockstep_check(res, sp, to_host(models[i].pred), to_host(models[i].leaf_values), where=f"problem {i}")
+        ties += rep["near_ties_followed"]
+    report("batched form, 16 problems x 20 trees (lock step)", {"near_ties_followed": ties})
+
+
+def test_batched_wait_runs_out_and_the_context_recovers(ctx):
+    """With the test hook on, every bounded wait of the batched kernel looks for a count
+    that cannot arrive: the kernel gives up after its limit, cbg_sync reports
+    CBG_ETIMEOUT, and the context then trains the same problems correctly (equal to
+    problem-by-problem runs)."""
+    depth, trees, lr, l2 = 4, 2, 0.1, 3.0
+    ws, preps, ys = _batched_inputs(ctx, 3, 20000, trees)
+    cbg.cbg_test_force_wait_timeout(ctx, True)
+    try:
+        train.fit_batched(ctx, preps, ys, [w.loss for w in ws], depth, trees, lr, l2)
+        with pytest.raises(cbg.CbgError) as e:
+            cbg.cbg_sync(ctx)
+        assert e.value.status == cbg.CBG_ETIMEOUT
+    finally:
+        cbg.cbg_test_force_wait_timeout(ctx, False)
+    cbg.cbg_sync(ctx)                       # the status word was cleared when reported
+    models, _ = train.fit_batched(ctx, preps, ys, [w.loss for w in ws], depth, trees, lr, l2)
+    cbg.cbg_sync(ctx)
+    for i, (w, p, y) in enumerate(zip(ws, preps, ys)):
+        alone = train.fit(ctx, p, y, w.loss, depth, trees, lr, l2, use_graph=True)
+        cbg.cbg_sync(ctx)
+        assert np.array_equal(alone.host_splits()["feature"], models[i].host_splits()["feature"]), i
+        assert np.allclose(to_host(alone.pred), to_host(models[i].pred), rtol=0, atol=1e-6), i
