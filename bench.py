@@ -45,9 +45,11 @@ def parse_args():
     p.add_argument("--ref-sample-trees", type=int, default=2)
     p.add_argument("--no-graph", action="store_true", help="launch every kernel from the host instead of "
                                                            "replaying one captured tree")
-    p.add_argument("--hist-kernel", choices=["auto", "pair", "lane", "wp", "red", "int", "cas64"], default="auto",
+    p.add_argument("--hist-kernel", choices=["auto", "pair", "lane", "lane_ld", "wp", "red", "int", "cas64"],
+                   default="auto",
                    help="histogram kernel: the autotuner's pick among the FP32 kernels (auto), lane per feature "
-                        "(lane), the same with G and H in separate warps (pair), warp-private 16-feature "
+                        "(lane), the same with a loader warp (lane_ld) or with G and H in separate warps (pair), "
+                        "warp-private 16-feature "
                         "histograms (wp), shared-memory float reductions (red) or shared-memory integer "
                         "reductions of fixed-point values (int)")
     p.add_argument("--cluster", type=int, default=0, help="CTAs per histogram cluster (0 = library default)")
@@ -167,7 +169,10 @@ HIST_KERNEL_START = ("template <typename GH, int NB, int MODE>\n__global__ void 
                      "level_hist_kernel(")
 LANE_UPDATE_START = "template <int N, int C>\n__device__ __forceinline__ void lane_batched_updates("
 LANE_KERNEL_START = "template <typename GH>\n__global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)\n    level_hist_lane_kernel("
-SOURCE_MARKERS = {"lane": (LANE_UPDATE_START, LANE_KERNEL_START)}
+LANE_LD_KERNEL_START = ("template <typename GH>\n__global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)\n"
+                        "    level_hist_lane_ld_kernel(")
+SOURCE_MARKERS = {"lane": (LANE_UPDATE_START, LANE_KERNEL_START),
+                  "lane_ld": (LANE_UPDATE_START, LANE_LD_KERNEL_START)}
 
 
 def hist_source_hash(variant="red"):
@@ -642,10 +647,12 @@ def run_ours(args):
         tiles = {k: tiles[k] for k in ("kernel", "cluster", "rows_per_item")}
         tiles["threads"] = args.hist_threads
     else:
-        tiles = {"kernel": {"wp": 2, "red": 1, "cas64": 3, "lane": 4, "pair": 5, "int": 7}[args.hist_kernel],
+        tiles = {"kernel": {"wp": 2, "red": 1, "cas64": 3, "lane": 4, "pair": 5, "int": 7, "lane_ld": 8}[
+                     args.hist_kernel],
                  "cluster": args.cluster,
                  "rows_per_item": args.rows_per_item, "threads": args.hist_threads}
-    variant = {2: "wp", 1: "red", 3: "cas64", 4: "lane", 5: "pair", 7: "int", 0: "red", 6: "lane4"}[tiles["kernel"]]
+    variant = {2: "wp", 1: "red", 3: "cas64", 4: "lane", 5: "pair", 7: "int", 0: "red", 6: "lane4",
+               8: "lane_ld"}[tiles["kernel"]]
     bufs = train.alloc_fit(prep0, D, T, args.gh, tiles=tiles)
     for _ in range(args.warmup):
         step(bufs)
@@ -698,7 +705,8 @@ def run_ours(args):
     per_row = recorded_traffic_per_row(variant)
     rows_per_launch = rows_hist / max(hist_launches, 1)
     roofline = {"bound": "hbm", "kernel": {"wp": "level_hist_wp_kernel", "lane": "level_hist_lane_kernel",
-                                           "pair": "level_hist_pair_kernel", "lane4": "level_hist_lane4_kernel"}.get(
+                                           "pair": "level_hist_pair_kernel", "lane4": "level_hist_lane4_kernel",
+                                           "lane_ld": "level_hist_lane_ld_kernel"}.get(
                     variant, "level_hist_kernel"),
                 "kernel_variant": variant,
                 "achieved": achieved, "peak": peak,

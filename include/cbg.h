@@ -80,7 +80,10 @@ typedef struct cbg_split {
  * packed bins of cbg_pack_bins4 (max_bins <= 16; the level arguments carry
  * bins4), 7 = one shared histogram per CTA of int32 fixed-point cells updated
  * with shared-memory integer reductions (4096 rows per CTA and clusters of 4 by
- * default). The default (0) is kernel 1, whose shared-memory accumulation is FP32.
+ * default), 8 = kernel 4 with loader warps: each histogram warp has a partner
+ * warp that stages its rows' bin records and (g, h), so that it only updates its
+ * histogram (threads counts both; bins 16-byte aligned). The default (0) is kernel 1, whose shared-memory
+ * accumulation is FP32.
  * Kernel 7 is an opt-in form that does not accumulate in FP32: it rounds each (g, h) of a CTA's rows to a
  * multiple of 2^-e, e the largest exponent with 2^e * 1.001 * S < 2^30 for S the
  * sum of |g| (of |h| for H) over those rows, with a dither hashed from the row's
@@ -124,11 +127,13 @@ const char* cbg_last_error(const cbg_ctx* ctx);
 cbg_status cbg_sync(cbg_ctx* ctx);
 /* Test hook for the bounded device-side waits (no counterpart in the paper). While
  * enabled (enable != 0), rounds that cbg_boost_batched captures make each wait of its
- * persistent per-level kernel look for a count that can never arrive, and give up after
- * a short limit (about a millisecond per wait) instead of the regular one (about a
- * second): the kernel records a timeout, skips the work behind the wait and ends, and
- * the next cbg_sync returns CBG_ETIMEOUT. The results of such rounds are meaningless;
- * the context stays usable. Off by default; not for production use. */
+ * persistent per-level kernel look for a count that can never arrive, and histogram
+ * launches of the loader-warp kernel (tiles.kernel 8) have their loaders skip the
+ * hand-over of every buffer, so that the compute warps wait for data that never comes.
+ * Either kernel gives up after a short limit (about a millisecond per wait) instead of
+ * the regular one (about a second): it records a timeout, skips the work behind the
+ * wait and ends, and the next cbg_sync returns CBG_ETIMEOUT. The results of such calls
+ * are meaningless; the context stays usable. Off by default; not for production use. */
 cbg_status cbg_test_force_wait_timeout(cbg_ctx* ctx, int enable);
 cbg_status cbg_set_stream(cbg_ctx* ctx, void* cuda_stream);
 /* Number of SMs of the context's device (for tiling decisions). */
@@ -465,7 +470,8 @@ cbg_status cbg_predict(cbg_ctx* ctx, const cbg_predict_args* args);
  * ctx stream, CUDA events), and writes the fastest to *best and its mean device
  * time per tree (ms) to *best_ms. The candidates vary:
  *  - the histogram kernel: shared-memory reductions (1), lane-per-feature warp
- *    histograms (4) and their one-statistic-per-warp form (5), 16-feature
+ *    histograms (4), their loader-warp form (8) and their one-statistic-per-warp
+ *    form (5), 16-feature
  *    warp-private histograms (2), with bins4 and max_bins <= 16 the packed
  *    lane-per-feature kernel (6), and with fixed_point != 0 the fixed-point
  *    shared-reduction kernel (7);

@@ -578,9 +578,8 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
 // the row id and the position-ordered (g, h) of row i four blocks ahead and copies the
 // row's 32-byte bin record with cp.async two blocks ahead. Within a block the rows are
 // updated in batches of LH_BATCH: the histogram loads of a batch are issued before its
-// stores, and a row whose cell repeats an earlier row of the batch takes that row's new
-// value (forwarding in registers), so one shared-memory round trip serves a whole batch
-// (lane_batched_updates). A 255-bin warp histogram is 64 KB, so an SM holds 3 such
+// stores, and rows of the batch that share a cell are summed before they are added to it,
+// so one shared-memory round trip serves a whole batch (lane_batched_updates). A 255-bin warp histogram is 64 KB, so an SM holds 3 such
 // warps; the batches give each warp the instruction-level parallelism it needs.
 // At the end of a work unit the warps of a CTA are summed into warp 0's histogram, and
 // CTA r of the cluster sums its slice of bins over the cluster (distributed shared
@@ -593,7 +592,7 @@ constexpr int LH_BATCH = 4;       // rows whose histogram loads are issued befor
 
 // Histogram accesses of the lane kernel. Volatile keeps them in program order among
 // themselves (a load issued ahead of a store to the same cell must stay ahead of it, the
-// forwarding relies on that); without a memory clobber the staging-buffer loads around
+// batched updates rely on that); without a memory clobber the staging-buffer loads around
 // them remain free to be scheduled early.
 __device__ __forceinline__ float2 lds_f2(uint32_t addr) {
   float2 v;
@@ -609,9 +608,12 @@ __device__ __forceinline__ void sts_f2(uint32_t addr, float2 v) {
 // from the staged pairs gh4, two rows per float4; row0 is even). A warp's shared load
 // waits for that warp's own earlier shared stores, so an update loop that loads a row's
 // cell after the previous row's store pays one full shared-memory round trip per row.
-// Here the loads of LH_BATCH rows (of every chain) are issued before any of their stores;
-// a row whose cell repeats an earlier row of the same batch and chain takes that row's new
-// value instead of its own, stale, load. Every cell still adds its rows in row order.
+// Here the loads of LH_BATCH rows (of every chain) are issued before any of their stores.
+// Rows of a batch that share a cell loaded the same value, so each row adds to its loaded
+// value the sum of its own (g, h) and those of the earlier rows of the batch in that cell,
+// and the last of them stores the cell's new value (the stores go in row order). The sums
+// depend only on the addresses and the staged pairs, not on the loads, which keeps the
+// dependent chain behind each load to one addition.
 template <int N, int C>
 __device__ __forceinline__ void lane_batched_updates(const uint32_t (&a)[C][N], const float4* __restrict__ gh4, int row0,
                                                      const bool (&act)[C]) {
@@ -623,18 +625,26 @@ __device__ __forceinline__ void lane_batched_updates(const uint32_t (&a)[C][N], 
     for (int c = 0; c < C; ++c)
 #pragma unroll
       for (int j = 0; j < LH_BATCH; ++j) v[c][j] = act[c] ? lds_f2(a[c][i0 + j]) : make_float2(0.f, 0.f);
+    float gx[LH_BATCH], hy[LH_BATCH];
 #pragma unroll
     for (int j = 0; j < LH_BATCH; ++j) {
       const float4 gq = gh4[(row0 + i0 + j) >> 1];
-      const float gx = ((i0 + j) & 1) ? gq.z : gq.x;
-      const float hy = ((i0 + j) & 1) ? gq.w : gq.y;
+      gx[j] = ((i0 + j) & 1) ? gq.z : gq.x;
+      hy[j] = ((i0 + j) & 1) ? gq.w : gq.y;
+    }
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+      for (int j = 0; j < LH_BATCH; ++j) {
+        float sx = gx[j], sy = hy[j];
 #pragma unroll
         for (int q = 0; q < j; ++q)
-          if (a[c][i0 + q] == a[c][i0 + j]) v[c][j] = v[c][q];
-        v[c][j].x += gx;
-        v[c][j].y += hy;
+          if (a[c][i0 + q] == a[c][i0 + j]) {
+            sx += gx[q];
+            sy += hy[q];
+          }
+        v[c][j].x += sx;
+        v[c][j].y += sy;
       }
     }
 #pragma unroll
@@ -791,6 +801,283 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
           const float2 v = hist_all[static_cast<int64_t>(w) * per_warp + e];
           s.x += v.x;
           s.y += v.y;
+        }
+        hist_all[e] = s;
+      }
+    }
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
+    // this CTA's slice of bins, summed over the cluster's CTAs in rank order
+    const int bs = (max_bins + cs - 1) / cs;
+    const int b0 = rank * bs;
+    const int nbs = max(0, min(max_bins, b0 + bs) - b0);
+    float* dst = partials + static_cast<int64_t>(item) * (2 * max_bins * GROUP);
+    for (int i = threadIdx.x; i < nbs * GROUP; i += blockDim.x) {
+      const int e = b0 * GROUP + i;
+      float sx = 0.f, sy = 0.f;
+      for (int r = 0; r < cs; ++r) {
+        const float2 v = peer0[r][e];
+        sx += v.x;
+        sy += v.y;
+      }
+      dst[e] = sx;
+      dst[max_bins * GROUP + e] = sy;
+    }
+    cl.sync();
+  }
+}
+
+// ------------------------- lane-per-feature with loader warps (warp specialised)
+// The lane kernel's warps stage their own rows: with one warp per scheduler, the time a
+// warp spends fetching row ids, copying bin records and waiting for them adds to the time
+// of its histogram updates instead of overlapping it. Here a CTA has W compute warps, each
+// with its private [max_bins][32] (G, H) table updated as in the lane kernel, and W loader
+// warps: warp W + w stages every block of 32 rows of compute warp w. Block b of a work item
+// goes to compute warp b % W, and every work item is padded to a multiple of W blocks. A
+// loader fetches row ids and position-ordered (g, h) into registers a batch of LD_AHEAD
+// blocks ahead and writes a block into one of its warp's LD_STAGES buffers: the rows'
+// 32-byte bin records with cp.async, the (g, h) pairs with plain stores. Two mbarriers per
+// buffer hand it over: `full` (32 arrivals, one per loader lane, each also waiting for
+// that lane's copies) and `empty` (one arrival by the compute warp once it has read the
+// buffer). One loader for all compute warps (its chain of shared-memory round trips
+// queues behind the compute warps' histogram traffic) fell behind them.
+// Every wait polls a bounded number of times: a wait that runs out records STATUS_TIMEOUT
+// in `status` and raises the CTA's abort flag, after which the CTA's waits all give up at
+// once and skip their work, so every warp still reaches the barriers of the work item and
+// the launch ends. For a test of that path, test_stall != 0 makes the loaders skip their
+// arrivals on `full` (the compute warps then wait for a phase that never completes) and
+// wait_limit sets the polls of a wait.
+constexpr int LD_STAGES = 4;                  // buffers per compute warp
+constexpr int LD_AHEAD = 8;                   // blocks per batch of row-id and (g, h) loads of the loader
+constexpr unsigned LD_WAIT_LIMIT = 1u << 24;  // polls of one mbarrier wait (about a second at most)
+
+inline size_t ld_warp_bytes(int max_bins) {
+  return static_cast<size_t>(max_bins) * GROUP * sizeof(float2) +
+         static_cast<size_t>(LD_STAGES) * (LH_ROWS * GROUP + LH_ROWS * sizeof(float2) + 2 * sizeof(uint64_t));
+}
+inline int ld_warps(int max_bins, int requested_threads) {   // compute warps (as many loaders come on top)
+  int w = static_cast<int>(SMEM_DYN_BUDGET / ld_warp_bytes(max_bins));
+  if (w > LH_MAX_WARPS / 2) w = LH_MAX_WARPS / 2;
+  if (requested_threads > 0 && requested_threads / 64 < w) w = requested_threads / 64;
+  return w < 1 ? 1 : w;
+}
+inline size_t ld_smem_bytes(int max_bins, int warps) { return static_cast<size_t>(warps) * ld_warp_bytes(max_bins); }
+
+// Waits until the mbarrier at shared address `bar` has completed the phase of the given
+// parity. Every lane of the warp calls it; false (for the whole warp) if the CTA aborts or
+// the wait runs out (which starts the abort).
+__device__ __forceinline__ bool ld_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* status,
+                                        unsigned limit) {
+  bool ok = false;
+  for (unsigned polls = 0;; ++polls) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) {
+      ok = true;
+      break;
+    }
+    if (*abort_flag) break;
+    if (polls >= limit) {
+      atomicOr(status, ::cbg::STATUS_TIMEOUT);
+      *abort_flag = 1;
+      break;
+    }
+  }
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// One arrival on `bar` once every cp.async this thread has issued so far has completed.
+__device__ __forceinline__ void mbar_arrive_after_copies(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+// Whether the mbarrier at `bar` has completed the phase of the given parity (one poll).
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+template <typename GH>
+__global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
+    level_hist_lane_ld_kernel(const uint8_t* __restrict__ bins, int64_t n, int G, int F,
+                              const uint32_t* __restrict__ order, const GH* __restrict__ gpos,
+                              const GH* __restrict__ hpos, const Plan* __restrict__ plan, int max_bins,
+                              float* __restrict__ partials, unsigned* __restrict__ status, int test_stall,
+                              unsigned wait_limit) {
+  namespace cgr = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char lsh[];
+  constexpr int MAX_CS = 16;
+  constexpr uint32_t NONE = 0xffffffffu;
+  constexpr uint32_t FULL_MASK = 0xffffffffu;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int cs = static_cast<int>(cl.num_blocks());
+  const int rank = static_cast<int>(cl.block_rank());
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int W = (blockDim.x >> 5) / 2;   // compute warps 0..W-1; warp W + w loads for warp w
+  const int per_warp = max_bins * GROUP;
+  float2* hist_all = reinterpret_cast<float2*>(lsh);
+  unsigned char* recs = lsh + static_cast<size_t>(W) * per_warp * sizeof(float2);
+  float2* ghs = reinterpret_cast<float2*>(recs + static_cast<size_t>(W) * LD_STAGES * LH_ROWS * GROUP);
+  const uint32_t recs_s = static_cast<uint32_t>(__cvta_generic_to_shared(recs));
+  const uint32_t full_s = static_cast<uint32_t>(__cvta_generic_to_shared(ghs + W * LD_STAGES * LH_ROWS));
+  const uint32_t empty_s = full_s + static_cast<uint32_t>(W * LD_STAGES * sizeof(uint64_t));
+  const int maxb1 = max_bins - 1;
+  const float2* peer0[MAX_CS];
+  for (int r = 0; r < cs && r < MAX_CS; ++r) peer0[r] = cl.map_shared_rank(hist_all, r);
+  const int total_items = plan->total_units * G;
+  const int n_small = plan->n_small;
+  __shared__ int s_next;    // this cluster's next work item
+  __shared__ int s_abort;   // a wait of this CTA ran out
+  if (threadIdx.x < 2 * W * LD_STAGES) {
+    const uint32_t bar = full_s + threadIdx.x * static_cast<uint32_t>(sizeof(uint64_t));
+    // full: one arrival per loader lane, each once that lane's copies have landed;
+    // empty: one by the compute warp
+    const uint32_t count = threadIdx.x < W * LD_STAGES ? 32u : 1u;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n\tfence.mbarrier_init.release.cluster;" ::"r"(bar),
+                 "r"(count)
+                 : "memory");
+  }
+  if (threadIdx.x == 0) s_abort = 0;
+  // Blocks each compute warp has taken so far in this launch: every work item is padded
+  // to a multiple of W blocks (the padding blocks have no rows), so the count is the same
+  // for every warp.
+  uint32_t U = 0;
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
+  cl.sync();
+  for (int item = queue_read(&s_next); item < total_items; item = queue_read(&s_next)) {
+    const int unit = item / G, grp = item - unit * G;
+    int lo = 0, hi = n_small - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (plan->unit_begin[mid] <= unit) lo = mid; else hi = mid - 1;
+    }
+    const int jj = lo;
+    const int chunk = unit - plan->unit_begin[jj];
+    const int seg_s = plan->seg_start[jj], seg_c = plan->seg_cnt[jj];
+    const int cr = plan->chunk_rows[jj];
+    const int p0 = seg_s + (chunk * cs + rank) * cr;
+    const int p1 = min(seg_s + seg_c, p0 + cr);
+    const int nblk = p1 > p0 ? (p1 - p0 + LH_ROWS - 1) / LH_ROWS : 0;
+    const int rounds = (nblk + W - 1) / W;   // blocks per warp; block b = j W + w is warp w's j-th
+    if (warp < W) {   // ---- compute warp
+      float2* my = hist_all + static_cast<int64_t>(warp) * per_warp;
+      const uint32_t hbase = static_cast<uint32_t>(__cvta_generic_to_shared(my + lane));
+      {
+        float4* z = reinterpret_cast<float4*>(my);
+        for (int i = lane; i < per_warp / 2; i += 32) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncwarp();
+      const bool act = lane < F - grp * GROUP;   // lanes of padding features do no updates
+      for (int j = 0; j < rounds; ++j) {
+        const uint32_t k = U + static_cast<uint32_t>(j);
+        const int slot = warp * LD_STAGES + static_cast<int>(k % LD_STAGES);
+        const bool ok = ld_wait(full_s + slot * 8u, (k / LD_STAGES) & 1u, &s_abort, status, wait_limit);
+        if (ok && act && j * W + warp < nblk) {
+          const unsigned char* sb = recs + slot * (LH_ROWS * GROUP) + lane;
+          const float4* gh4 = reinterpret_cast<const float4*>(ghs + slot * LH_ROWS);
+          uint32_t a[1][LH_ROWS];
+#pragma unroll
+          for (int i = 0; i < LH_ROWS; ++i)
+            a[0][i] = hbase + static_cast<uint32_t>(min(static_cast<int>(sb[i * GROUP]), maxb1)) * (GROUP * 8u);
+          const bool on[1] = {true};
+          lane_batched_updates<LH_ROWS, 1>(a, gh4, 0, on);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty_s + slot * 8u);
+      }
+    } else {   // ---- loader warp W + w, for compute warp w
+      const int w = warp - W;
+      const uint8_t* gb = bins + static_cast<int64_t>(grp) * n * GROUP;
+      // row ids and (g, h) of the next LD_AHEAD blocks load while the current LD_AHEAD
+      // blocks are handed out; the registers are moved only once per batch, after the
+      // loads have had a whole batch of hand-overs to arrive
+      uint32_t rc[LD_AHEAD], rn[LD_AHEAD];
+      float gc[LD_AHEAD], hc[LD_AHEAD], gn[LD_AHEAD], hn[LD_AHEAD];
+      auto fetch = [&](int j, uint32_t& row, float& gv, float& hv) {   // warp w's j-th block
+        const int b = j * W + w;
+        const int pos = p0 + b * LH_ROWS + lane;
+        if (b < nblk && pos < p1) {
+          row = order ? __ldg(order + pos) : static_cast<uint32_t>(pos);
+          gv = cbgd::load_gh(gpos, pos);
+          hv = cbgd::load_gh(hpos, pos);
+        } else {
+          row = NONE;   // a row past the end: (g, h) = 0, and its record is not copied
+          gv = 0.f;
+          hv = 0.f;
+        }
+      };
+#pragma unroll
+      for (int q = 0; q < LD_AHEAD; ++q) fetch(q, rc[q], gc[q], hc[q]);
+      for (int j0 = 0; j0 < rounds; j0 += LD_AHEAD) {
+#pragma unroll
+        for (int q = 0; q < LD_AHEAD; ++q) fetch(j0 + LD_AHEAD + q, rn[q], gn[q], hn[q]);
+        // one poll of the `empty` barrier of each of the batch's first LD_STAGES blocks, a
+        // lane each (a later block's buffer is last filled within this batch, and its poll
+        // could see the phase before last, which has the same parity: it is left to the
+        // wait below)
+        bool free_l = false;
+        if (lane < LD_AHEAD && lane < LD_STAGES && j0 + lane < rounds) {
+          const uint32_t k = U + static_cast<uint32_t>(j0 + lane);
+          free_l = mbar_test(empty_s + (w * LD_STAGES + static_cast<int>(k % LD_STAGES)) * 8u,
+                             ((k / LD_STAGES) & 1u) ^ 1u);
+        }
+        const uint32_t free_mask = __ballot_sync(FULL_MASK, free_l);
+#pragma unroll
+        for (int q = 0; q < LD_AHEAD; ++q) {
+          if (j0 + q < rounds) {
+            const uint32_t k = U + static_cast<uint32_t>(j0 + q);
+            const int slot = w * LD_STAGES + static_cast<int>(k % LD_STAGES);
+            // a fresh mbarrier counts as having completed the phase before its first, so
+            // the first LD_STAGES blocks find their buffers free
+            const bool ok = ((free_mask >> q) & 1u) ||
+                            ld_wait(empty_s + slot * 8u, ((k / LD_STAGES) & 1u) ^ 1u, &s_abort, status, wait_limit);
+            if (ok) {
+              // rows past the end keep whatever record the buffer held: with (g, h) = 0
+              // their clamped bins add zero to some cell
+              if (rc[q] != NONE) {
+                const uint32_t dst = recs_s + static_cast<uint32_t>((slot * LH_ROWS + lane) * GROUP);
+                const uint8_t* src = gb + static_cast<int64_t>(rc[q]) * GROUP;
+                cp_async16(dst, src);
+                cp_async16(dst + 16, src + 16);
+              }
+              ghs[slot * LH_ROWS + lane] = make_float2(gc[q], hc[q]);
+              if (!test_stall) {
+                mbar_arrive_after_copies(full_s + slot * 8u);
+                mbar_arrive(full_s + slot * 8u);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < LD_AHEAD; ++q) {
+          rc[q] = rn[q];
+          gc[q] = gn[q];
+          hc[q] = hn[q];
+        }
+      }
+      cp_async_wait<0>();
+    }
+    U += static_cast<uint32_t>(rounds);
+    __syncthreads();
+    // the CTA's warps, summed in warp order into warp 0's histogram
+    if (W > 1) {
+      for (int e = threadIdx.x; e < per_warp; e += blockDim.x) {
+        float2 s = hist_all[e];
+        for (int v = 1; v < W; ++v) {
+          const float2 x = hist_all[static_cast<int64_t>(v) * per_warp + e];
+          s.x += x.x;
+          s.y += x.y;
         }
         hist_all[e] = s;
       }
@@ -1597,17 +1884,38 @@ cbg_status wp_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   return CBG_OK;
 }
 
+// Warps, threads and shared memory of the lane-per-feature kernels (V as for lane_geom):
+// `warps` counts the warps that hold histograms; the loader form adds its loader warp.
+inline int lane_warps(const HistConfig& L, int V) {
+  return V == 1   ? lp_warps(L.max_bins, L.threads)
+         : V == 2 ? l4_warps(L.max_bins, L.threads)
+         : V == 3 ? ld_warps(L.max_bins, L.threads)
+                  : lh_warps(L.max_bins, L.threads);
+}
+inline int lane_threads_warps(int V, int warps) { return V == 3 ? 2 * warps : warps; }
+inline size_t lane_smem(const HistConfig& L, int V, int warps) {
+  return V == 1   ? lp_smem_bytes(L.max_bins, warps)
+         : V == 2 ? l4_smem_bytes(L.max_bins, warps)
+         : V == 3 ? ld_smem_bytes(L.max_bins, warps)
+                  : lh_smem_bytes(L.max_bins, warps);
+}
+template <typename GH>
+const void* lane_kernel_fn(int V) {
+  return V == 1   ? reinterpret_cast<const void*>(level_hist_pair_kernel<GH>)
+         : V == 2 ? reinterpret_cast<const void*>(level_hist_lane4_kernel<GH>)
+         : V == 3 ? reinterpret_cast<const void*>(level_hist_lane_ld_kernel<GH>)
+                  : reinterpret_cast<const void*>(level_hist_lane_kernel<GH>);
+}
+
 // Geometry of the lane-per-feature kernels (V: 0 one warp per 32 features, 1 one statistic
-// per warp, 2 the 4-bit packed records): one CTA per SM
+// per warp, 2 the 4-bit packed records, 3 with a loader warp): one CTA per SM
 // with as many warp histograms as fit, and the cluster size (<= the requested one) that
 // keeps the most CTAs resident.
 template <typename GH, int V>
 cbg_status lane_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   static std::mutex mu;
   static std::map<std::tuple<int, int, int, int, int>, HistGeom> cache;
-  const int warps = V == 1 ? lp_warps(L.max_bins, L.threads)
-                  : V == 2 ? l4_warps(L.max_bins, L.threads)
-                           : lh_warps(L.max_bins, L.threads);
+  const int warps = lane_warps(L, V);
   const auto key = std::make_tuple(ctx->device, L.max_bins, warps, L.cluster, static_cast<int>(sizeof(GH)));
   {
     std::lock_guard<std::mutex> lk(mu);
@@ -1617,17 +1925,15 @@ cbg_status lane_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
       return CBG_OK;
     }
   }
-  auto kern = V == 1 ? level_hist_pair_kernel<GH> : V == 2 ? level_hist_lane4_kernel<GH> : level_hist_lane_kernel<GH>;
-  const size_t smem = V == 1   ? lp_smem_bytes(L.max_bins, warps)
-                      : V == 2 ? l4_smem_bytes(L.max_bins, warps)
-                               : lh_smem_bytes(L.max_bins, warps);
+  const void* kern = lane_kernel_fn<GH>(V);
+  const size_t smem = lane_smem(L, V, warps);
   CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN_BUDGET));
   HistGeom geom;
   for (int cs = L.cluster; cs >= 1; cs >>= 1) {
     if (cs > 8) CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(cs * ctx->num_sms));
-    cfg.blockDim = dim3(static_cast<unsigned>(32 * warps));
+    cfg.blockDim = dim3(static_cast<unsigned>(32 * lane_threads_warps(V, warps)));
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1662,6 +1968,7 @@ cbg_status hist_cluster_geom(cbg_ctx* ctx, const HistConfig& L, int* cs, int* cl
                   : L.kind == 4 ? lane_geom<float, 0>(ctx, L, &g)
                   : L.kind == 5 ? lane_geom<float, 1>(ctx, L, &g)
                   : L.kind == 6 ? lane_geom<float, 2>(ctx, L, &g)
+                  : L.kind == 8 ? lane_geom<float, 3>(ctx, L, &g)
                                 : hist_geom<float>(ctx, L, &g);
   if (st != CBG_OK) return st;
   *cs = g.cs;
@@ -1686,6 +1993,7 @@ cbg_status hist_warm(cbg_ctx* ctx, const HistConfig& L) {
                   : L.kind == 4 ? lane_geom<GH, 0>(ctx, L, &g)
                   : L.kind == 5 ? lane_geom<GH, 1>(ctx, L, &g)
                   : L.kind == 6 ? lane_geom<GH, 2>(ctx, L, &g)
+                  : L.kind == 8 ? lane_geom<GH, 3>(ctx, L, &g)
                                 : hist_geom<GH>(ctx, L, &g);
   if (st != CBG_OK) return st;
   int cs = 1;
@@ -1870,6 +2178,29 @@ cbg_status launch_hist(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins, c
                                      : packed ? level_hist_lane4_kernel<GH>
                                               : level_hist_lane_kernel<GH>,
                                      bins, L.n, L.G, L.F, order, gg, hh, plan, L.max_bins, partials));
+    return CBG_OK;
+  }
+  if (L.kind == 8) {
+    HistGeom geom;
+    st = lane_geom<GH, 3>(ctx, L, &geom);
+    if (st != CBG_OK) return st;
+    if (geom.cs != cs) return ::cbg::fail(ctx, CBG_ECUDA, "histogram cluster size changed between plan and launch");
+    const int warps = ld_warps(L.max_bins, L.threads);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(geom.cs * geom.clusters));
+    cfg.blockDim = dim3(static_cast<unsigned>(32 * lane_threads_warps(3, warps)));
+    cfg.dynamicSmemBytes = ld_smem_bytes(L.max_bins, warps);
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(geom.cs);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_lane_ld_kernel<GH>, bins, L.n, L.G, L.F, order, gg, hh, plan,
+                                     L.max_bins, partials, ctx->d_status, ctx->test_force_wait_timeout ? 1 : 0,
+                                     ctx->test_force_wait_timeout ? 4096u : LD_WAIT_LIMIT));
     return CBG_OK;
   }
   if (L.kind == 7) {

@@ -83,13 +83,13 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
   L->nb_alloc = pow2_at_least(L->max_bins);
   L->D = s->max_depth;
   CBG_REQUIRE(ctx, t.cluster >= 0 && t.cluster <= 16, "cluster must be in [0, 16]");
-  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 7, "kernel must be 0 (default), 1 (shared reductions), 2 "
+  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 8, "kernel must be 0 (default), 1 (shared reductions), 2 "
               "(warp-private, 16 features per warp), 3 (64-bit compare-and-swap), 4 (lane per feature), 5 (lane "
-              "per feature, one statistic per warp), 6 (lane per feature over 4-bit packed bins) or 7 (shared "
-              "integer reductions of fixed-point values)");
+              "per feature, one statistic per warp), 6 (lane per feature over 4-bit packed bins), 7 (shared "
+              "integer reductions of fixed-point values) or 8 (lane per feature with a loader warp)");
   CBG_REQUIRE(ctx, t.kernel != 6 || s->max_bins <= 16, "the 4-bit packed kernel needs max_bins <= 16");
   L->kind = t.kernel == 2 ? 0 : (t.kernel >= 3 ? t.kernel : 1);
-  const bool lane_kind = L->kind == 4 || L->kind == 5 || L->kind == 6;
+  const bool lane_kind = L->kind == 4 || L->kind == 5 || L->kind == 6 || L->kind == 8;
   const bool fixed_kind = L->kind == 7;
   L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : (lane_kind ? 8192 : fixed_kind ? 4096 : 2048);
   L->cluster = t.cluster > 0 ? t.cluster : (lane_kind ? 2 : fixed_kind ? 4 : 8);
@@ -1129,7 +1129,7 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   const int d = a->depth;
   CBG_REQUIRE(ctx, d >= 0 && d < L.D, "depth %d outside [0, max_depth)", d);
   CBG_REQUIRE(ctx, a->bins && a->n_borders && a->g && a->h && a->leaf && a->splits && a->child_totals, "NULL argument");
-  CBG_REQUIRE(ctx, (L.kind != 4 && L.kind != 5) || (reinterpret_cast<uintptr_t>(a->bins) & 15) == 0,
+  CBG_REQUIRE(ctx, (L.kind != 4 && L.kind != 5 && L.kind != 8) || (reinterpret_cast<uintptr_t>(a->bins) & 15) == 0,
               "bins must be 16-byte aligned for the lane-per-feature histogram kernel");
   CBG_REQUIRE(ctx, L.kind != 6 || (a->bins4 != nullptr && (reinterpret_cast<uintptr_t>(a->bins4) & 15) == 0),
               "the 4-bit packed histogram kernel needs bins4 (16-byte aligned, cbg_pack_bins4)");
@@ -1167,7 +1167,7 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   // caller's arrays at the root (positions are rows), then the copies the previous level's
   // partition moved along (for the FP32 shared-reduction kernel, which is bound by its
   // compare-and-swap loops, the copy costs the partition more than it saves)
-  const bool by_pos = L.kind == 4 || L.kind == 5 || L.kind == 6 || L.kind == 7;
+  const bool by_pos = L.kind == 4 || L.kind == 5 || L.kind == 6 || L.kind == 7 || L.kind == 8;
   const uint8_t* hist_bins = L.kind == 6 ? a->bins4 : a->bins;
   const void* g_pos = d == 0 ? a->g : at<char>(S, d % 2 == 1 ? L.o_gp_a : L.o_gp_b);
   const void* h_pos = d == 0 ? a->h : at<char>(S, d % 2 == 1 ? L.o_hp_a : L.o_hp_b);
@@ -1745,8 +1745,8 @@ namespace {
 
 // The tilings the autotuner times: the shared-reduction kernel with clusters of 1, 2, 4
 // or 8 and 2048 or 4096 rows per CTA of a unit; on request its fixed-point form with
-// clusters of 4 or 8 and 4096 or 8192 rows; the lane-per-feature kernel with clusters of 2
-// and 8192 or 16384 rows; its one-statistic-per-warp form with clusters of 2 or 4 and
+// clusters of 4 or 8 and 4096 or 8192 rows; the lane-per-feature kernel and its loader-warp
+// form with clusters of 2 and 8192 or 16384 rows; its one-statistic-per-warp form with clusters of 2 or 4 and
 // 8192 or 16384 rows; the 16-feature warp-private kernel once; with 4-bit packed bins
 // (at most 16 bins), the packed lane-per-feature kernel with clusters of 2 and 8192 or
 // 16384 rows.
@@ -1765,6 +1765,7 @@ std::vector<cbg_tiles> autotune_candidates(bool packed, bool fixed_point) {
     for (int cl : {4, 8})
       for (int r : {4096, 8192}) add(7, cl, r);
   for (int r : {8192, 16384}) add(4, 2, r);
+  for (int r : {8192, 16384}) add(8, 2, r);
   for (int cl : {2, 4})
     for (int r : {8192, 16384}) add(5, cl, r);
   add(2, 2, 8192);

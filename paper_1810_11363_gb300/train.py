@@ -325,6 +325,7 @@ def autotune(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, l2: flo
 # lane-per-feature kernels per problem.
 BATCH_CANDIDATES = ([{"kernel": 1, "cluster": c, "rows_per_item": 2048} for c in (1, 2, 8)] +
                     [{"kernel": 4, "cluster": 2, "rows_per_item": r} for r in (8192, 16384)] +
+                    [{"kernel": 8, "cluster": 2, "rows_per_item": r} for r in (8192, 16384)] +
                     [{"kernel": 5, "cluster": 2, "rows_per_item": 8192}])
 
 

@@ -340,7 +340,7 @@ def test_autotuned_tiles_train_like_the_oracle(ctx):
                             seed=w.seed)
     y = to_dev(w.y)
     tiles, ms = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2)
-    assert tiles["kernel"] in (1, 2, 4, 5) and tiles["cluster"] >= 1 and tiles["rows_per_item"] >= 2048
+    assert tiles["kernel"] in (1, 2, 4, 5, 8) and tiles["cluster"] >= 1 and tiles["rows_per_item"] >= 2048
     assert ms > 0
     model = train.fit(ctx, prep, y, w.loss, w.depth, w.trees, w.lr, w.l2, tiles=tiles, use_graph=True)
     cbg.cbg_sync(ctx)
@@ -370,12 +370,12 @@ def test_autotuned_tiles_train_like_the_oracle(ctx):
 
 @pytest.mark.parametrize("case", [LEVEL_CASES[0], LEVEL_CASES[3], LEVEL_CASES[5]])
 @pytest.mark.parametrize("cluster", [1, 4])
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 7])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 7, 8])
 def test_histogram_kernel_variants_match_oracle(ctx, case, cluster, kernel):
     """Every histogram kernel -- shared-memory reductions (tiles.kernel = 1), warp-private
     with 16 features per warp (2), 64-bit compare-and-swap on interleaved (G, H) (3), lane
-    per feature with store forwarding (4), the same with one statistic per warp (5) and
-    the opt-in fixed-point shared reductions (7) -- with and without thread-block
+    per feature with batched updates (4), the same with one statistic per warp (5) or
+    with a loader warp (8), and the opt-in fixed-point shared reductions (7) -- with and without thread-block
     clusters, on forced levels against the oracle. The FP32 kernels meet the 1e-5 bound;
     the fixed-point kernel is exact on integer gradients and otherwise adds at most its
     per-row rounding bound for each of the root's rows of the bin."""
@@ -469,6 +469,67 @@ def test_packed_histogram_kernel_matches_oracle(ctx, case, cluster):
         assert np.array_equal(gl, leaf), d
 
 
+@pytest.mark.parametrize("case", [LEVEL_CASES[1], LEVEL_CASES[3], LEVEL_CASES[4], LEVEL_CASES[6]])
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_loader_warp_kernel_equals_lane_kernel(ctx, case, cluster):
+    """The loader-warp kernel (tiles.kernel = 8) with W compute warps hands block b of a
+    work item to warp b % W, as the lane kernel (4) with W warps does, and updates each
+    warp's table with the same routine: with 3 compute warps (and their 3 loaders) against
+    3 lane warps the histograms, splits and child totals agree bit for bit on every level."""
+    n, F, F_pad, max_bins, depth, intg, dtype, bt = case
+    bins, nb, g, h, forced = synth.random_level_case(n + F + 13, n, F, F_pad, max_bins, depth, integer_grads=intg)
+    if dtype == "bf16":
+        g, h = _bf16(g), _bf16(h)
+    tiles = {"kernel": 8, "cluster": cluster, "rows_per_item": 8192, "threads": 192}
+    t = Tree(ctx, bins, nb, g, h, depth, dtype, tiles=tiles, with_bins_t=bt)
+    u = Tree(ctx, bins, nb, g, h, depth, dtype, tiles=dict(tiles, kernel=4, threads=96), with_bins_t=bt)
+    for d in range(depth):
+        hist, sf, sk, _, gl, child = t.level(d, 3.0, force=forced[d], last=(d == depth - 1))
+        hist_u, sf_u, sk_u, _, gl_u, child_u = u.level(d, 3.0, force=forced[d], last=(d == depth - 1))
+        assert np.array_equal(hist, hist_u), d
+        assert np.array_equal(child, child_u), d
+        assert (sf, sk) == (sf_u, sk_u) and np.array_equal(gl, gl_u), d
+
+
+def test_loader_warp_kernel_trains_like_the_oracle(ctx):
+    """Whole boosting runs with tiles.kernel = 8 (captured graph) on logloss_1m-shaped data
+    at 60k rows, in lock step with the oracle."""
+    w = synth.logloss_1m(n=60000, trees=12)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    model = train.fit(ctx, prep, to_dev(w.y), w.loss, w.depth, w.trees, w.lr, w.l2,
+                      tiles={"kernel": 8, "cluster": 2, "rows_per_item": 8192}, use_graph=True)
+    cbg.cbg_sync(ctx)
+    ref_prep = oracle.preprocess(w, prep.F_pad)
+    sp = model.host_splits()
+    res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, w.depth, w.trees, w.lr,
+                     w.l2, follow=sp)
+    lockstep_check(res, sp, to_host(model.pred), to_host(model.leaf_values), where="loader-warp kernel")
+
+
+def test_loader_warp_wait_runs_out_and_the_context_recovers(ctx):
+    """With the test hook on, the loader warps hand over no buffer: every compute warp's
+    bounded wait runs out, the launch ends, cbg_sync reports CBG_ETIMEOUT, and the same
+    level built again with the hook off matches the lane kernel bit for bit."""
+    n, F, F_pad, max_bins, depth, intg, dtype, bt = LEVEL_CASES[1]
+    bins, nb, g, h, forced = synth.random_level_case(n + F + 17, n, F, F_pad, max_bins, depth, integer_grads=intg)
+    tiles = {"kernel": 8, "cluster": 2, "rows_per_item": 8192, "threads": 192}
+    t = Tree(ctx, bins, nb, g, h, depth, dtype, tiles=tiles, with_bins_t=bt)
+    cbg.cbg_test_force_wait_timeout(ctx, True)
+    try:
+        with pytest.raises(cbg.CbgError) as e:
+            t.level(0, 3.0, force=forced[0])
+        assert e.value.status == cbg.CBG_ETIMEOUT
+    finally:
+        cbg.cbg_test_force_wait_timeout(ctx, False)
+    cbg.cbg_sync(ctx)
+    t = Tree(ctx, bins, nb, g, h, depth, dtype, tiles=tiles, with_bins_t=bt)
+    u = Tree(ctx, bins, nb, g, h, depth, dtype, tiles=dict(tiles, kernel=4, threads=96), with_bins_t=bt)
+    hist, *_ = t.level(0, 3.0, force=forced[0])
+    hist_u, *_ = u.level(0, 3.0, force=forced[0])
+    assert np.array_equal(hist, hist_u)
+
+
 def test_packed_kernel_trains_like_the_oracle(ctx):
     """Whole boosting runs with tiles.kernel = 6 on a 15-border workload, against the oracle."""
     import dataclasses
@@ -486,7 +547,7 @@ def test_packed_kernel_trains_like_the_oracle(ctx):
                      follow=sp)
     lockstep_check(res, sp, to_host(model.pred), to_host(model.leaf_values), where="packed")
     tiles, ms = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2)
-    assert tiles["kernel"] in (1, 2, 4, 5, 6) and ms > 0
+    assert tiles["kernel"] in (1, 2, 4, 5, 6, 8) and ms > 0
 
 
 def test_fixed_point_form_trains_like_the_oracle(ctx):
@@ -512,7 +573,7 @@ def test_fixed_point_form_trains_like_the_oracle(ctx):
     t_plain, _ = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2)
     assert t_plain["kernel"] != 7
     t_fixed, ms = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2, fixed_point=True)
-    assert t_fixed["kernel"] in (1, 2, 4, 5, 7) and ms > 0
+    assert t_fixed["kernel"] in (1, 2, 4, 5, 7, 8) and ms > 0
 
 
 def test_pack_bins4_flags_bins_of_16_and_more(ctx):
