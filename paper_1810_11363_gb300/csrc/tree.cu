@@ -27,6 +27,7 @@ namespace {
 
 constexpr int PT = 2048;           // positions per partition tile (256 threads x 8)
 constexpr int PT_THREADS = 256;
+constexpr int PT_PER_THREAD = PT / PT_THREADS;   // consecutive positions of a thread
 
 
 struct Segs {                       // row segments of the leaves of one level
@@ -677,6 +678,23 @@ __device__ __forceinline__ int seg_find(const int* seg_pos, int L, int64_t pos) 
   return lo;
 }
 
+// Row ids of positions base .. base + PT_PER_THREAD - 1 (identity without an order; rows
+// past n read as 0 and are not used), in two 16-byte loads where they are whole.
+__device__ __forceinline__ void load_rows(const uint32_t* __restrict__ order, int64_t n, int64_t base,
+                                          uint32_t (&rows)[PT_PER_THREAD]) {
+  static_assert(PT_PER_THREAD == 8, "two 16-byte loads per thread");
+  if (order && base + PT_PER_THREAD <= n) {   // order buffers are 256-byte aligned, base a multiple of 8
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(order + base));
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(order + base) + 1);
+    rows[0] = a.x; rows[1] = a.y; rows[2] = a.z; rows[3] = a.w;
+    rows[4] = b.x; rows[5] = b.y; rows[6] = b.z; rows[7] = b.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < PT_PER_THREAD; ++i)
+      rows[i] = base + i >= n ? 0u : order ? __ldg(order + base + i) : static_cast<uint32_t>(base + i);
+  }
+}
+
 // A: the FP64 child totals of the level's split (one warp per leaf); per position (8
 // consecutive positions per thread), the split bit of its row; leaf += 2^d * bit. Unless this is the last level: ones per tile and per leaf (run-length counted
 // in shared memory, since positions are grouped by leaf), and the last block to finish
@@ -711,21 +729,29 @@ __device__ __forceinline__ void part_flags_body(const uint8_t* __restrict__ bins
     else
       child_totals_warp(hist, l, L, F, max_bins, f, k, child_totals);
   }
-  const int64_t base = static_cast<int64_t>(bid) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
+  const int64_t base = static_cast<int64_t>(bid) * PT + static_cast<int64_t>(threadIdx.x) * PT_PER_THREAD;
   int si = seg_find(sh_pos, L, base);
   uint32_t cnt = 0, run = 0;
   int cur = -1;
+  // all row ids of the thread's positions, then all their split bits, so that the loads
+  // of each kind are in flight together
+  uint32_t rows[PT_PER_THREAD];
+  load_rows(order, n, base, rows);
+  int bits[PT_PER_THREAD];
 #pragma unroll
-  for (int i = 0; i < PT / PT_THREADS; ++i) {
+  for (int i = 0; i < PT_PER_THREAD; ++i)
+    bits[i] = base + i >= n ? 0 : chal ? (chal_bins[rows[i]] > k ? 1 : 0) : split_bit(bins, bins_t, n, rows[i], f, k);
+  uint32_t fw[PT_PER_THREAD / 4] = {};
+#pragma unroll
+  for (int i = 0; i < PT_PER_THREAD; ++i) {
     const int64_t pos = base + i;
     if (pos < n) {
-      const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
-      const int bit = chal ? (chal_bins[row] > k ? 1 : 0) : split_bit(bins, bins_t, n, row, f, k);
+      const int bit = bits[i];
       while (si + 1 < L && sh_pos[si + 1] <= pos) ++si;
       const int lf = sh_leaf[si];
-      if (bit) leaf[row] = static_cast<uint16_t>(lf + L);   // rows of leaf lf already hold lf
+      if (bit) leaf[rows[i]] = static_cast<uint16_t>(lf + L);   // rows of leaf lf already hold lf
       if (write_flags) {
-        flags[pos] = static_cast<uint8_t>(bit);
+        fw[i / 4] |= static_cast<uint32_t>(bit) << (8 * (i % 4));
         if (lf != cur) {
           if (run) atomicAdd(&sh_ones[cur], run);
           cur = lf;
@@ -734,6 +760,15 @@ __device__ __forceinline__ void part_flags_body(const uint8_t* __restrict__ bins
         run += bit;
         cnt += bit;
       }
+    }
+  }
+  if (write_flags) {
+    if (base + PT_PER_THREAD <= n) {
+      *reinterpret_cast<uint2*>(flags + base) = make_uint2(fw[0], fw[1]);   // base is a multiple of 8
+    } else {
+#pragma unroll
+      for (int i = 0; i < PT_PER_THREAD; ++i)
+        if (base + i < n) flags[base + i] = static_cast<uint8_t>((fw[i / 4] >> (8 * (i % 4))) & 1u);
     }
   }
   if (!write_flags) return;
@@ -786,13 +821,47 @@ __device__ __forceinline__ void part_scatter_body(const uint32_t* __restrict__ o
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int L = 1 << depth;
   load_seg_table(cur, L, sh_pos, sh_leaf);
-  const int64_t base = static_cast<int64_t>(bid) * PT + static_cast<int64_t>(threadIdx.x) * (PT / PT_THREADS);
-  uint8_t fl[PT / PT_THREADS];
+  const int64_t base = static_cast<int64_t>(bid) * PT + static_cast<int64_t>(threadIdx.x) * PT_PER_THREAD;
+  const bool whole = base + PT_PER_THREAD <= n;
+  uint8_t fl[PT_PER_THREAD];
   uint32_t s = 0;
+  if (whole) {   // the flags buffer is 256-byte aligned and base a multiple of 8
+    const uint2 w = *reinterpret_cast<const uint2*>(flags + base);
 #pragma unroll
-  for (int i = 0; i < PT / PT_THREADS; ++i) {
-    fl[i] = (base + i < n) ? flags[base + i] : 0;
-    s += fl[i];
+    for (int i = 0; i < PT_PER_THREAD; ++i) fl[i] = static_cast<uint8_t>(((i < 4 ? w.x : w.y) >> (8 * (i % 4))) & 0xffu);
+  } else {
+#pragma unroll
+    for (int i = 0; i < PT_PER_THREAD; ++i) fl[i] = (base + i < n) ? flags[base + i] : 0;
+  }
+#pragma unroll
+  for (int i = 0; i < PT_PER_THREAD; ++i) s += fl[i];
+  // the row ids and (g, h) of the thread's positions, loaded together ahead of the stores
+  uint32_t rows[PT_PER_THREAD];
+  load_rows(order, n, base, rows);
+  uint32_t gv[PT_PER_THREAD], hv[PT_PER_THREAD];
+  if (gh_bytes == 4) {
+    const uint32_t* gi = static_cast<const uint32_t*>(g_in);
+    const uint32_t* hi = static_cast<const uint32_t*>(h_in);
+    if (whole && ((reinterpret_cast<uintptr_t>(gi + base) | reinterpret_cast<uintptr_t>(hi + base)) & 15) == 0) {
+      const uint4 g0 = *reinterpret_cast<const uint4*>(gi + base), g1 = *(reinterpret_cast<const uint4*>(gi + base) + 1);
+      const uint4 h0 = *reinterpret_cast<const uint4*>(hi + base), h1 = *(reinterpret_cast<const uint4*>(hi + base) + 1);
+      gv[0] = g0.x; gv[1] = g0.y; gv[2] = g0.z; gv[3] = g0.w; gv[4] = g1.x; gv[5] = g1.y; gv[6] = g1.z; gv[7] = g1.w;
+      hv[0] = h0.x; hv[1] = h0.y; hv[2] = h0.z; hv[3] = h0.w; hv[4] = h1.x; hv[5] = h1.y; hv[6] = h1.z; hv[7] = h1.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < PT_PER_THREAD; ++i) {
+        gv[i] = base + i < n ? gi[base + i] : 0u;
+        hv[i] = base + i < n ? hi[base + i] : 0u;
+      }
+    }
+  } else if (gh_bytes == 2) {
+    const uint16_t* gi = static_cast<const uint16_t*>(g_in);
+    const uint16_t* hi = static_cast<const uint16_t*>(h_in);
+#pragma unroll
+    for (int i = 0; i < PT_PER_THREAD; ++i) {
+      gv[i] = base + i < n ? gi[base + i] : 0u;
+      hv[i] = base + i < n ? hi[base + i] : 0u;
+    }
   }
   uint32_t x = s;
   for (int o = 1; o < 32; o <<= 1) {
@@ -813,10 +882,10 @@ __device__ __forceinline__ void part_scatter_body(const uint32_t* __restrict__ o
   uint32_t ones_before = tile_off[bid] + sh[warp] + x - s;
   int si = seg_find(sh_pos, L, base);
 #pragma unroll
-  for (int i = 0; i < PT / PT_THREADS; ++i) {
+  for (int i = 0; i < PT_PER_THREAD; ++i) {
     const int64_t pos = base + i;
     if (pos < n) {
-      const uint32_t row = order ? order[pos] : static_cast<uint32_t>(pos);
+      const uint32_t row = rows[i];
       while (si + 1 < L && sh_pos[si + 1] <= pos) ++si;
       const int l = sh_leaf[si];
       const int start = cur->start[l];
@@ -830,11 +899,11 @@ __device__ __forceinline__ void part_scatter_body(const uint32_t* __restrict__ o
       if (dst >= 0 && dst < n) {
         order_out[dst] = row;
         if (gh_bytes == 4) {
-          static_cast<uint32_t*>(g_out)[dst] = static_cast<const uint32_t*>(g_in)[pos];
-          static_cast<uint32_t*>(h_out)[dst] = static_cast<const uint32_t*>(h_in)[pos];
+          static_cast<uint32_t*>(g_out)[dst] = gv[i];
+          static_cast<uint32_t*>(h_out)[dst] = hv[i];
         } else if (gh_bytes == 2) {
-          static_cast<uint16_t*>(g_out)[dst] = static_cast<const uint16_t*>(g_in)[pos];
-          static_cast<uint16_t*>(h_out)[dst] = static_cast<const uint16_t*>(h_in)[pos];
+          static_cast<uint16_t*>(g_out)[dst] = static_cast<uint16_t>(gv[i]);
+          static_cast<uint16_t*>(h_out)[dst] = static_cast<uint16_t>(hv[i]);
         }
       }
     }
@@ -1166,7 +1235,8 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   // the lane-per-feature kernels and the fixed-point kernel read (g, h) by position: the
   // caller's arrays at the root (positions are rows), then the copies the previous level's
   // partition moved along (for the FP32 shared-reduction kernel, which is bound by its
-  // compare-and-swap loops, the copy costs the partition more than it saves)
+  // compare-and-swap loops, the copy costs the partition more than it saves; the loader-
+  // warp kernel, whose loaders could gather by row from L2, lost a third of its speed so)
   const bool by_pos = L.kind == 4 || L.kind == 5 || L.kind == 6 || L.kind == 7 || L.kind == 8;
   const uint8_t* hist_bins = L.kind == 6 ? a->bins4 : a->bins;
   const void* g_pos = d == 0 ? a->g : at<char>(S, d % 2 == 1 ? L.o_gp_a : L.o_gp_b);
