@@ -70,6 +70,8 @@ def parse_args():
     p.add_argument("--ordered-trees", type=int, default=200,
                    help="trees of the ordered-boosting comparison (0 skips it)")
     p.add_argument("--ordered-s", type=int, default=4, help="permutations of the ordered-boosting comparison")
+    p.add_argument("--binary-trees", type=int, default=200,
+                   help="trees of the binary-feature (1-bit kernel) comparison (0 skips it)")
     p.add_argument("--combo-trees", type=int, default=10,
                    help="trees of the feature-combination comparison (0 skips it)")
     p.add_argument("--combo-borders", type=int, default=15, help="borders of a combination's column")
@@ -527,6 +529,55 @@ def ordered_bench(ctx, dev, x, cat, y, w, trees, s, tiles):
     return out
 
 
+def binary_bench(ctx, dev, x, cat, y, w, trees):
+    """Binary features (Section 5, "Dense numerical features": 1 bit per binary feature,
+    32 to an integer): logloss_1m's columns quantised with one border each (every feature
+    has 2 bins), trained with the 1-bit histogram kernel (tiles.kernel 9) and with the
+    autotuner's pick among the uint8 kernels, both with graph replay: mean time per tree
+    after the one-off preprocessing, final training loss, and the histogram's average
+    launch (CUDA events around the histogram launches of 5 trees with host launches)."""
+    import dataclasses
+
+    import torch
+    from paper_1810_11363_gb300 import cbg, train
+    stream = torch.cuda.current_stream(dev)
+    prep = train.preprocess(ctx, x, cat, y, "binary", 1, a=w.a, seed=w.seed)
+    out = {"workload": f"logloss_1m columns with 1 border each (10^6 x 110, {prep.max_bins} bins), depth {w.depth}, "
+                       f"{trees} trees, lr {w.lr}, L2 {w.l2}", "trees": trees}
+    tiles_u8, _ = train.autotune(ctx, dataclasses.replace(prep, bins4=None, bits1=None), y, w.loss, w.depth, w.l2)
+    for name, tiles in (("bits1", {"kernel": 9, "cluster": 2, "rows_per_item": 8192}), ("uint8", tiles_u8)):
+        tiles = {k: tiles[k] for k in ("kernel", "cluster", "rows_per_item")}
+        bufs = train.alloc_fit(prep, w.depth, trees, tiles=tiles)
+
+        def run(T, graph=True):
+            bufs.pred.zero_()
+            return train.fit(ctx, prep, y, w.loss, w.depth, T, w.lr, w.l2, bufs=bufs, use_graph=graph)
+        run(min(trees, 5))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(trees)
+        e1.record(stream)
+        e1.synchronize()
+        cbg.cbg_sync(ctx)
+        ms = e0.elapsed_time(e1)
+        loss = training_loss(w.loss, y, bufs.pred)
+        cbg.cbg_profile_read(ctx, reset=True)
+        cbg.cbg_profile_enable(ctx, True)
+        run(5, graph=False)
+        cbg.cbg_profile_enable(ctx, False)
+        torch.cuda.synchronize()
+        hist_ms, launches = cbg.cbg_profile_read(ctx, reset=True)
+        out[name] = {"ms_per_tree": ms / trees, "trees_per_s": trees / (ms / 1e3), "final_loss": loss,
+                     "hist_tiles": tiles, "hist_avg_launch_us": hist_ms * 1e3 / max(launches, 1)}
+        del bufs
+    out["speed_bits1_over_uint8"] = out["uint8"]["ms_per_tree"] / out["bits1"]["ms_per_tree"]
+    out["rel_final_loss_diff"] = abs(out["bits1"]["final_loss"] - out["uint8"]["final_loss"]) / out["uint8"]["final_loss"]
+    del prep
+    torch.cuda.empty_cache()
+    return out
+
+
 def combos_bench(ctx, dev, x, cat, y, w, trees, max_borders, max_complexity, tiles):
     """Classic boosting with greedy feature combinations (Section 2) on logloss_1m against
     plain classic boosting on the same data: mean time per tree (host-driven levels, one
@@ -825,6 +876,9 @@ def run_ours(args):
     ordered = None
     if args.ordered_trees > 0 and rank == 0:
         ordered = ordered_bench(ctx, dev, x, cat, y, w, args.ordered_trees, args.ordered_s, tiles)
+    binary = None
+    if args.binary_trees > 0 and rank == 0:
+        binary = binary_bench(ctx, dev, x, cat, y, w, args.binary_trees)
     combos = None
     if args.combo_trees > 0 and rank == 0:
         combos = combos_bench(ctx, dev, x, cat, y, w, args.combo_trees, args.combo_borders, 4, tiles)
@@ -864,7 +918,7 @@ def run_ours(args):
                 "roofline": roofline, "roofline_smem": roofline_smem, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk,
                 "forms": forms, "batched_vs_plain": batched, "scorer": scorer, "paper_setting": paper_setting,
-                "ordered_boosting": ordered, "feature_combinations": combos,
+                "ordered_boosting": ordered, "binary_features": binary, "feature_combinations": combos,
                 "dense_400k": dense, "precision_10m": precision,
                 "breakdown": {"step_ms": step_ms}}
         print(json.dumps(line), flush=True)

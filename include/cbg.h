@@ -82,7 +82,9 @@ typedef struct cbg_split {
  * with shared-memory integer reductions (4096 rows per CTA and clusters of 4 by
  * default), 8 = kernel 4 with loader warps: each histogram warp has a partner
  * warp that stages its rows' bin records and (g, h), so that it only updates its
- * histogram (threads counts both; bins 16-byte aligned). The default (0) is kernel 1, whose shared-memory
+ * histogram (threads counts both; bins 16-byte aligned), 9 = binary features
+ * over the 1-bit packed bins of cbg_pack_bits1 (max_bins <= 2; the level
+ * arguments carry bits1; 512-thread CTAs whatever threads says). The default (0) is kernel 1, whose shared-memory
  * accumulation is FP32.
  * Kernel 7 is an opt-in form that does not accumulate in FP32: it rounds each (g, h) of a CTA's rows to a
  * multiple of 2^-e, e the largest exponent with 2^e * 1.001 * S < 2^30 for S the
@@ -243,6 +245,9 @@ typedef struct cbg_level_args {
   /* 4-bit packed bins of the same rows (cbg_pack_bins4), read by the histogram when
    * shape->tiles.kernel is 6; NULL otherwise. */
   const uint8_t* bins4;
+  /* 1-bit packed bins of the same rows (cbg_pack_bits1), read by the histogram when
+   * shape->tiles.kernel is 9; NULL otherwise. */
+  const uint32_t* bits1;
 } cbg_level_args;
 
 /* One level d (Sections 3-4): FP64 histograms hist[l][f][b] = sum of (g, h)
@@ -317,6 +322,7 @@ typedef struct cbg_boost_args {
   double* child_totals;   /* device [2^depth][2] scratch */
   int32_t use_graph;
   const uint8_t* bins4;        /* device 4-bit packed bins or NULL (tiles kernel 6 needs them) */
+  const uint32_t* bits1;       /* device 1-bit packed bins or NULL (tiles kernel 9 needs them) */
 } cbg_boost_args;
 cbg_status cbg_boost(cbg_ctx* ctx, const cbg_boost_args* args);
 
@@ -473,8 +479,8 @@ cbg_status cbg_predict(cbg_ctx* ctx, const cbg_predict_args* args);
  *    histograms (4), their loader-warp form (8) and their one-statistic-per-warp
  *    form (5), 16-feature
  *    warp-private histograms (2), with bins4 and max_bins <= 16 the packed
- *    lane-per-feature kernel (6), and with fixed_point != 0 the fixed-point
- *    shared-reduction kernel (7);
+ *    lane-per-feature kernel (6), with bits1 and max_bins <= 2 the 1-bit kernel
+ *    (9), and with fixed_point != 0 the fixed-point shared-reduction kernel (7);
  *  - CTAs per cluster;
  *  - rows per CTA of a work unit.
  * Ownership and layout follow cbg_build_level. args->shape->tiles is ignored.
@@ -502,6 +508,8 @@ typedef struct cbg_autotune_args {
   const uint8_t* bins4;        /* device 4-bit packed bins (cbg_pack_bins4) or NULL; with
                                   max_bins <= 16 the packed kernel is a candidate too */
   int32_t fixed_point;         /* nonzero: the fixed-point kernel (7) is a candidate too */
+  const uint32_t* bits1;       /* device 1-bit packed bins (cbg_pack_bits1) or NULL; with
+                                  max_bins <= 2 the 1-bit kernel (9) is a candidate too */
 } cbg_autotune_args;
 
 /* 4-bit packed bins (Section 5 "Dense numerical features": features with at most
@@ -512,6 +520,14 @@ typedef struct cbg_autotune_args {
  * CBG_EDATA. The packed records are half the bytes of the grouped layout; the
  * histogram kernel 6 (tiles.kernel) reads them. */
 cbg_status cbg_pack_bins4(cbg_ctx* ctx, const uint8_t* bins, int64_t n, int32_t F_pad, uint8_t* bins4);
+
+/* 1-bit packed bins (Section 5 "Dense numerical features": binary features take 1
+ * bit, 32 features to a 32-bit integer): bit i of bits1[q][r] is 1 when feature
+ * 32q + i of row r has bin 1 (device uint32 [F_pad/32][n], caller-owned, 16-byte
+ * aligned like bins). Every bin of bins must be 0 or 1; a larger one makes the
+ * next cbg_sync() return CBG_EDATA. A row's 32 features take 4 bytes instead of
+ * 32; the histogram kernel 9 (tiles.kernel) reads them. */
+cbg_status cbg_pack_bits1(cbg_ctx* ctx, const uint8_t* bins, int64_t n, int32_t F_pad, uint32_t* bits1);
 
 /* Tree-state bytes large enough for every autotuner candidate of `shape`. */
 cbg_status cbg_autotune_state_bytes(const cbg_tree_shape* shape, size_t* bytes);

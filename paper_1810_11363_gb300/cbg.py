@@ -48,7 +48,8 @@ class AutotuneArgs(C.Structure):
     _fields_ = [("shape", C.POINTER(TreeShape)), ("state", c_vp), ("state_bytes", C.c_size_t),
                 ("bins", c_vp), ("bins_t", c_vp), ("n_borders", c_vp), ("g", c_vp), ("h", c_vp),
                 ("gh_dtype", c_i32), ("depth", c_i32), ("l2", c_f64), ("leaf", c_vp), ("splits", c_vp),
-                ("child_totals", c_vp), ("reps", c_i32), ("bins4", c_vp), ("fixed_point", c_i32)]
+                ("child_totals", c_vp), ("reps", c_i32), ("bins4", c_vp), ("fixed_point", c_i32),
+                ("bits1", c_vp)]
 
 
 class PredictArgs(C.Structure):
@@ -62,7 +63,8 @@ class LevelArgs(C.Structure):
                 ("gh_dtype", c_i32), ("depth", c_i32), ("l2", c_f64), ("force_feature", c_i32),
                 ("force_border", c_i32), ("leaf", c_vp), ("splits", c_vp), ("child_totals", c_vp),
                 ("hist_out", c_vp), ("last_level", c_i32), ("challenger", c_vp), ("challenger_bins", c_vp),
-                ("challenger_hist", c_vp), ("challenger_max_bins", c_i32), ("bins4", c_vp)]
+                ("challenger_hist", c_vp), ("challenger_max_bins", c_i32), ("bins4", c_vp),
+                ("bits1", c_vp)]
 
 
 class ApplyArgs(C.Structure):
@@ -77,7 +79,8 @@ class BoostArgs(C.Structure):
                 ("bins", c_vp), ("bins_t", c_vp), ("n_borders", c_vp), ("y", c_vp), ("loss", c_i32),
                 ("gh_dtype", c_i32), ("depth", c_i32), ("trees", c_i32), ("lr", c_f64), ("l2", c_f64),
                 ("pred", c_vp), ("g", c_vp), ("h", c_vp), ("leaf", c_vp), ("splits", c_vp),
-                ("leaf_values", c_vp), ("child_totals", c_vp), ("use_graph", c_i32), ("bins4", c_vp)]
+                ("leaf_values", c_vp), ("child_totals", c_vp), ("use_graph", c_i32), ("bins4", c_vp),
+                ("bits1", c_vp)]
 
 
 class Problem(C.Structure):
@@ -149,6 +152,7 @@ SIGNATURES = {
     "cbg_combo_work_bytes": (c_i32, [c_i64, c_i32, c_i32, c_i32, c_i32, C.POINTER(C.c_size_t)]),
     "cbg_boost_combos": (c_i32, [c_vp, C.POINTER(ComboArgs)]),
     "cbg_pack_bins4": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp]),
+    "cbg_pack_bits1": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp]),
     "cbg_combo_ids": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_i64, c_vp]),
 }
 
@@ -287,12 +291,13 @@ def cbg_tree_begin(ctx: Context, shape: TreeShape, state, leaf):
 
 def cbg_build_level(ctx: Context, shape: TreeShape, state, bins, n_borders, g, h, gh_dtype: str, depth: int,
                     l2: float, leaf, splits, child_totals, bins_t=None, force=None, hist_out=None,
-                    last_level: bool = False, bins4=None):
+                    last_level: bool = False, bins4=None, bits1=None):
     ff, fk = force if force is not None else (-1, -1)
     a = LevelArgs(C.pointer(shape), _p(state), state.numel() * state.element_size(), _p(bins), _p(bins_t),
                   _p(n_borders), _p(g), _p(h), DTYPE[gh_dtype], depth, l2, ff, fk, _p(leaf), _p(splits),
                   _p(child_totals), _p(hist_out), int(last_level))
     a.bins4 = _p(bins4)
+    a.bits1 = _p(bits1)
     ctx.check(ctx.lib.cbg_build_level(ctx.h, C.byref(a)), "cbg_build_level")
 
 
@@ -308,10 +313,11 @@ def cbg_apply_tree(ctx: Context, n: int, depth: int, pred, *, bins=None, F_pad: 
 
 def cbg_boost(ctx: Context, shape: TreeShape, state, bins, n_borders, y, loss: str, gh_dtype: str, depth: int,
               trees: int, lr: float, l2: float, pred, g, h, leaf, splits, leaf_values, child_totals,
-              bins_t=None, use_graph: bool = False, bins4=None):
+              bins_t=None, use_graph: bool = False, bins4=None, bits1=None):
     a = BoostArgs(C.pointer(shape), _p(state), state.numel() * state.element_size(), _p(bins), _p(bins_t),
                   _p(n_borders), _p(y), LOSS[loss], DTYPE[gh_dtype], depth, trees, lr, l2, _p(pred), _p(g),
-                  _p(h), _p(leaf), _p(splits), _p(leaf_values), _p(child_totals), int(use_graph), _p(bins4))
+                  _p(h), _p(leaf), _p(splits), _p(leaf_values), _p(child_totals), int(use_graph), _p(bins4),
+                  _p(bits1))
     ctx.check(ctx.lib.cbg_boost(ctx.h, C.byref(a)), "cbg_boost")
 
 
@@ -359,12 +365,12 @@ def cbg_autotune_state_bytes(shape: TreeShape) -> int:
 
 def cbg_autotune_tiles(ctx: Context, shape: TreeShape, state, bins, n_borders, g, h, gh_dtype: str, depth: int,
                        l2: float, leaf, splits, child_totals, bins_t=None, reps: int = 2, bins4=None,
-                       fixed_point: bool = False):
+                       fixed_point: bool = False, bits1=None):
     """Fastest histogram tiling for this problem (dict of cbg_tiles fields) and its device
     time per tree in ms. fixed_point: the fixed-point kernel (7) is a candidate too."""
     a = AutotuneArgs(C.pointer(shape), _p(state), state.numel() * state.element_size(), _p(bins), _p(bins_t),
                      _p(n_borders), _p(g), _p(h), DTYPE[gh_dtype], depth, l2, _p(leaf), _p(splits),
-                     _p(child_totals), reps, _p(bins4), 1 if fixed_point else 0)
+                     _p(child_totals), reps, _p(bins4), 1 if fixed_point else 0, _p(bits1))
     best = Tiles()
     ms = c_f64()
     ctx.check(ctx.lib.cbg_autotune_tiles(ctx.h, C.byref(a), C.byref(best), C.byref(ms)), "cbg_autotune_tiles")
@@ -443,6 +449,10 @@ def cbg_boost_combos(ctx: Context, shape: TreeShape, state, bins, bins_t, n_bord
                      work.numel() * work.element_size(), combo_items.ctypes.data, combo_nb.ctypes.data,
                      combo_borders.ctypes.data)
     ctx.check(ctx.lib.cbg_boost_combos(ctx.h, C.byref(args)), "cbg_boost_combos")
+
+
+def cbg_pack_bits1(ctx: Context, bins, n: int, F_pad: int, bits1):
+    ctx.check(ctx.lib.cbg_pack_bits1(ctx.h, _p(bins), n, F_pad, _p(bits1)), "cbg_pack_bits1")
 
 
 def cbg_pack_bins4(ctx: Context, bins, n: int, F_pad: int, bins4):

@@ -40,7 +40,7 @@ namespace cbg {
 constexpr unsigned STATUS_NONFINITE = 1u;
 constexpr unsigned STATUS_BAD_LABEL = 2u;
 constexpr unsigned STATUS_TIMEOUT = 4u;
-constexpr unsigned STATUS_BAD_BIN = 8u;     // a bin that does not fit the 4-bit packed layout
+constexpr unsigned STATUS_BAD_BIN = 8u;     // a bin that does not fit a packed layout (4-bit or 1-bit)
 
 cbg_status fail(cbg_ctx* ctx, cbg_status code, const char* fmt, ...);
 
@@ -122,6 +122,16 @@ namespace cbgd {
 __device__ __forceinline__ float load_gh(const float* p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float load_gh(const __nv_bfloat16* p, int64_t i) {
   return __bfloat162float(p[i]);
+}
+// The stored bits of element i, and their value: a load whose value is needed only later
+// keeps the raw bits, so that no conversion right after the load waits for it.
+__device__ __forceinline__ uint32_t load_gh_bits(const float* p, int64_t i) { return __float_as_uint(__ldg(p + i)); }
+__device__ __forceinline__ uint32_t load_gh_bits(const __nv_bfloat16* p, int64_t i) {
+  return __ldg(reinterpret_cast<const unsigned short*>(p) + i);
+}
+template <typename GH>
+__device__ __forceinline__ float gh_from_bits(uint32_t b) {
+  return __uint_as_float(sizeof(GH) == 2 ? b << 16 : b);   // a BF16 is the high half of an FP32
 }
 __device__ __forceinline__ void store_gh(float* p, int64_t i, float v) { p[i] = v; }
 __device__ __forceinline__ void store_gh(__nv_bfloat16* p, int64_t i, float v) {

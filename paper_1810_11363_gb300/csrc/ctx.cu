@@ -173,7 +173,8 @@ cbg_status cbg_sync(cbg_ctx* ctx) {
     if (status & STATUS_TIMEOUT) return fail(ctx, CBG_ETIMEOUT, "a bounded device-side wait ran out");
     if (status & STATUS_NONFINITE) return fail(ctx, CBG_EDATA, "a feature value was NaN or infinite");
     if (status & STATUS_BAD_LABEL) return fail(ctx, CBG_EDATA, "a binary label was not 0 or 1");
-    if (status & STATUS_BAD_BIN) return fail(ctx, CBG_EDATA, "a bin of 16 or more cannot be packed in 4 bits");
+    if (status & STATUS_BAD_BIN)
+      return fail(ctx, CBG_EDATA, "a bin too large for its packed layout (16 or more in 4 bits, 2 or more in 1 bit)");
     return fail(ctx, CBG_EDATA, "device status 0x%x", status);
   }
   return CBG_OK;

@@ -1002,19 +1002,20 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
       // row ids and (g, h) of the next LD_AHEAD blocks load while the current LD_AHEAD
       // blocks are handed out; the registers are moved only once per batch, after the
       // loads have had a whole batch of hand-overs to arrive
+      // (g, h) stay raw bits until the hand-over converts them
       uint32_t rc[LD_AHEAD], rn[LD_AHEAD];
-      float gc[LD_AHEAD], hc[LD_AHEAD], gn[LD_AHEAD], hn[LD_AHEAD];
-      auto fetch = [&](int j, uint32_t& row, float& gv, float& hv) {   // warp w's j-th block
+      uint32_t gc[LD_AHEAD], hc[LD_AHEAD], gn[LD_AHEAD], hn[LD_AHEAD];
+      auto fetch = [&](int j, uint32_t& row, uint32_t& gv, uint32_t& hv) {   // warp w's j-th block
         const int b = j * W + w;
         const int pos = p0 + b * LH_ROWS + lane;
         if (b < nblk && pos < p1) {
           row = order ? __ldg(order + pos) : static_cast<uint32_t>(pos);
-          gv = cbgd::load_gh(gpos, pos);
-          hv = cbgd::load_gh(hpos, pos);
+          gv = cbgd::load_gh_bits(gpos, pos);
+          hv = cbgd::load_gh_bits(hpos, pos);
         } else {
           row = NONE;   // a row past the end: (g, h) = 0, and its record is not copied
-          gv = 0.f;
-          hv = 0.f;
+          gv = 0u;
+          hv = 0u;
         }
       };
 #pragma unroll
@@ -1051,7 +1052,7 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
                 cp_async16(dst, src);
                 cp_async16(dst + 16, src + 16);
               }
-              ghs[slot * LH_ROWS + lane] = make_float2(gc[q], hc[q]);
+              ghs[slot * LH_ROWS + lane] = make_float2(cbgd::gh_from_bits<GH>(gc[q]), cbgd::gh_from_bits<GH>(hc[q]));
               if (!test_stall) {
                 mbar_arrive_after_copies(full_s + slot * 8u);
                 mbar_arrive(full_s + slot * 8u);
@@ -1310,6 +1311,126 @@ __global__ void pack_bins4_kernel(const uint8_t* __restrict__ bins, int64_t n, i
                                                     lo.w | (hi.w << 4));
   }
   if (bad) atomicOr(status, ::cbg::STATUS_BAD_BIN);
+}
+
+// ------------------------------------------------------ 1-bit binary features
+// Section 5 ("Dense numerical features") packs binary features 32 to a 32-bit integer
+// and builds their histograms 32 features and 2 statistics at a time. Here bits1[q][r]
+// (uint32) holds bit i = [bin of feature 32q + i of row r is 1] (cbg_pack_bits1). A
+// feature of at most 2 bins has only two cells per leaf, so lane f of a warp keeps both
+// of feature f's (G, H) cells of the work item in registers: for every row of a staged
+// block of 32 it tests its bit of the row's word and adds the row's (g, h) to bin 1 or
+// bin 0. No shared-memory histogram and no atomics; the warps of a CTA, then the CTAs of
+// the cluster, are summed in order at the end of the item into the same [stat][bin][32]
+// FP32 partial as the other kernels (max_bins = 2), for the FP64 reduction.
+constexpr int LB_WARPS = 16;
+
+__global__ void pack_bits1_kernel(const uint8_t* __restrict__ bins, int64_t n, int G, uint32_t* __restrict__ bits1,
+                                  unsigned int* __restrict__ status) {
+  const int64_t total = static_cast<int64_t>(G) * n;
+  bool bad = false;
+  for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+       x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint4* rec = reinterpret_cast<const uint4*>(bins) + 2 * x;   // group q, row r: record x = q n + r
+    const uint4 a = rec[0], b = rec[1];
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t word = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      bad |= (w[k] & 0xfefefefeu) != 0u;
+      // bytes 0..3 of w[k] (each 0 or 1) are features 4k .. 4k + 3
+      const uint32_t nib = (w[k] & 1u) | ((w[k] >> 7) & 2u) | ((w[k] >> 14) & 4u) | ((w[k] >> 21) & 8u);
+      word |= nib << (4 * k);
+    }
+    bits1[x] = word;
+  }
+  if (bad) atomicOr(status, ::cbg::STATUS_BAD_BIN);
+}
+
+template <typename GH>
+__global__ void __launch_bounds__(LB_WARPS * 32, 2)
+    level_hist_bits_kernel(const uint32_t* __restrict__ bits1, int64_t n, int G, int F,
+                           const uint32_t* __restrict__ order, const GH* __restrict__ gpos,
+                           const GH* __restrict__ hpos, const Plan* __restrict__ plan, float* __restrict__ partials) {
+  namespace cgr = cooperative_groups;
+  constexpr int CELLS = 2 * 2 * GROUP;   // [stat][bin][feature]
+  __shared__ float4 s_row[LB_WARPS][LH_ROWS];         // (word, g, h, -) of the rows of a warp's block
+  __shared__ float s_acc[LB_WARPS][CELLS];            // each warp's cells at the end of an item
+  __shared__ float s_cta[CELLS];                      // the CTA's cells, read by the cluster
+  __shared__ int s_next;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int cs = static_cast<int>(cl.num_blocks());
+  const int rank = static_cast<int>(cl.block_rank());
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int total_items = plan->total_units * G;
+  const int n_small = plan->n_small;
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
+  cl.sync();
+  for (int item = queue_read(&s_next); item < total_items; item = queue_read(&s_next)) {
+    const int unit = item / G, grp = item - unit * G;
+    int lo = 0, hi = n_small - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (plan->unit_begin[mid] <= unit) lo = mid; else hi = mid - 1;
+    }
+    const int jj = lo;
+    const int chunk = unit - plan->unit_begin[jj];
+    const int seg_s = plan->seg_start[jj], seg_c = plan->seg_cnt[jj];
+    const int cr = plan->chunk_rows[jj];
+    const int p0 = seg_s + (chunk * cs + rank) * cr;
+    const int p1 = min(seg_s + seg_c, p0 + cr);
+    const int nblk = p1 > p0 ? (p1 - p0 + LH_ROWS - 1) / LH_ROWS : 0;
+    const uint32_t* gb = bits1 + static_cast<int64_t>(grp) * n;
+    float g0 = 0.f, h0 = 0.f, g1 = 0.f, h1 = 0.f;   // lane f: feature 32 grp + f, bins 0 and 1
+    for (int blk = warp; blk < nblk; blk += W) {
+      const int pos = p0 + blk * LH_ROWS + lane;
+      uint32_t word = 0u;
+      float gv = 0.f, hv = 0.f;   // rows past the end add zero
+      if (pos < p1) {
+        const uint32_t row = order ? __ldg(order + pos) : static_cast<uint32_t>(pos);
+        word = __ldg(gb + row);
+        gv = cbgd::load_gh(gpos, pos);
+        hv = cbgd::load_gh(hpos, pos);
+      }
+      s_row[warp][lane] = make_float4(__uint_as_float(word), gv, hv, 0.f);
+      __syncwarp();
+#pragma unroll 4
+      for (int j = 0; j < LH_ROWS; ++j) {
+        const float4 v = s_row[warp][j];
+        if ((__float_as_uint(v.x) >> lane) & 1u) {
+          g1 += v.y;
+          h1 += v.z;
+        } else {
+          g0 += v.y;
+          h0 += v.z;
+        }
+      }
+      __syncwarp();
+    }
+    s_acc[warp][0 * 2 * GROUP + 0 * GROUP + lane] = g0;   // [stat][bin][feature]
+    s_acc[warp][0 * 2 * GROUP + 1 * GROUP + lane] = g1;
+    s_acc[warp][1 * 2 * GROUP + 0 * GROUP + lane] = h0;
+    s_acc[warp][1 * 2 * GROUP + 1 * GROUP + lane] = h1;
+    __syncthreads();
+    // the CTA's warps in warp order
+    for (int c = threadIdx.x; c < CELLS; c += blockDim.x) {
+      float v = s_acc[0][c];
+      for (int w = 1; w < W; ++w) v += s_acc[w][c];
+      s_cta[c] = v;
+    }
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) queue_take(plan, &s_next, cs);
+    // this CTA's slice of the cells, summed over the cluster's CTAs in rank order
+    const int per = (CELLS + cs - 1) / cs;
+    float* dst = partials + static_cast<int64_t>(item) * CELLS;
+    for (int c = rank * per + threadIdx.x; c < min(CELLS, (rank + 1) * per); c += blockDim.x) {
+      float v = 0.f;
+      for (int r = 0; r < cs; ++r) v += cl.map_shared_rank(s_cta, r)[c];
+      dst[c] = v;
+    }
+    cl.sync();
+  }
 }
 
 // ---------------------------------------- lane-per-feature, one statistic per warp
@@ -1960,6 +2081,54 @@ cbg_status lane_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
   return CBG_OK;
 }
 
+// Geometry of the 1-bit kernel: 512-thread CTAs with static shared memory only, and the
+// cluster size (<= the requested one) that keeps the most CTAs resident.
+template <typename GH>
+cbg_status bits_geom(cbg_ctx* ctx, const HistConfig& L, HistGeom* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, HistGeom> cache;
+  const auto key = std::make_tuple(ctx->device, L.cluster, static_cast<int>(sizeof(GH)));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *out = it->second;
+      return CBG_OK;
+    }
+  }
+  auto kern = level_hist_bits_kernel<GH>;
+  HistGeom geom;
+  for (int cs = L.cluster; cs >= 1; cs >>= 1) {
+    if (cs > 8) CBG_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(cs * ctx->num_sms));
+    cfg.blockDim = dim3(static_cast<unsigned>(32 * LB_WARPS));
+    cfg.dynamicSmemBytes = 0;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(cs);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      clusters = 0;
+    }
+    if (clusters * cs > geom.clusters * geom.cs) {
+      geom.cs = cs;
+      geom.clusters = clusters;
+    }
+  }
+  if (geom.clusters == 0) return ::cbg::fail(ctx, CBG_EUNSUPPORTED, "no co-resident histogram cluster fits on this device");
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = geom;
+  *out = geom;
+  return CBG_OK;
+}
+
 // The cluster size the plan must chunk for, and the clusters of a launch (identical for
 // FP32 and BF16 gradients).
 cbg_status hist_cluster_geom(cbg_ctx* ctx, const HistConfig& L, int* cs, int* clusters) {
@@ -1969,6 +2138,7 @@ cbg_status hist_cluster_geom(cbg_ctx* ctx, const HistConfig& L, int* cs, int* cl
                   : L.kind == 5 ? lane_geom<float, 1>(ctx, L, &g)
                   : L.kind == 6 ? lane_geom<float, 2>(ctx, L, &g)
                   : L.kind == 8 ? lane_geom<float, 3>(ctx, L, &g)
+                  : L.kind == 9 ? bits_geom<float>(ctx, L, &g)
                                 : hist_geom<float>(ctx, L, &g);
   if (st != CBG_OK) return st;
   *cs = g.cs;
@@ -1994,6 +2164,7 @@ cbg_status hist_warm(cbg_ctx* ctx, const HistConfig& L) {
                   : L.kind == 5 ? lane_geom<GH, 1>(ctx, L, &g)
                   : L.kind == 6 ? lane_geom<GH, 2>(ctx, L, &g)
                   : L.kind == 8 ? lane_geom<GH, 3>(ctx, L, &g)
+                  : L.kind == 9 ? bits_geom<GH>(ctx, L, &g)
                                 : hist_geom<GH>(ctx, L, &g);
   if (st != CBG_OK) return st;
   int cs = 1;
@@ -2178,6 +2349,28 @@ cbg_status launch_hist(cbg_ctx* ctx, const HistConfig& L, const uint8_t* bins, c
                                      : packed ? level_hist_lane4_kernel<GH>
                                               : level_hist_lane_kernel<GH>,
                                      bins, L.n, L.G, L.F, order, gg, hh, plan, L.max_bins, partials));
+    return CBG_OK;
+  }
+  if (L.kind == 9) {   // `bins` is the 1-bit layout (bits1)
+    HistGeom geom;
+    st = bits_geom<GH>(ctx, L, &geom);
+    if (st != CBG_OK) return st;
+    if (geom.cs != cs) return ::cbg::fail(ctx, CBG_ECUDA, "histogram cluster size changed between plan and launch");
+    if (L.max_bins != 2) return ::cbg::fail(ctx, CBG_EINVAL, "the 1-bit histogram kernel needs max_bins = 2");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(geom.cs * geom.clusters));
+    cfg.blockDim = dim3(static_cast<unsigned>(32 * LB_WARPS));
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(geom.cs);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CBG_CUDA(ctx, cudaLaunchKernelEx(&cfg, level_hist_bits_kernel<GH>, reinterpret_cast<const uint32_t*>(bins), L.n,
+                                     L.G, L.F, order, gg, hh, plan, partials));
     return CBG_OK;
   }
   if (L.kind == 8) {

@@ -84,13 +84,15 @@ cbg_status make_layout(cbg_ctx* ctx, const cbg_tree_shape* s, Layout* L) {
   L->nb_alloc = pow2_at_least(L->max_bins);
   L->D = s->max_depth;
   CBG_REQUIRE(ctx, t.cluster >= 0 && t.cluster <= 16, "cluster must be in [0, 16]");
-  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 8, "kernel must be 0 (default), 1 (shared reductions), 2 "
+  CBG_REQUIRE(ctx, t.kernel >= 0 && t.kernel <= 9, "kernel must be 0 (default), 1 (shared reductions), 2 "
               "(warp-private, 16 features per warp), 3 (64-bit compare-and-swap), 4 (lane per feature), 5 (lane "
               "per feature, one statistic per warp), 6 (lane per feature over 4-bit packed bins), 7 (shared "
-              "integer reductions of fixed-point values) or 8 (lane per feature with a loader warp)");
+              "integer reductions of fixed-point values), 8 (lane per feature with loader warps) or 9 (1-bit "
+              "binary features)");
   CBG_REQUIRE(ctx, t.kernel != 6 || s->max_bins <= 16, "the 4-bit packed kernel needs max_bins <= 16");
+  CBG_REQUIRE(ctx, t.kernel != 9 || s->max_bins <= 2, "the 1-bit kernel needs max_bins <= 2");
   L->kind = t.kernel == 2 ? 0 : (t.kernel >= 3 ? t.kernel : 1);
-  const bool lane_kind = L->kind == 4 || L->kind == 5 || L->kind == 6 || L->kind == 8;
+  const bool lane_kind = L->kind == 4 || L->kind == 5 || L->kind == 6 || L->kind == 8 || L->kind == 9;
   const bool fixed_kind = L->kind == 7;
   L->rows_per_item = t.rows_per_item > 0 ? t.rows_per_item : (lane_kind ? 8192 : fixed_kind ? 4096 : 2048);
   L->cluster = t.cluster > 0 ? t.cluster : (lane_kind ? 2 : fixed_kind ? 4 : 8);
@@ -1202,6 +1204,8 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
               "bins must be 16-byte aligned for the lane-per-feature histogram kernel");
   CBG_REQUIRE(ctx, L.kind != 6 || (a->bins4 != nullptr && (reinterpret_cast<uintptr_t>(a->bins4) & 15) == 0),
               "the 4-bit packed histogram kernel needs bins4 (16-byte aligned, cbg_pack_bins4)");
+  CBG_REQUIRE(ctx, L.kind != 9 || (a->bits1 != nullptr && (reinterpret_cast<uintptr_t>(a->bits1) & 15) == 0),
+              "the 1-bit histogram kernel needs bits1 (16-byte aligned, cbg_pack_bits1)");
   CBG_REQUIRE(ctx, a->gh_dtype == CBG_F32 || a->gh_dtype == CBG_BF16, "bad gh_dtype");
   CBG_REQUIRE(ctx, a->l2 >= 0.0 && std::isfinite(a->l2), "l2 must be finite and >= 0");
   CBG_REQUIRE(ctx, a->force_feature < L.F, "force_feature out of range");
@@ -1237,8 +1241,10 @@ cbg_status build_level_impl(cbg_ctx* ctx, const cbg_level_args* a, bool do_hist)
   // partition moved along (for the FP32 shared-reduction kernel, which is bound by its
   // compare-and-swap loops, the copy costs the partition more than it saves; the loader-
   // warp kernel, whose loaders could gather by row from L2, lost a third of its speed so)
-  const bool by_pos = L.kind == 4 || L.kind == 5 || L.kind == 6 || L.kind == 7 || L.kind == 8;
-  const uint8_t* hist_bins = L.kind == 6 ? a->bins4 : a->bins;
+  const bool by_pos = L.kind == 4 || L.kind == 5 || L.kind == 6 || L.kind == 7 || L.kind == 8 || L.kind == 9;
+  const uint8_t* hist_bins = L.kind == 6   ? a->bins4
+                             : L.kind == 9 ? reinterpret_cast<const uint8_t*>(a->bits1)
+                                           : a->bins;
   const void* g_pos = d == 0 ? a->g : at<char>(S, d % 2 == 1 ? L.o_gp_a : L.o_gp_b);
   const void* h_pos = d == 0 ? a->h : at<char>(S, d % 2 == 1 ? L.o_hp_a : L.o_hp_b);
   void* g_pos_nxt = at<char>(S, (d + 1) % 2 == 1 ? L.o_gp_a : L.o_gp_b);
@@ -1378,6 +1384,7 @@ cbg_status boost_one_tree(cbg_ctx* ctx, const cbg_boost_args* a, cbg_split* sp, 
     la.hist_out = nullptr;
     la.last_level = d == D - 1;
     la.bins4 = a->bins4;
+    la.bits1 = a->bits1;
     st = cbg_build_level(ctx, &la);
     if (st != CBG_OK) return st;
   }
@@ -1795,6 +1802,21 @@ cbg_status cbg_boost_batched(cbg_ctx* ctx, const cbg_problem* problems, int32_t 
 
 }  // extern "C"
 
+cbg_status cbg_pack_bits1(cbg_ctx* ctx, const uint8_t* bins, int64_t n, int32_t F_pad, uint32_t* bits1) {
+  if (!ctx) return CBG_EINVAL;
+  CBG_REQUIRE(ctx, n >= 1 && n <= INT32_MAX, "n must be in [1, 2^31-1]");
+  CBG_REQUIRE(ctx, F_pad >= GROUP && F_pad % GROUP == 0, "F_pad must be a positive multiple of 32");
+  CBG_REQUIRE(ctx, bins && bits1, "NULL argument");
+  CBG_REQUIRE(ctx, ((reinterpret_cast<uintptr_t>(bins) | reinterpret_cast<uintptr_t>(bits1)) & 15) == 0,
+              "bins and bits1 must be 16-byte aligned");
+  DeviceGuard guard(ctx->device);
+  const int G = F_pad / GROUP;
+  pack_bits1_kernel<<<grid_stride_blocks(static_cast<int64_t>(G) * n, 256), 256, 0, ctx->stream>>>(bins, n, G, bits1,
+                                                                                                   ctx->d_status);
+  CBG_CHECK_LAUNCH(ctx);
+  return CBG_OK;
+}
+
 cbg_status cbg_pack_bins4(cbg_ctx* ctx, const uint8_t* bins, int64_t n, int32_t F_pad, uint8_t* bins4) {
   if (!ctx) return CBG_EINVAL;
   CBG_REQUIRE(ctx, n >= 1 && n <= INT32_MAX, "n must be in [1, 2^31-1]");
@@ -1819,8 +1841,9 @@ namespace {
 // form with clusters of 2 and 8192 or 16384 rows; its one-statistic-per-warp form with clusters of 2 or 4 and
 // 8192 or 16384 rows; the 16-feature warp-private kernel once; with 4-bit packed bins
 // (at most 16 bins), the packed lane-per-feature kernel with clusters of 2 and 8192 or
-// 16384 rows.
-std::vector<cbg_tiles> autotune_candidates(bool packed, bool fixed_point) {
+// 16384 rows; with 1-bit packed bins (at most 2 bins), the 1-bit kernel with clusters of
+// 2 and 8192 or 32768 rows.
+std::vector<cbg_tiles> autotune_candidates(bool packed, bool fixed_point, bool bits) {
   std::vector<cbg_tiles> c;
   auto add = [&](int kernel, int cluster, int rows) {
     cbg_tiles t{};
@@ -1841,6 +1864,8 @@ std::vector<cbg_tiles> autotune_candidates(bool packed, bool fixed_point) {
   add(2, 2, 8192);
   if (packed)
     for (int r : {8192, 16384}) add(6, 2, r);
+  if (bits)
+    for (int r : {8192, 32768}) add(9, 2, r);
   return c;
 }
 
@@ -1867,6 +1892,7 @@ cbg_status tune_tree(cbg_ctx* ctx, const cbg_tree_shape* s, const cbg_autotune_a
     la.child_totals = a->child_totals;
     la.last_level = d == a->depth - 1;
     la.bins4 = a->bins4;
+    la.bits1 = a->bits1;
     st = cbg_build_level(ctx, &la);
     if (st != CBG_OK) return st;
   }
@@ -1878,7 +1904,7 @@ cbg_status tune_tree(cbg_ctx* ctx, const cbg_tree_shape* s, const cbg_autotune_a
 cbg_status cbg_autotune_state_bytes(const cbg_tree_shape* shape, size_t* bytes) {
   if (!shape || !bytes) return CBG_EINVAL;
   size_t mx = 0;
-  for (const cbg_tiles& t : autotune_candidates(shape->max_bins <= 16, true)) {
+  for (const cbg_tiles& t : autotune_candidates(shape->max_bins <= 16, true, shape->max_bins <= 2)) {
     cbg_tree_shape s = *shape;
     s.tiles = t;
     Layout L;
@@ -1910,7 +1936,8 @@ cbg_status cbg_autotune_tiles(cbg_ctx* ctx, const cbg_autotune_args* a, cbg_tile
   cbg_tiles best_c{};
   cbg_status result = CBG_OK;
   for (const cbg_tiles& cand : autotune_candidates(a->bins4 != nullptr && a->shape->max_bins <= 16,
-                                                   a->fixed_point != 0)) {
+                                                   a->fixed_point != 0,
+                                                   a->bits1 != nullptr && a->shape->max_bins <= 2)) {
     cbg_tree_shape s = *a->shape;
     s.tiles = cand;
     Layout L;

@@ -50,6 +50,7 @@ class Prepared:
     bins_t: object
     max_bins: int
     bins4: object = None   # 4-bit packed bins (cbg_pack_bins4) when max_bins <= 16
+    bits1: object = None   # 1-bit packed bins (cbg_pack_bits1) when max_bins <= 2
 
 
 def preprocess(ctx: cbg.Context, x, cat, y, label_kind: str, max_borders: int, a: float = 1.0,
@@ -90,7 +91,11 @@ def preprocess(ctx: cbg.Context, x, cat, y, label_kind: str, max_borders: int, a
     if max_bins <= 16:
         bins4 = torch.empty(((F_pad // 32 + 1) // 2) * 32 * n, dtype=torch.uint8, device=dev)
         cbg.cbg_pack_bins4(ctx, bins, n, F_pad, bins4)
-    return Prepared(n, F, Ff, F_pad, perm, prior, ts, borders, nb, bins, bins_t, max_bins, bins4)
+    bits1 = None
+    if max_bins <= 2:
+        bits1 = torch.empty((F_pad // 32) * n, dtype=torch.int32, device=dev)
+        cbg.cbg_pack_bits1(ctx, bins, n, F_pad, bits1)
+    return Prepared(n, F, Ff, F_pad, perm, prior, ts, borders, nb, bins, bins_t, max_bins, bins4, bits1)
 
 
 @dataclass
@@ -143,7 +148,7 @@ def fit(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, trees: int, 
         bufs = alloc_fit(prep, depth, trees, gh_dtype, tiles)
     cbg.cbg_boost(ctx, bufs.shape, bufs.state, prep.bins, prep.n_borders, y, loss, gh_dtype, depth, trees, lr,
                   l2, bufs.pred, bufs.g, bufs.h, bufs.leaf, bufs.splits, bufs.leaf_values, bufs.child_totals,
-                  bins_t=prep.bins_t, use_graph=use_graph, bins4=prep.bins4)
+                  bins_t=prep.bins_t, use_graph=use_graph, bins4=prep.bins4, bits1=prep.bits1)
     return Model(bufs.splits[:trees], bufs.leaf_values[:trees], bufs.pred, depth, lr)
 
 
@@ -317,7 +322,7 @@ def autotune(ctx: cbg.Context, prep: Prepared, y, loss: str, depth: int, l2: flo
     child = torch.empty((1 << depth, 2), dtype=torch.float64, device=dev)
     return cbg.cbg_autotune_tiles(ctx, shape, state, prep.bins, prep.n_borders, g, h, gh_dtype, depth, l2, leaf,
                                   splits, child, bins_t=prep.bins_t, reps=reps, bins4=prep.bins4,
-                                  fixed_point=fixed_point)
+                                  fixed_point=fixed_point, bits1=prep.bits1)
 
 
 # Tilings timed on a whole batch: the shared-reduction kernel (whose histograms of a level

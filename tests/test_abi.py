@@ -69,3 +69,16 @@ def test_context_on_missing_device_is_rejected():
     h = ctypes.c_void_p()
     assert lib.cbg_ctx_create(999, None, 0, ctypes.byref(h)) == cbg.CBG_EINVAL
     assert not h.value
+
+
+def test_packed_kernels_reject_shapes_with_too_many_bins():
+    """Host-side shape checks: the 1-bit kernel (9) needs max_bins <= 2, the 4-bit one (6)
+    max_bins <= 16, and kernels above 9 do not exist."""
+    ok = cbg.cbg_tree_state_bytes(cbg.make_shape(1000, 10, 32, 2, 4, {"kernel": 9}))
+    assert ok > 0
+    assert cbg.cbg_tree_state_bytes(cbg.make_shape(1000, 10, 32, 16, 4, {"kernel": 6})) > 0
+    for bad in (cbg.make_shape(1000, 10, 32, 3, 4, {"kernel": 9}), cbg.make_shape(1000, 10, 32, 17, 4, {"kernel": 6}),
+                cbg.make_shape(1000, 10, 32, 2, 4, {"kernel": 10})):
+        with pytest.raises(cbg.CbgError) as e:
+            cbg.cbg_tree_state_bytes(bad)
+        assert e.value.status == cbg.CBG_EINVAL

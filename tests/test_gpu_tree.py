@@ -78,6 +78,10 @@ class Tree:
         if tiles and tiles.get("kernel") == 6:
             self.bins4 = torch.empty(((F_pad // 32 + 1) // 2) * 32 * n, dtype=torch.uint8, device="cuda")
             cbg.cbg_pack_bins4(ctx, self.bins, n, F_pad, self.bins4)
+        self.bits1 = None
+        if tiles and tiles.get("kernel") == 9:
+            self.bits1 = torch.empty((F_pad // 32) * n, dtype=torch.int32, device="cuda")
+            cbg.cbg_pack_bits1(ctx, self.bins, n, F_pad, self.bits1)
         self.nb = to_dev(nb.astype(np.int32))
         tdt = torch.float32 if dtype == "f32" else torch.bfloat16
         self.dtype = dtype
@@ -98,7 +102,7 @@ class Tree:
         t.ctx, t.n, t.F, t.F_pad, t.max_bins, t.D, t.dtype = ctx, n, F, F_pad, max_bins, max_depth, dtype
         t.shape = cbg.make_shape(n, F, F_pad, max_bins, max_depth)
         t.state = torch.empty(cbg.cbg_tree_state_bytes(t.shape), dtype=torch.uint8, device="cuda")
-        t.bins, t.bins_t, t.bins4, t.nb, t.g, t.h = bins, bins_t, None, nb, g, h
+        t.bins, t.bins_t, t.bins4, t.bits1, t.nb, t.g, t.h = bins, bins_t, None, None, nb, g, h
         t.leaf = torch.empty(n, dtype=torch.int16, device="cuda")
         t.splits = torch.empty((max_depth, 2), dtype=torch.float64, device="cuda")
         t.child = torch.empty((1 << max_depth, 2), dtype=torch.float64, device="cuda")
@@ -110,7 +114,7 @@ class Tree:
         hist = torch.empty(((1 << d), self.F, self.max_bins, 2), dtype=torch.float64, device="cuda")
         cbg.cbg_build_level(self.ctx, self.shape, self.state, self.bins, self.nb, self.g, self.h, self.dtype, d, l2,
                             self.leaf, self.splits, self.child, bins_t=self.bins_t, force=force, hist_out=hist,
-                            last_level=last, bins4=self.bins4)
+                            last_level=last, bins4=self.bins4, bits1=self.bits1)
         cbg.cbg_sync(self.ctx)
         sp = train.decode_splits(self.splits)[d]
         return to_host(hist), int(sp["feature"]), int(sp["border"]), float(sp["score"]), \
@@ -548,6 +552,99 @@ def test_packed_kernel_trains_like_the_oracle(ctx):
     lockstep_check(res, sp, to_host(model.pred), to_host(model.leaf_values), where="packed")
     tiles, ms = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2)
     assert tiles["kernel"] in (1, 2, 4, 5, 6, 8) and ms > 0
+
+
+def test_pack_bits1_layout(ctx):
+    import torch
+    rng = np.random.default_rng(5)
+    for n, F_pad in [(1, 32), (1000, 96), (4097, 128)]:
+        rm = rng.integers(0, 2, size=(n, F_pad)).astype(np.uint8)
+        bins = to_dev(train.grouped_from_rowmajor(rm))
+        out = torch.empty((F_pad // 32) * n, dtype=torch.int32, device="cuda")
+        cbg.cbg_pack_bits1(ctx, bins, n, F_pad, out)
+        cbg.cbg_sync(ctx)
+        got = to_host(out).view(np.uint32).reshape(F_pad // 32, n)
+        weights = (np.uint64(1) << np.arange(32, dtype=np.uint64))
+        want = np.stack([(rm[:, 32 * q:32 * q + 32].astype(np.uint64) * weights).sum(axis=1)
+                         for q in range(F_pad // 32)]).astype(np.uint32)
+        assert np.array_equal(got, want), (n, F_pad)
+
+
+def test_pack_bits1_flags_bins_of_2_and_more(ctx):
+    """A bin that does not fit 1 bit makes the next cbg_sync report CBG_EDATA."""
+    import torch
+    rm = np.zeros((100, 64), np.uint8)
+    rm[41, 37] = 2
+    out = torch.empty(2 * 100, dtype=torch.int32, device="cuda")
+    cbg.cbg_pack_bits1(ctx, to_dev(train.grouped_from_rowmajor(rm)), 100, 64, out)
+    with pytest.raises(cbg.CbgError) as e:
+        cbg.cbg_sync(ctx)
+    assert e.value.status == cbg.CBG_EDATA
+    cbg.cbg_sync(ctx)
+
+
+BITS_CASES = [
+    # n, F, F_pad, max_bins, depth, integer_grads, dtype, bins_t
+    (5003, 40, 64, 2, 6, True, "f32", True),
+    (50000, 70, 96, 2, 6, False, "f32", True),
+    (777, 1, 32, 2, 3, False, "f32", True),
+    (20000, 33, 64, 2, 5, False, "bf16", False),
+    (1, 3, 32, 2, 2, False, "f32", True),
+    (30011, 64, 64, 2, 7, True, "f32", True),
+]
+
+
+@pytest.mark.parametrize("case", BITS_CASES)
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_bits1_histogram_kernel_matches_oracle(ctx, case, cluster):
+    """The 1-bit kernel (tiles.kernel = 9) on forced levels against the oracle: exact on
+    integer gradients (where it also equals the uint8 lane kernel bit for bit), within the
+    FP32-accumulation bound otherwise; its leaf indices and child totals follow."""
+    n, F, F_pad, max_bins, depth, intg, dtype, bt = case
+    bins, nb, g, h, forced = synth.random_level_case(n + F + 19, n, F, F_pad, max_bins, depth, integer_grads=intg)
+    if dtype == "bf16":
+        g, h = _bf16(g), _bf16(h)
+    tiles = {"kernel": 9, "cluster": cluster, "rows_per_item": 8192}
+    t = Tree(ctx, bins, nb, g, h, depth, dtype, tiles=tiles, with_bins_t=bt)
+    u = Tree(ctx, bins, nb, g, h, depth, dtype, tiles=dict(tiles, kernel=4), with_bins_t=bt) if intg else None
+    g64, h64 = g.astype(np.float64), h.astype(np.float64)
+    leaf = np.zeros(n, np.uint16)
+    root_abs = None
+    for d in range(depth):
+        hist, sf, sk, _, gl, child = t.level(d, 3.0, force=forced[d], last=(d == depth - 1))
+        ref = oracle.histogram(bins, F, g64, h64, leaf, 1 << d, t.max_bins)
+        ref_abs = oracle.histogram(bins, F, np.abs(g64), np.abs(h64), leaf, 1 << d, t.max_bins)
+        if root_abs is None:
+            root_abs = ref_abs[0]
+        if intg:
+            assert np.array_equal(hist, ref), d
+            hist_u, *_, child_u = u.level(d, 3.0, force=forced[d], last=(d == depth - 1))
+            assert np.array_equal(hist, hist_u) and np.array_equal(child, child_u), d
+        else:
+            assert hist_tolerance_ok(hist, ref, np.maximum(ref_abs, root_abs[None])), d
+        leaf = oracle.update_leaf(bins, forced[d][0], forced[d][1], d, leaf)
+        assert np.array_equal(gl, leaf), d
+
+
+def test_bits1_kernel_trains_like_the_oracle(ctx):
+    """Whole boosting runs with tiles.kernel = 9 on a 1-border (binary) workload, in lock
+    step with the oracle; the autotuner, given the 1-bit bins, may pick the kernel."""
+    import dataclasses
+    w = dataclasses.replace(synth.logloss_1m(n=40000, trees=8), max_borders=1)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    assert prep.max_bins <= 2 and prep.bits1 is not None
+    y = to_dev(w.y)
+    model = train.fit(ctx, prep, y, w.loss, w.depth, w.trees, w.lr, w.l2,
+                      tiles={"kernel": 9, "cluster": 2, "rows_per_item": 8192}, use_graph=True)
+    cbg.cbg_sync(ctx)
+    ref_prep = oracle.preprocess(w, prep.F_pad)
+    sp = model.host_splits()
+    res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, w.depth, w.trees, w.lr, w.l2,
+                     follow=sp)
+    lockstep_check(res, sp, to_host(model.pred), to_host(model.leaf_values), where="1-bit")
+    tiles, ms = train.autotune(ctx, prep, y, w.loss, w.depth, w.l2)
+    assert tiles["kernel"] in (1, 2, 4, 5, 6, 8, 9) and ms > 0
 
 
 def test_fixed_point_form_trains_like_the_oracle(ctx):
