@@ -453,7 +453,6 @@ __global__ void __launch_bounds__(512, 1) level_hist_wp_kernel(const uint8_t* __
   cgr::cluster_group cl = cgr::this_cluster();
   const int cs = static_cast<int>(cl.num_blocks());
   const int rank = static_cast<int>(cl.block_rank());
-  const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int half = warp & 1, share = warp >> 1, shares = W >> 1;
   const int r = lane >> 4, f = lane & 15;
@@ -688,7 +687,6 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
   cgr::cluster_group cl = cgr::this_cluster();
   const int cs = static_cast<int>(cl.num_blocks());
   const int rank = static_cast<int>(cl.block_rank());
-  const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int per_warp = max_bins * GROUP;   // float2 cells of one warp histogram
   float2* hist_all = reinterpret_cast<float2*>(lsh);
@@ -1141,7 +1139,6 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
   cgr::cluster_group cl = cgr::this_cluster();
   const int cs = static_cast<int>(cl.num_blocks());
   const int rank = static_cast<int>(cl.block_rank());
-  const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int G4 = (G + 1) / 2;
   const int per_warp = max_bins * 2 * GROUP;   // float2 cells of one warp histogram
@@ -1475,7 +1472,6 @@ __global__ void __launch_bounds__(LH_MAX_WARPS * 32, 1)
   cgr::cluster_group cl = cgr::this_cluster();
   const int cs = static_cast<int>(cl.num_blocks());
   const int rank = static_cast<int>(cl.block_rank());
-  const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int pair = warp >> 1, stat = warp & 1, P = W >> 1;
   const GH* sv = stat == 0 ? gpos : hpos;
