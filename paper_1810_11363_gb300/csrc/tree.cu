@@ -820,9 +820,16 @@ __device__ __forceinline__ void part_scatter_body(const uint32_t* __restrict__ o
                                     void* __restrict__ g_out, void* __restrict__ h_out, int gh_bytes, int bid, int nblk) {
   __shared__ uint32_t sh[PT_THREADS / 32];
   __shared__ int sh_pos[1 << (MAX_DEPTH - 1)], sh_leaf[1 << (MAX_DEPTH - 1)];
+  __shared__ uint32_t sh_ob[1 << (MAX_DEPTH - 1)];   // per segment: ones before it (level order)
+  __shared__ int sh_zeros[1 << (MAX_DEPTH - 1)];     // per segment: rows of its "0" side
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int L = 1 << depth;
   load_seg_table(cur, L, sh_pos, sh_leaf);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {   // the same thread wrote sh_leaf[i]
+    const int l = sh_leaf[i];
+    sh_ob[i] = cur->ones_before[l];
+    sh_zeros[i] = cur->cnt[l] - static_cast<int>(cur->ones[l]);
+  }
   const int64_t base = static_cast<int64_t>(bid) * PT + static_cast<int64_t>(threadIdx.x) * PT_PER_THREAD;
   const bool whole = base + PT_PER_THREAD <= n;
   uint8_t fl[PT_PER_THREAD];
@@ -889,10 +896,9 @@ __device__ __forceinline__ void part_scatter_body(const uint32_t* __restrict__ o
     if (pos < n) {
       const uint32_t row = rows[i];
       while (si + 1 < L && sh_pos[si + 1] <= pos) ++si;
-      const int l = sh_leaf[si];
-      const int start = cur->start[l];
-      const uint32_t ob = ones_before - cur->ones_before[l];       // ones of leaf l before pos
-      const int zeros_total = cur->cnt[l] - static_cast<int>(cur->ones[l]);
+      const int start = sh_pos[si];
+      const uint32_t ob = ones_before - sh_ob[si];   // ones of the segment before pos
+      const int zeros_total = sh_zeros[si];
       int dst;
       if (fl[i])
         dst = start + zeros_total + static_cast<int>(ob);
