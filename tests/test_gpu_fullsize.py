@@ -48,15 +48,22 @@ def _check_bins(prep, ref, n):
     return bins
 
 
+# The histogram tiles the bench's autotuner picks on these workloads (the loader-warp
+# kernel), so that the full-size parity runs in the launch configuration the bench times.
+BENCH_TILES_DENSE = {"kernel": 8, "cluster": 2, "rows_per_item": 8192}
+BENCH_TILES_PRECISION = {"kernel": 8, "cluster": 2, "rows_per_item": 16384}
+
+
 def test_dense_400k_full_size(ctx):
     """The Epsilon-shaped workload at its stated size: 4e5 rows x 2000 N(0,1) features, 128
-    borders, depth 8, lr 0.1. Preprocessing bit-exact, then 5 trees in lock step."""
+    borders, depth 8, lr 0.1, with the bench's histogram tiles. Preprocessing bit-exact,
+    then 5 trees in lock step."""
     import torch
     w = synth.dense_400k(trees=5)
     y = to_dev(w.y)
     prep = train.preprocess(ctx, to_dev(w.x), torch.zeros((0, w.n), dtype=torch.int32, device="cuda"), y,
                             "binary", w.max_borders, a=w.a, seed=w.seed)
-    model = train.fit(ctx, prep, y, w.loss, w.depth, w.trees, w.lr, w.l2, use_graph=True)
+    model = train.fit(ctx, prep, y, w.loss, w.depth, w.trees, w.lr, w.l2, tiles=BENCH_TILES_DENSE, use_graph=True)
     cbg.cbg_sync(ctx)
     assert np.array_equal(to_host(prep.perm, np.uint32), oracle.make_permutation(w.seed, w.n))
     ref = oracle.preprocess(w, prep.F_pad, workers=WORKERS)
@@ -181,12 +188,13 @@ def test_precision_10m_tree_levels(ctx, p10m, dtype, levels):
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_precision_10m_lockstep(ctx, p10m, dtype):
-    """3 depth-10 trees on the full 10^7 rows in lock step with the oracle that rounds g and
-    h to the same storage type (splits, leaf values, predictions within 1e-4). For BF16
-    storage, the error against the oracle on unrounded (FP32-stored) gradients, with the
-    same tree structure, is reported too."""
+    """3 depth-10 trees on the full 10^7 rows, with the bench's histogram tiles, in lock step
+    with the oracle that rounds g and h to the same storage type (splits, leaf values,
+    predictions within 1e-4). For BF16 storage, the error against the oracle on unrounded
+    (FP32-stored) gradients, with the same tree structure, is reported too."""
     w, P, prep, ref, yd = p10m
-    model = train.fit(ctx, prep, yd, w.loss, w.depth, w.trees, w.lr, w.l2, gh_dtype=dtype, use_graph=True)
+    model = train.fit(ctx, prep, yd, w.loss, w.depth, w.trees, w.lr, w.l2, gh_dtype=dtype, tiles=BENCH_TILES_PRECISION,
+                      use_graph=True)
     cbg.cbg_sync(ctx)
     sp = model.host_splits()
     pred, lv = to_host(model.pred), to_host(model.leaf_values)

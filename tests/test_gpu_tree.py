@@ -273,23 +273,53 @@ def test_boost_logloss_end_to_end(ctx, use_graph):
 
 
 @pytest.mark.slow
-def test_full_size_logloss_1m_lockstep(ctx):
+@pytest.mark.parametrize("tiles", [None, {"kernel": 8, "cluster": 2, "rows_per_item": 16384}],
+                         ids=["default", "bench"])
+def test_full_size_logloss_1m_lockstep(ctx, tiles):
     """The benchmark's 1M x 110 workload, depth 6, lr 0.05: 50 trees in lock step with the
     oracle on the same bins (every level's split, every leaf value, and the predictions
-    after the last tree within 1e-4)."""
+    after the last tree within 1e-4), with the library's default histogram kernel and with
+    the tiles the bench's autotuner picks (the loader-warp kernel)."""
     w = synth.logloss_1m(trees=50)
     prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
                             seed=w.seed)
     ref_prep = oracle.preprocess(w, prep.F_pad)
     bins_gpu = train.rowmajor_from_grouped(to_host(prep.bins), w.n, prep.F_pad)
     assert np.array_equal(bins_gpu, ref_prep["bins"])
-    model = train.fit(ctx, prep, to_dev(w.y), w.loss, w.depth, w.trees, w.lr, w.l2, use_graph=True)
+    model = train.fit(ctx, prep, to_dev(w.y), w.loss, w.depth, w.trees, w.lr, w.l2, tiles=tiles, use_graph=True)
     cbg.cbg_sync(ctx)
     sp = model.host_splits()
     res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, w.depth, w.trees, w.lr,
                      w.l2, follow=sp)
     rep = lockstep_check(res, sp, to_host(model.pred), to_host(model.leaf_values), where="logloss_1m")
-    report(f"logloss_1m 1M x 110, {w.trees} trees", rep)
+    report(f"logloss_1m 1M x 110, {w.trees} trees, {'bench' if tiles else 'default'} tiles", rep)
+
+
+def test_full_size_binary_features_1bit_lockstep(ctx):
+    """logloss_1m's columns quantised with one border each (every feature binary) at the
+    full 10^6 rows: 1-bit packing bit-exact against the oracle's bins, and 10 trees of the
+    1-bit histogram kernel in lock step with the oracle (splits, leaf values, predictions
+    after the last tree within 1e-4)."""
+    import dataclasses
+    w = dataclasses.replace(synth.logloss_1m(trees=10), max_borders=1)
+    prep = train.preprocess(ctx, to_dev(w.x), to_dev(w.cat), to_dev(w.y), "binary", w.max_borders, a=w.a,
+                            seed=w.seed)
+    assert prep.max_bins == 2 and prep.bits1 is not None
+    ref_prep = oracle.preprocess(w, prep.F_pad)
+    assert np.array_equal(train.rowmajor_from_grouped(to_host(prep.bins), w.n, prep.F_pad), ref_prep["bins"])
+    words = to_host(prep.bits1).view(np.uint32).reshape(prep.F_pad // 32, w.n)
+    weights = np.uint64(1) << np.arange(32, dtype=np.uint64)
+    for q in range(prep.F_pad // 32):
+        want = (ref_prep["bins"][:, 32 * q:32 * q + 32].astype(np.uint64) * weights).sum(axis=1).astype(np.uint32)
+        assert np.array_equal(words[q], want), q
+    model = train.fit(ctx, prep, to_dev(w.y), w.loss, w.depth, w.trees, w.lr, w.l2,
+                      tiles={"kernel": 9, "cluster": 2, "rows_per_item": 8192}, use_graph=True)
+    cbg.cbg_sync(ctx)
+    sp = model.host_splits()
+    res = oracle.fit(ref_prep["bins"], w.n_features, ref_prep["n_borders"], w.y, w.loss, w.depth, w.trees, w.lr,
+                     w.l2, follow=sp)
+    rep = lockstep_check(res, sp, to_host(model.pred), to_host(model.leaf_values), where="binary 1M")
+    report(f"binary features 1M x 110 (1 border), 1-bit kernel, {w.trees} trees", rep)
 
 
 def test_invalid_level_arguments_are_rejected(ctx):
